@@ -1,0 +1,367 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module builds geometry only: cell types, fill levels, density and
+velocity fields, plus the physical parameters of each workload.  It holds none
+of the method's arithmetic (no distributions, no mass exchange, no bubble
+volumes), so both the CUDA library and the CPU oracle can take their inputs
+from it.
+
+Lattice conventions: arrays have shape (nz, ny, nx) and flatten to the linear
+index i = x + nx*(y + ny*z); cell (x, y, z) covers [x, x+1) x [y, y+1) x
+[z, z+1) and its centre is (x+0.5, y+0.5, z+0.5).  Every axis wraps; walls are
+obstacle cells inside the box.  Fill levels (the liquid fraction, Sec. 2.2 of
+the paper) are the fraction of sub x sub x sub sample points of the cell that
+lie outside every gas region.
+
+Workloads (paper Sec. 3 stands behind 2 and 3):
+  static_bubble       32^3 periodic box, one spherical bubble of radius 8.
+  gas_thread          256x64x64, gas cylinder along x with a sinusoidal radius
+                      perturbation (capillary breakup of a gas thread, Sec. 3.1).
+  orifice             128x128x256 bubble formation at a submerged orifice fed by
+                      a gas reservoir (Sec. 3.2).
+  bubble_population   many independent small domains with random bubbles.
+  foam                512^3 dense lognormal bubble packing under a moving lid.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, List, Optional, Tuple
+
+import numpy as np
+
+LIQUID, INTERFACE, GAS, OBSTACLE, LID = 0, 1, 2, 3, 4
+BGK, TRT = 0, 1
+
+# the 18 non-rest neighbour offsets (dx, dy, dz) of the D3Q19 neighbourhood
+_N18 = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+        if 0 < abs(dx) + abs(dy) + abs(dz) <= 2]
+
+
+@dataclasses.dataclass
+class Scenario:
+    """One lattice: geometry arrays plus its physical parameters."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    flags: np.ndarray          # uint8 (nz, ny, nx)
+    fill: np.ndarray           # float64 (nz, ny, nx)
+    rho: np.ndarray            # float64 (nz, ny, nx)
+    u: np.ndarray              # float64 (3, nz, ny, nx)
+    collision: int = BGK
+    tau: float = 0.8
+    magic: float = 3.0 / 16.0
+    sigma: float = 0.0
+    gravity: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    eps: float = 1e-3
+    lid: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    normal_rule: int = 1
+    # (seed cell, extra volume, volume drain per step, constant pressure)
+    sources: List[Tuple[int, float, float, int]] = dataclasses.field(default_factory=list)
+    steps: int = 0
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def params(self) -> dict:
+        return dict(nx=self.nx, ny=self.ny, nz=self.nz, collision=self.collision, tau=self.tau,
+                    magic=self.magic, sigma=self.sigma, gravity=tuple(self.gravity), eps=self.eps,
+                    lid=tuple(self.lid), normal_rule=self.normal_rule)
+
+    def linear(self, x: int, y: int, z: int) -> int:
+        return int(x + self.nx * (y + self.ny * z))
+
+
+# ------------------------------------------------------------------ helpers
+
+def _centres(shape):
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64) + 0.5,
+                          np.arange(ny, dtype=np.float64) + 0.5,
+                          np.arange(nx, dtype=np.float64) + 0.5, indexing="ij")
+    return x, y, z
+
+
+def liquid_fraction(shape, sdf: Callable, sub: int = 4, band: float = 1.0) -> np.ndarray:
+    """Fraction of sub^3 sample points per cell where sdf(x, y, z) >= 0.
+
+    sdf < 0 marks gas; it must grow no faster than about one unit per cell, so
+    that cells whose centre value exceeds `band` in magnitude are entirely on
+    one side and only the band around the surface is sub-sampled.
+    """
+    x, y, z = _centres(shape)
+    d = sdf(x, y, z)
+    fill = (d >= 0.0).astype(np.float64)
+    near = np.abs(d) <= band
+    if not near.any():
+        return fill
+    xs, ys, zs = x[near], y[near], z[near]
+    cnt = np.zeros(xs.shape, dtype=np.int64)
+    offs = (np.arange(sub, dtype=np.float64) + 0.5) / sub - 0.5
+    for oz in offs:
+        for oy in offs:
+            for ox in offs:
+                cnt += (sdf(xs + ox, ys + oy, zs + oz) >= 0.0)
+    fill[near] = cnt / float(sub ** 3)
+    return fill
+
+
+def _any_neighbour(mask: np.ndarray) -> np.ndarray:
+    out = np.zeros_like(mask)
+    for dx, dy, dz in _N18:
+        out |= np.roll(mask, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
+    return out
+
+
+def classify(fill: np.ndarray, obstacle: Optional[np.ndarray] = None,
+             lid: Optional[np.ndarray] = None) -> np.ndarray:
+    """Cell types from fill levels, closing the interface layer.
+
+    Full cells are liquid, empty cells gas, partial cells interface; a liquid
+    cell with a gas neighbour becomes interface, so interface cells always
+    separate liquid from gas (Sec. 2.2).
+    """
+    flags = np.full(fill.shape, INTERFACE, dtype=np.uint8)
+    flags[fill >= 1.0] = LIQUID
+    flags[fill <= 0.0] = GAS
+    if obstacle is not None:
+        flags[obstacle] = OBSTACLE
+    if lid is not None:
+        flags[lid] = LID
+    gas = flags == GAS
+    close = (flags == LIQUID) & _any_neighbour(gas)
+    flags[close] = INTERFACE
+    return flags
+
+
+def _finish(name, flags, fill, rho=None, u=None, **kw) -> Scenario:
+    nz, ny, nx = flags.shape
+    fill = np.where(flags == LIQUID, 1.0, np.where(flags == INTERFACE, fill, 0.0))
+    if rho is None:
+        rho = np.ones(flags.shape)
+    if u is None:
+        u = np.zeros((3,) + flags.shape)
+    return Scenario(name=name, nx=nx, ny=ny, nz=nz, flags=np.ascontiguousarray(flags),
+                    fill=np.ascontiguousarray(fill, dtype=np.float64),
+                    rho=np.ascontiguousarray(rho, dtype=np.float64),
+                    u=np.ascontiguousarray(u, dtype=np.float64), **kw)
+
+
+def _spheres_sdf(centres: np.ndarray, radii: np.ndarray):
+    """Signed distance to a union of spheres (negative inside gas)."""
+    def sdf(x, y, z):
+        d = np.full(np.shape(x), np.inf)
+        for (cx, cy, cz), r in zip(centres, radii):
+            d = np.minimum(d, np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) - r)
+        return d
+    return sdf
+
+
+def _wall_shell(shape, axes) -> np.ndarray:
+    nz, ny, nx = shape
+    obs = np.zeros(shape, dtype=bool)
+    if 0 in axes:
+        obs[:, :, 0] = obs[:, :, nx - 1] = True
+    if 1 in axes:
+        obs[:, 0, :] = obs[:, ny - 1, :] = True
+    if 2 in axes:
+        obs[0, :, :] = obs[nz - 1, :, :] = True
+    return obs
+
+
+# ---------------------------------------------------------------- workloads
+
+def static_bubble(n: int = 32, radius: float = 8.0, sigma: float = 1e-3, tau: float = 0.8,
+                  collision: int = BGK, steps: int = 200) -> Scenario:
+    """Periodic n^3 box of liquid at rest with one spherical bubble at the centre."""
+    c = n / 2.0
+    sdf = _spheres_sdf(np.array([[c, c, c]]), np.array([radius]))
+    fill = liquid_fraction((n, n, n), sdf)
+    flags = classify(fill)
+    return _finish(f"static_bubble_{n}_r{radius:g}", flags, fill, collision=collision, tau=tau,
+                   sigma=sigma, steps=steps)
+
+
+def gas_thread(nx: int = 256, ny: int = 64, nz: int = 64, radius: float = 8.0, amp: float = 0.1,
+               wavelength: float = 64.0, sigma: float = 5e-3, tau: float = 0.8,
+               collision: int = TRT, steps: int = 20000) -> Scenario:
+    """Gas cylinder along x with radius R(x) = R (1 + amp sin(2 pi x / wavelength)),
+    periodic in x, no-slip walls on the other four sides (paper Sec. 3.1)."""
+    cy, cz = ny / 2.0, nz / 2.0
+
+    def sdf(x, y, z):
+        r = np.sqrt((y - cy) ** 2 + (z - cz) ** 2)
+        return r - radius * (1.0 + amp * np.sin(2.0 * np.pi * x / wavelength))
+
+    shape = (nz, ny, nx)
+    fill = liquid_fraction(shape, sdf, band=1.2)
+    obs = _wall_shell(shape, axes=(1, 2))
+    flags = classify(fill, obstacle=obs)
+    return _finish(f"gas_thread_{nx}x{ny}x{nz}", flags, fill, collision=collision, tau=tau,
+                   sigma=sigma, steps=steps)
+
+
+def orifice(nx: int = 128, ny: int = 128, nz: int = 256, plate_z: int = 8, hole_radius: float = 6.0,
+            depth: int = 200, cap_radius: float = 6.0, drain: float = 0.02, reservoir: float = 2e4,
+            gravity: float = 1e-5, sigma: float = 2e-3, tau: float = 0.8, steps: int = 100000) -> Scenario:
+    """Bubble formation at a submerged circular orifice (paper Sec. 3.2).
+
+    No-slip box; a plate at z = plate_z with a circular hole; gas reservoir
+    below the plate whose volume shrinks by `drain` cells^3 per step; liquid up
+    to z = plate_z + depth with a constant-pressure gas layer above; a
+    hemispherical gas cap of radius `cap_radius` sits on the hole.  Density is
+    hydrostatic, rho = 1 + 3 g (h - z), h the liquid surface height.
+    """
+    shape = (nz, ny, nx)
+    x, y, z = _centres(shape)
+    hx, hy = nx / 2.0, ny / 2.0
+    top = plate_z + 1 + depth
+    obs = _wall_shell(shape, axes=(0, 1, 2))
+    rr = np.sqrt((x - hx) ** 2 + (y - hy) ** 2)
+    plate = (np.floor(z) == plate_z) & (rr > hole_radius)
+    obs |= plate
+
+    def sdf(xx, yy, zz):
+        below = plate_z + 0.5 - zz           # > 0 below the plate centre: reservoir gas
+        above = zz - top                      # > 0 in the atmosphere
+        cap = cap_radius - np.sqrt((xx - hx) ** 2 + (yy - hy) ** 2 + (zz - (plate_z + 1.0)) ** 2)
+        hole = np.where(np.abs(zz - (plate_z + 0.5)) <= 0.5, hole_radius - np.sqrt((xx - hx) ** 2 + (yy - hy) ** 2), -np.inf)
+        gas = np.maximum(np.maximum(below, above), np.maximum(cap, hole))
+        return -gas
+
+    fill = liquid_fraction(shape, sdf, band=1.5)
+    flags = classify(fill, obstacle=obs)
+    rho = 1.0 + 3.0 * gravity * (top - z)
+    rho = np.where((flags == LIQUID) | (flags == INTERFACE), rho, 1.0)
+    seed = int(hx) + nx * (int(hy) + ny * 2)
+    atm = int(hx) + nx * (int(hy) + ny * (nz - 3))
+    return _finish(f"orifice_{nx}x{ny}x{nz}", flags, fill, rho=rho, collision=TRT, tau=tau,
+                   sigma=sigma, gravity=(0.0, 0.0, -gravity), steps=steps,
+                   sources=[(seed, reservoir, drain, 0), (atm, 0.0, 0.0, 1)])
+
+
+def _rsa(rng, dims, radii, gap, max_attempts, periodic=True):
+    """Random sequential addition of non-overlapping spheres with a liquid gap."""
+    placed_c, placed_r = [], []
+    dims = np.asarray(dims, dtype=np.float64)
+    attempts = 0
+    for r in radii:
+        ok = False
+        while attempts < max_attempts and not ok:
+            attempts += 1
+            c = rng.uniform(0.0, 1.0, 3) * dims
+            good = True
+            for pc, pr in zip(placed_c, placed_r):
+                d = c - pc
+                if periodic:
+                    d -= dims * np.round(d / dims)
+                if np.sqrt((d * d).sum()) < r + pr + gap:
+                    good = False
+                    break
+            if good:
+                placed_c.append(c)
+                placed_r.append(r)
+                ok = True
+        if attempts >= max_attempts:
+            break
+    return np.array(placed_c).reshape(-1, 3), np.array(placed_r)
+
+
+def _periodic_spheres_sdf(centres, radii, dims):
+    dims = np.asarray(dims, dtype=np.float64)
+
+    def sdf(x, y, z):
+        d = np.full(np.shape(x), np.inf)
+        for c, r in zip(centres, radii):
+            dx = x - c[0]; dx -= dims[0] * np.round(dx / dims[0])
+            dy = y - c[1]; dy -= dims[1] * np.round(dy / dims[1])
+            dz = z - c[2]; dz -= dims[2] * np.round(dz / dims[2])
+            d = np.minimum(d, np.sqrt(dx * dx + dy * dy + dz * dz) - r)
+        return d
+    return sdf
+
+
+def random_bubbles(nx: int, ny: int, nz: int, n_bubbles: int, r_min: float, r_max: float,
+                   u_max: float, sigma: float, seed: int, gap: float = 2.0,
+                   collision: int = TRT, tau: float = 0.8, max_attempts: int = 10000,
+                   steps: int = 2000) -> Scenario:
+    """Periodic box with randomly placed bubbles and a smooth random velocity field
+    (one Fourier mode per component, |u| <= u_max)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    radii = rng.uniform(r_min, r_max, n_bubbles)
+    centres, radii = _rsa(rng, (nx, ny, nz), radii, gap, max_attempts)
+    shape = (nz, ny, nx)
+    sdf = _periodic_spheres_sdf(centres, radii, (nx, ny, nz))
+    fill = liquid_fraction(shape, sdf)
+    flags = classify(fill)
+    x, y, z = _centres(shape)
+    u = np.zeros((3,) + shape)
+    k = rng.integers(1, 3, size=(3, 3))
+    ph = rng.uniform(0.0, 2.0 * np.pi, size=3)
+    amp = u_max * rng.uniform(0.3, 1.0) / math.sqrt(3.0)
+    for c in range(3):
+        arg = 2.0 * np.pi * (k[c, 0] * x / nx + k[c, 1] * y / ny + k[c, 2] * z / nz) + ph[c]
+        u[c] = amp * np.sin(arg)
+    u[:, (flags == GAS)] = 0.0
+    return _finish(f"random_bubbles_{nx}x{ny}x{nz}_s{seed}", flags, fill, u=u, collision=collision,
+                   tau=tau, sigma=sigma, steps=steps)
+
+
+def bubble_population(n_domains: int = 64, seed: int = 0, sides=(32, 48, 64, 96), steps: int = 2000):
+    """Independent domains, each axis drawn from `sides`, 20-200 bubbles of radius
+    U[3, 10] per domain by random sequential addition (attempt cap 10^4),
+    |u0| <= 0.02, sigma ~ U[1e-3, 5e-3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for d in range(n_domains):
+        nx, ny, nz = (int(v) for v in rng.choice(sides, 3))
+        nb = int(rng.integers(20, 201))
+        sig = float(rng.uniform(1e-3, 5e-3))
+        out.append(random_bubbles(nx, ny, nz, nb, 3.0, 10.0, 0.02, sig, seed=int(rng.integers(1 << 31)),
+                                  steps=steps))
+    return out
+
+
+def foam(n: int = 512, gas_fraction: float = 0.4, seed: int = 0, lid_speed: float = 0.05,
+         gravity: float = 1e-5, sigma: float = 3e-3, max_attempts: int = 200000, steps: int = 10000) -> Scenario:
+    """Dense bubble packing: lognormal radii (median 8, sigma_log 0.3, clipped to
+    [4, 16]) placed by random sequential addition toward `gas_fraction`; periodic
+    in x and y, no-slip bottom, lid moving at u_x = lid_speed on top."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    target = gas_fraction * n ** 3
+    radii = []
+    vol = 0.0
+    while vol < target:
+        r = float(np.clip(np.exp(np.log(8.0) + 0.3 * rng.standard_normal()), 4.0, 16.0))
+        radii.append(r)
+        vol += 4.0 / 3.0 * np.pi * r ** 3
+    radii = np.sort(np.array(radii))[::-1]
+    centres, radii = _rsa(rng, (n, n, n - 4), radii, 2.0, max_attempts)
+    centres[:, 2] += 2.0
+    shape = (n, n, n)
+    fill = np.ones(shape)
+    # per-sphere local stamping keeps this linear in the number of spheres
+    offs = (np.arange(4, dtype=np.float64) + 0.5) / 4 - 0.5
+    for c, r in zip(centres, radii):
+        lo = np.floor(c - r - 1).astype(int)
+        hi = np.ceil(c + r + 1).astype(int)
+        zi = np.arange(lo[2], hi[2]); yi = np.arange(lo[1], hi[1]); xi = np.arange(lo[0], hi[0])
+        zz, yy, xx = np.meshgrid(zi, yi, xi, indexing="ij")
+        cnt = np.zeros(zz.shape)
+        for oz in offs:
+            for oy in offs:
+                for ox in offs:
+                    d = np.sqrt((xx + 0.5 + ox - c[0]) ** 2 + (yy + 0.5 + oy - c[1]) ** 2 + (zz + 0.5 + oz - c[2]) ** 2)
+                    cnt += d < r
+        frac_gas = cnt / 64.0
+        sl = (np.mod(zz, n), np.mod(yy, n), np.mod(xx, n))
+        fill[sl] = np.minimum(fill[sl], 1.0 - frac_gas)
+    obs = np.zeros(shape, dtype=bool)
+    obs[0] = True
+    lid = np.zeros(shape, dtype=bool)
+    lid[n - 1] = True
+    flags = classify(fill, obstacle=obs, lid=lid)
+    return _finish(f"foam_{n}", flags, fill, collision=TRT, sigma=sigma, gravity=(0.0, 0.0, -gravity),
+                   lid=(lid_speed, 0.0, 0.0), steps=steps)
