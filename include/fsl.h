@@ -1,0 +1,161 @@
+/*
+ * fsl.h -- C ABI of the GB300 (sm_103a) free-surface lattice Boltzmann library
+ * with the enhanced bubble model of Anderl, Bogner, Rauh, Ruede and Delgado,
+ * "Free Surface Lattice Boltzmann with Enhanced Bubble Model" (arXiv:1604.01632).
+ *
+ * One handle (fsl_domain) holds one or more independent lattices ("domains")
+ * that advance together, one GPU, one CUDA stream.  All state lives in device
+ * memory owned by the library; inputs are copied in, outputs copied out.
+ *
+ * Lattice conventions (every call):
+ *   - domain d has nx*ny*nz cells; linear index i = x + nx*(y + ny*z); every
+ *     axis wraps, walls are obstacle cells;
+ *   - cell types (uint8): FSL_LIQUID, FSL_INTERFACE, FSL_GAS, FSL_OBSTACLE
+ *     (no-slip wall), FSL_LID (wall moving at lid_velocity) -- paper Sec. 2.2,
+ *     "Different cell types": only liquid and interface cells carry PDFs;
+ *   - vector fields are structure-of-arrays: u[c*n + i], c = 0,1,2; PDF fields
+ *     are f[a*n + i] in the D3Q19 order rest, +x, -x, +y, -y, +z, -z, then the
+ *     (x,y), (x,z), (y,z) edge pairs with each direction followed by its
+ *     opposite (paper Sec. 2.1, D3Q19).
+ *
+ * Errors: every call returns an fsl_status.  Errors found on the device
+ * (NaN density, a broken interface layer, a full bubble table, a labelling pass
+ * that did not converge) latch into a device status word that the next
+ * synchronising call (fsl_sync, fsl_bubbles, fsl_fields) returns; the handle
+ * stays usable for reading state.  No call throws; no device wait is
+ * unbounded.  fsl_last_error() gives a one-line description.
+ */
+#ifndef FSL_H
+#define FSL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsl_domain fsl_domain;
+
+typedef enum {
+    FSL_OK = 0,
+    FSL_ERR_ARG = -1,                 /* bad argument or call order */
+    FSL_ERR_GEOMETRY = -2,            /* a liquid cell touches a gas cell */
+    FSL_ERR_OOM = -3,                 /* device allocation failed */
+    FSL_ERR_NAN = -4,                 /* a cell density became NaN */
+    FSL_ERR_CCL_NOT_CONVERGED = -5,   /* union-find pass hit its iteration cap */
+    FSL_ERR_TABLE_FULL = -6,          /* more bubbles than bubble_capacity */
+    FSL_ERR_CUDA = -7                 /* a CUDA runtime call failed */
+} fsl_status;
+
+enum { FSL_LIQUID = 0, FSL_INTERFACE = 1, FSL_GAS = 2, FSL_OBSTACLE = 3, FSL_LID = 4 };
+enum { FSL_BGK = 0, FSL_TRT = 1 };
+
+/* Storage precision of the PDFs.  FP64 collides in FP64; the others collide in
+ * FP32.  The F16S/BF16S forms store the deviation f_a - w_a (rho0 = 1).  Mass,
+ * fill level and every bubble quantity stay FP64 in all forms. */
+typedef enum { FSL_P_FP64 = 0, FSL_P_FP32 = 1, FSL_P_F16S = 2, FSL_P_BF16S = 3 } fsl_precision;
+
+/* Physical parameters of one domain, lattice units. */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t collision;        /* FSL_BGK or FSL_TRT (paper Sec. 2.1 uses BGK) */
+    double tau;               /* relaxation time, omega+ = 1/tau (paper Eq. 6) */
+    double magic;             /* TRT magic parameter Lambda, e.g. 3/16 */
+    double sigma;             /* surface tension (paper Eq. 15) */
+    double gravity[3];        /* body force per unit density, Guo forcing */
+    double eps;               /* conversion threshold: filled m > (1+eps) rho, emptied m < -eps rho */
+    double lid_velocity[3];   /* velocity of FSL_LID cells */
+    int32_t normal_rule;      /* 1: also rebuild PDFs whose direction has n.c < 0 (paper Eq. 11 text) */
+    int32_t bubble_capacity;  /* bubble-table slots for this domain; 0 = default */
+} fsl_params;
+
+/* One bubble (paper Sec. 2.3): id = minimum linear index of its gas and
+ * interface cells; volume = V(t) including extra_volume; init_volume = V*;
+ * pressure = p_V of paper Eq. 13 (p0 = 1/3). */
+typedef struct {
+    int64_t id;
+    double volume;
+    double init_volume;
+    double pressure;
+    int64_t n_cells;
+    int32_t const_pressure;
+    int32_t pad;
+    double extra_volume;
+} fsl_bubble;
+
+/* Field selectors for fsl_fields; dst[k] receives the k-th selected field in
+ * this bit order. */
+enum {
+    FSL_F_FLAGS = 1,   /* uint8[n] */
+    FSL_F_FILL = 2,    /* double[n], fill level phi (paper Eq. 9) */
+    FSL_F_MASS = 4,    /* double[n], interface mass m (meaningful on interface cells) */
+    FSL_F_ID = 8,      /* int64[n], bubble id of gas/interface cells, -1 elsewhere */
+    FSL_F_RHO = 16,    /* double[n], density of the stored (post-collision) PDFs (Eq. 4) */
+    FSL_F_U = 32,      /* double[3n], velocity of the stored PDFs (Eq. 5) */
+    FSL_F_PDF = 64     /* double[19n], stored post-collision PDFs, unshifted */
+};
+
+/* Create a handle for n_domains independent domains; params[d] describes
+ * domain d.  cuda_stream: the cudaStream_t every call enqueues on (NULL =
+ * legacy default stream).  Allocates all device state. */
+fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t precision,
+                      void* cuda_stream, fsl_domain** out);
+
+/* Load the initial state of domain d (paper Sec. 2.2): cell types, fill
+ * levels (interface cells), density and velocity; f = f_eq(rho, u), m = phi
+ * rho.  Pointers are host memory (on_device = 0) or device memory on the
+ * handle's GPU (on_device = 1).  Rejects (FSL_ERR_GEOMETRY) a liquid cell with
+ * a gas neighbour.  Every domain must be initialised before the first step;
+ * bubbles are found (flood fill, paper Sec. 2.3.2) with V* = V, p = p0. */
+fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, const double* fill,
+                             const double* rho, const double* u, int32_t on_device);
+
+/* Attach a source to the bubble holding seed_cell of domain d: a reservoir of
+ * extra volume extra0 that shrinks by rate per step (gas inflow, paper Sec.
+ * 3.2), or a constant-pressure atmosphere (const_pressure = 1, p = p0).  Call
+ * after fsl_init_geometry, before stepping.  One reservoir per domain. */
+fsl_status fsl_set_bubble_source(fsl_domain* h, int32_t d, int64_t seed_cell, double extra0,
+                                 double rate, int32_t const_pressure);
+
+/* Advance every domain by nsteps time steps: stream/bounce-back, mass
+ * exchange (paper Eq. 10), free-surface reconstruction (Eq. 11-15),
+ * collision (Eq. 6), cell conversion with excess-mass redistribution, bubble
+ * volume update, and merge/split detection by connected-component labelling
+ * (Secs. 2.3.1, 2.3.2).  Asynchronous on the handle's stream. */
+fsl_status fsl_step(fsl_domain* h, int64_t nsteps);
+
+/* Wait for the stream and return the latched device status. */
+fsl_status fsl_sync(fsl_domain* h);
+
+/* Bubble table of domain d sorted by id; writes min(cap, count) records and
+ * the number of bubbles to *count.  Synchronises. */
+fsl_status fsl_bubbles(fsl_domain* h, int32_t d, fsl_bubble* out, int64_t cap, int64_t* count);
+
+/* Copy the fields selected by mask of domain d into dst[0..], host memory
+ * (on_device = 0) or device memory (on_device = 1).  Synchronises. */
+fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst, int32_t on_device);
+
+/* Free the handle and its device memory. */
+fsl_status fsl_destroy(fsl_domain* h);
+
+/* Last error text of this handle ("" if none); valid until the next call. */
+const char* fsl_last_error(const fsl_domain* h);
+
+/* Number of kernels this handle has launched (graph replays count each of
+ * their kernels). */
+int64_t fsl_kernel_launches(const fsl_domain* h);
+
+/* Device time of the stream-collide kernels of the last fsl_step call, in
+ * milliseconds, summed over its steps (0 when timing is off).  Timing is
+ * switched on with fsl_set_timing(h, 1); it brackets each stream-collide
+ * launch with CUDA events on the handle's stream. */
+fsl_status fsl_set_timing(fsl_domain* h, int32_t on);
+double fsl_stream_collide_ms(const fsl_domain* h);
+
+/* Counts of the cell types of domain d (array of 5), synchronises. */
+fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

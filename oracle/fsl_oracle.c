@@ -43,7 +43,9 @@
  *     (filled cells turn gas neighbours into interface, cancel emptied marks
  *     next to them), phase B (emptied cells turn liquid neighbours into
  *     interface).  New interface cells from gas get f = f_eq of the mean
- *     density and velocity of their liquid/interface neighbours, m = 0.
+ *     density and velocity of their liquid/interface neighbours, m = 0; new
+ *     interface cells from liquid keep f, take m = rho and join the bubble of
+ *     their first emptied neighbour in direction order.
  *   - Excess mass (filled: m - rho; emptied: m) is split equally among the
  *     neighbours that are interface after conversion; with no such neighbour
  *     it goes to a global pool (fixed point 2^-40) that is shared equally by
@@ -626,12 +628,12 @@ static void step_once(ora_sim* s) {
      * initialised from their liquid/interface neighbours. */
     for (int64_t i = 0; i < n; ++i) {
         if (s->flag[i] != LIQ) continue;
+        /* the new interface cell joins the bubble of its first emptied
+         * neighbour in direction order */
         int64_t best = -1;
-        for (int a = 1; a < 19; ++a) {
+        for (int a = 1; a < 19 && best < 0; ++a) {
             int64_t z = nbr(s, i, CX[a], CY[a], CZ[a]);
-            if (s->flag[z] == IFC && s->mark[z] == MK_EMPTIED) {
-                if (best < 0 || s->id[z] < best) best = s->id[z];
-            }
+            if (s->flag[z] == IFC && s->mark[z] == MK_EMPTIED) best = s->id[z];
         }
         if (best >= 0) {
             double fo[19], r, j[3];

@@ -1,0 +1,656 @@
+// fsl_api.cu -- the C ABI of include/fsl.h: device memory, stream ordering,
+// step graphs, state exports.  Host code only; kernels live in fsl_core.cu
+// (precision-independent + FP64) and fsl_fast.cu (FP32 / FP16 / BF16 forms).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/fsl.h"
+#include "fsl_device.cuh"
+#include "fsl_internal.h"
+
+using namespace fsl;
+
+namespace {
+
+const int kDefaultCapacityMin = 256;
+
+}  // namespace
+
+struct fsl_domain {
+    int ndom = 0;
+    int precision = 0;
+    size_t fbytes = 8;            // bytes per stored PDF
+    cudaStream_t user = nullptr;  // caller's stream (may be the legacy default)
+    cudaStream_t ls = nullptr;    // library stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<fsl_params> params;
+    std::vector<Dom> hdoms;
+    long long stride = 0;          // padded cells
+    long long nblocks = 0;
+    long long nslots = 0;
+    std::vector<int> blk_dom;
+    std::vector<int> slot_dom;
+
+    // device state
+    Dom* d_doms = nullptr;
+    int* d_blk_dom = nullptr;
+    int* d_slot_dom = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t *flag = nullptr, *mark = nullptr;
+    double *m = nullptr, *phi = nullptr, *rhoi = nullptr, *exs = nullptr;
+    int* id = nullptr;
+    long long *vfx = nullptr, *vxfx = nullptr, *vsfx = nullptr, *ncells = nullptr;
+    int* constp = nullptr;
+    long long *pool = nullptr, *nif = nullptr;
+    int* trig = nullptr;
+    int* status = nullptr;
+    // labelling scratch
+    int *lab = nullptr, *aux = nullptr;
+    unsigned long long* hkeys = nullptr;
+    long long* hvals = nullptr;
+    long long hcap = 0;
+    long long *nvfx = nullptr, *nvxfx = nullptr, *nvsfx = nullptr, *nncells = nullptr;
+    int *nconstp = nullptr, *croot = nullptr, *minc = nullptr, *nslot = nullptr;
+    long long* vtot = nullptr;
+    int* minidx = nullptr;
+    long long* counts = nullptr;
+
+    std::vector<bool> inited;
+    bool need_initial_ccl = true;
+    bool stepped = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_kernels = 0;
+    long long launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> evpool;
+    size_t evused = 0;
+    double k1_ms = 0.0;
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+namespace {
+
+fsl_status fail(fsl_domain* h, fsl_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+fsl_status cuda_fail(fsl_domain* h, cudaError_t e, const char* where) {
+    return fail(h, FSL_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(fsl_domain* h, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) {
+        h->allocs.push_back(q);
+        *p = (P*)q;
+    }
+    return e;
+}
+
+StepArgs step_args(fsl_domain* h, int src) {
+    StepArgs A;
+    A.doms = h->d_doms;
+    A.blk_dom = h->d_blk_dom;
+    A.stride = h->stride;
+    A.fsrc = h->f[src];
+    A.fdst = h->f[1 - src];
+    A.flag = h->flag;
+    A.mark = h->mark;
+    A.m = h->m;
+    A.phi = h->phi;
+    A.rhoi = h->rhoi;
+    A.exs = h->exs;
+    A.id = h->id;
+    A.vfx = h->vfx;
+    A.vxfx = h->vxfx;
+    A.vsfx = h->vsfx;
+    A.ncells = h->ncells;
+    A.constp = h->constp;
+    A.pool = h->pool;
+    A.nif = h->nif;
+    A.trig = h->trig;
+    A.status = h->status;
+    A.ndom = h->ndom;
+    return A;
+}
+
+CclArgs ccl_args(fsl_domain* h, int initial) {
+    CclArgs K;
+    K.lab = h->lab;
+    K.aux = h->aux;
+    K.hkeys = h->hkeys;
+    K.hvals = h->hvals;
+    K.hcap = h->hcap;
+    K.nvfx = h->nvfx;
+    K.nvxfx = h->nvxfx;
+    K.nvsfx = h->nvsfx;
+    K.nncells = h->nncells;
+    K.nconstp = h->nconstp;
+    K.croot = h->croot;
+    K.vtot = h->vtot;
+    K.minc = h->minc;
+    K.nslot = h->nslot;
+    K.slot_dom = h->d_slot_dom;
+    K.nslots_total = h->nslots;
+    K.initial = initial;
+    // find() walks strictly decreasing indices and every retry of unite()
+    // follows a link made by another thread, so both loops end; the caps only
+    // turn a corrupted label array into an error status
+    K.max_iter = 1 << 24;
+    return K;
+}
+
+void launch_k1(fsl_domain* h, const StepArgs& A) {
+    switch (h->precision) {
+    case FSL_P_FP64: launch_stream_collide<double>(A, h->nblocks, h->ls); break;
+    case FSL_P_FP32: launch_stream_collide<float>(A, h->nblocks, h->ls); break;
+    case FSL_P_F16S: launch_stream_collide<__half>(A, h->nblocks, h->ls); break;
+    default: launch_stream_collide<__nv_bfloat16>(A, h->nblocks, h->ls); break;
+    }
+}
+
+void launch_cb(fsl_domain* h, const StepArgs& A) {
+    switch (h->precision) {
+    case FSL_P_FP64: launch_convert_b<double>(A, h->nblocks, h->ls); break;
+    case FSL_P_FP32: launch_convert_b<float>(A, h->nblocks, h->ls); break;
+    case FSL_P_F16S: launch_convert_b<__half>(A, h->nblocks, h->ls); break;
+    default: launch_convert_b<__nv_bfloat16>(A, h->nblocks, h->ls); break;
+    }
+}
+
+// One time step from buffer src into 1 - src.  Returns the kernels launched.
+int enqueue_step(fsl_domain* h, int src, bool timed) {
+    StepArgs A = step_args(h, src);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+        while (h->evpool.size() < h->evused + 2) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->evpool.push_back(e);
+        }
+        e0 = h->evpool[h->evused++];
+        e1 = h->evpool[h->evused++];
+        cudaEventRecord(e0, h->ls);
+    }
+    launch_k1(h, A);
+    if (timed) cudaEventRecord(e1, h->ls);
+    launch_convert_a(A, h->nblocks, h->ls);
+    launch_cb(h, A);
+    launch_convert_c(A, h->nblocks, h->ls);
+    launch_convert_d(A, h->nblocks, h->ls);
+    int k = 5 + launch_ccl(A, ccl_args(h, 0), h->nblocks, h->vsfx, h->constp, h->ls);
+    return k;
+}
+
+// Order library work after the caller's stream, and the caller after it.
+void join_in(fsl_domain* h) {
+    cudaEventRecord(h->ev_in, h->user);
+    cudaStreamWaitEvent(h->ls, h->ev_in, 0);
+}
+void join_out(fsl_domain* h) {
+    cudaEventRecord(h->ev_out, h->ls);
+    cudaStreamWaitEvent(h->user, h->ev_out, 0);
+}
+
+fsl_status latch(fsl_domain* h) {
+    int st = 0;
+    cudaError_t e = cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (st != 0) {
+        const char* what = st == FSL_ERR_GEOMETRY ? "a liquid cell touches a gas cell"
+                           : st == FSL_ERR_NAN ? "a density became NaN"
+                           : st == FSL_ERR_CCL_NOT_CONVERGED ? "bubble labelling hit its iteration cap"
+                           : st == FSL_ERR_TABLE_FULL ? "bubble table full"
+                                                      : "device error";
+        return fail(h, (fsl_status)st, what);
+    }
+    return FSL_OK;
+}
+
+fsl_status ensure_initial(fsl_domain* h) {
+    if (!h->need_initial_ccl) return FSL_OK;
+    for (int d = 0; d < h->ndom; ++d)
+        if (!h->inited[d]) return fail(h, FSL_ERR_ARG, "every domain must be initialised first");
+    StepArgs A = step_args(h, h->cur);
+    h->launches += launch_ccl(A, ccl_args(h, 1), h->nblocks, h->vsfx, h->constp, h->ls);
+    h->need_initial_ccl = false;
+    return FSL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t precision, void* cuda_stream,
+                      fsl_domain** out) {
+    if (!params || !out || n_domains <= 0 || precision < 0 || precision > 3) return FSL_ERR_ARG;
+    *out = nullptr;
+    fsl_domain* h = new fsl_domain();
+    h->ndom = n_domains;
+    h->precision = precision;
+    h->fbytes = precision == FSL_P_FP64 ? 8 : (precision == FSL_P_FP32 ? 4 : 2);
+    h->user = (cudaStream_t)cuda_stream;
+    long long off = 0;
+    long long soff = 0;
+    for (int d = 0; d < n_domains; ++d) {
+        const fsl_params& p = params[d];
+        long long n = (long long)p.nx * p.ny * p.nz;
+        if (p.nx <= 0 || p.ny <= 0 || p.nz <= 0 || n >= (1LL << 31) || !(p.tau > 0.5)) {
+            delete h;
+            return FSL_ERR_ARG;
+        }
+        h->params.push_back(p);
+        Dom D;
+        memset(&D, 0, sizeof(D));
+        D.nx = p.nx; D.ny = p.ny; D.nz = p.nz; D.n = (int)n;
+        D.off = off;
+        long long cap = p.bubble_capacity > 0 ? p.bubble_capacity : std::max<long long>(kDefaultCapacityMin, n / 64);
+        D.slot_off = (int)soff;
+        D.slot_cap = (int)cap;
+        D.seed = -1;
+        D.normal_rule = p.normal_rule;
+        D.rate_fx = 0;
+        D.omp = 1.0 / p.tau;
+        D.omm = p.collision == FSL_TRT ? 1.0 / (p.magic / (p.tau - 0.5) + 0.5) : D.omp;
+        D.sigma2 = 2.0 * p.sigma;
+        for (int k = 0; k < 3; ++k) { D.g[k] = p.gravity[k]; D.lid[k] = p.lid_velocity[k]; }
+        D.eps = p.eps;
+        h->hdoms.push_back(D);
+        long long padded = (n + FSL_BLOCK - 1) / FSL_BLOCK * FSL_BLOCK;
+        for (long long b = 0; b < padded / FSL_BLOCK; ++b) h->blk_dom.push_back(d);
+        for (long long s = 0; s < cap; ++s) h->slot_dom.push_back(d);
+        off += padded;
+        soff += cap;
+    }
+    if (off >= (1LL << 31) || soff >= (1LL << 31)) { delete h; return FSL_ERR_ARG; }
+    h->stride = off;
+    h->nblocks = off / FSL_BLOCK;
+    h->nslots = soff;
+    h->inited.assign(n_domains, false);
+    long long hc = 1024;
+    while (hc < 4 * soff) hc <<= 1;
+    h->hcap = hc;
+
+    cudaError_t e = upload_tables();
+    if (e != cudaSuccess) { fsl_status st = cuda_fail(h, e, "tables"); delete h; return st; }
+    e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    const size_t N = (size_t)h->stride, NS = (size_t)h->nslots;
+#define AL(ptr, bytes) if (e == cudaSuccess) e = dalloc(h, &(ptr), (bytes))
+    AL(h->d_doms, sizeof(Dom) * n_domains);
+    AL(h->d_blk_dom, sizeof(int) * h->blk_dom.size());
+    AL(h->d_slot_dom, sizeof(int) * NS);
+    AL(h->f[0], 19 * N * h->fbytes);
+    AL(h->f[1], 19 * N * h->fbytes);
+    AL(h->flag, N);
+    AL(h->mark, N);
+    AL(h->m, 8 * N);
+    AL(h->phi, 8 * N);
+    AL(h->rhoi, 8 * N);
+    AL(h->exs, 8 * N);
+    AL(h->id, 4 * N);
+    AL(h->vfx, 8 * NS);
+    AL(h->vxfx, 8 * NS);
+    AL(h->vsfx, 8 * NS);
+    AL(h->ncells, 8 * NS);
+    AL(h->constp, 4 * NS);
+    AL(h->pool, 8 * n_domains);
+    AL(h->nif, 8 * n_domains);
+    AL(h->trig, sizeof(int));
+    AL(h->status, sizeof(int));
+    AL(h->lab, 4 * N);
+    AL(h->aux, 4 * N);
+    AL(h->hkeys, 8 * (size_t)hc);
+    AL(h->hvals, 8 * (size_t)hc);
+    AL(h->nvfx, 8 * NS);
+    AL(h->nvxfx, 8 * NS);
+    AL(h->nvsfx, 8 * NS);
+    AL(h->nncells, 8 * NS);
+    AL(h->nconstp, 4 * NS);
+    AL(h->croot, 4 * NS);
+    AL(h->minc, 4 * NS);
+    AL(h->vtot, 8 * NS);
+    AL(h->nslot, 4 * n_domains);
+    AL(h->minidx, 4 * NS);
+    AL(h->counts, 8 * 8);
+#undef AL
+    if (e != cudaSuccess) {
+        fsl_status st = (e == cudaErrorMemoryAllocation) ? FSL_ERR_OOM : FSL_ERR_CUDA;
+        fsl_destroy(h);
+        return st;
+    }
+    e = cudaMemcpy(h->d_doms, h->hdoms.data(), sizeof(Dom) * n_domains, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_blk_dom, h->blk_dom.data(), sizeof(int) * h->blk_dom.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_slot_dom, h->slot_dom.data(), sizeof(int) * NS, cudaMemcpyHostToDevice);
+    // padding and not-yet-initialised cells are obstacles
+    if (e == cudaSuccess) e = cudaMemset(h->flag, OBS, N);
+    if (e == cudaSuccess) e = cudaMemset(h->mark, 0, N);
+    if (e == cudaSuccess) e = cudaMemset(h->id, 0xff, 4 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->m, 0, 8 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->phi, 0, 8 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->rhoi, 0, 8 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->exs, 0, 8 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->f[0], 0, 19 * N * h->fbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->f[1], 0, 19 * N * h->fbytes);
+    if (e == cudaSuccess) e = cudaMemset(h->pool, 0, 8 * n_domains);
+    if (e == cudaSuccess) e = cudaMemset(h->nif, 0, 8 * n_domains);
+    if (e == cudaSuccess) e = cudaMemset(h->trig, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->vfx, 0, 8 * NS);
+    if (e == cudaSuccess) e = cudaMemset(h->vxfx, 0, 8 * NS);
+    if (e == cudaSuccess) e = cudaMemset(h->vsfx, 0, 8 * NS);
+    if (e == cudaSuccess) e = cudaMemset(h->ncells, 0, 8 * NS);
+    if (e == cudaSuccess) e = cudaMemset(h->constp, 0, 4 * NS);
+    if (e != cudaSuccess) {
+        fsl_destroy(h);
+        return FSL_ERR_CUDA;
+    }
+    *out = h;
+    return FSL_OK;
+}
+
+fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, const double* fill, const double* rho,
+                             const double* u, int32_t on_device) {
+    if (!h || d < 0 || d >= h->ndom || !flags || !fill || !rho || !u) return fail(h, FSL_ERR_ARG, "bad argument");
+    if (h->stepped) return fail(h, FSL_ERR_ARG, "initialise every domain before the first step");
+    const Dom& D = h->hdoms[d];
+    const size_t n = (size_t)D.n;
+    uint8_t* dfl = nullptr;
+    double *dfi = nullptr, *drh = nullptr, *du = nullptr;
+    bool staged = !on_device;
+    if (staged) {
+        CK(h, cudaMalloc(&dfl, n));
+        CK(h, cudaMalloc(&dfi, 8 * n));
+        CK(h, cudaMalloc(&drh, 8 * n));
+        CK(h, cudaMalloc(&du, 24 * n));
+        CK(h, cudaMemcpy(dfl, flags, n, cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(dfi, fill, 8 * n, cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(drh, rho, 8 * n, cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(du, u, 24 * n, cudaMemcpyHostToDevice));
+    } else {
+        dfl = (uint8_t*)flags; dfi = (double*)fill; drh = (double*)rho; du = (double*)u;
+    }
+    join_in(h);
+    StepArgs A = step_args(h, 1 - h->cur);   // writes into f[cur]
+    switch (h->precision) {
+    case FSL_P_FP64: launch_init_state<double>(A, d, D.n, dfl, dfi, drh, du, h->ls); break;
+    case FSL_P_FP32: launch_init_state<float>(A, d, D.n, dfl, dfi, drh, du, h->ls); break;
+    case FSL_P_F16S: launch_init_state<__half>(A, d, D.n, dfl, dfi, drh, du, h->ls); break;
+    default: launch_init_state<__nv_bfloat16>(A, d, D.n, dfl, dfi, drh, du, h->ls); break;
+    }
+    h->launches += 1;
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->ls));
+    if (staged) {
+        cudaFree(dfl); cudaFree(dfi); cudaFree(drh); cudaFree(du);
+    }
+    fsl_status st = latch(h);
+    if (st != FSL_OK) return st;
+    h->inited[d] = true;
+    h->need_initial_ccl = true;
+    join_out(h);
+    return FSL_OK;
+}
+
+fsl_status fsl_set_bubble_source(fsl_domain* h, int32_t d, int64_t seed_cell, double extra0, double rate,
+                                 int32_t const_pressure) {
+    if (!h || d < 0 || d >= h->ndom) return fail(h, FSL_ERR_ARG, "bad domain");
+    Dom& D = h->hdoms[d];
+    if (seed_cell < 0 || seed_cell >= D.n) return fail(h, FSL_ERR_ARG, "seed cell outside the domain");
+    if (h->stepped) return fail(h, FSL_ERR_ARG, "sources are attached before the first step");
+    fsl_status st = ensure_initial(h);
+    if (st != FSL_OK) return st;
+    CK(h, cudaStreamSynchronize(h->ls));
+    int slot = -1;
+    CK(h, cudaMemcpy(&slot, h->id + D.off + seed_cell, sizeof(int), cudaMemcpyDeviceToHost));
+    if (slot < 0) return fail(h, FSL_ERR_ARG, "seed cell is not a gas or interface cell");
+    if (const_pressure) {
+        int one = 1;
+        CK(h, cudaMemcpy(h->constp + slot, &one, sizeof(int), cudaMemcpyHostToDevice));
+        return FSL_OK;
+    }
+    if (D.seed >= 0) return fail(h, FSL_ERR_ARG, "one reservoir per domain");
+    long long x0 = llrint(extra0 * 4294967296.0);
+    long long vs = 0;
+    CK(h, cudaMemcpy(&vs, h->vsfx + slot, sizeof(long long), cudaMemcpyDeviceToHost));
+    vs += x0;
+    CK(h, cudaMemcpy(h->vsfx + slot, &vs, sizeof(long long), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->vxfx + slot, &x0, sizeof(long long), cudaMemcpyHostToDevice));
+    D.seed = (int)seed_cell;
+    D.rate_fx = llrint(rate * 4294967296.0);
+    CK(h, cudaMemcpy(h->d_doms + d, &D, sizeof(Dom), cudaMemcpyHostToDevice));
+    return FSL_OK;
+}
+
+fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return fail(h, FSL_ERR_ARG, "bad argument");
+    fsl_status st = ensure_initial(h);
+    if (st != FSL_OK) return st;
+    h->stepped = true;
+    join_in(h);
+    if (h->timing) {
+        for (int64_t k = 0; k < nsteps; ++k) {
+            h->launches += enqueue_step(h, h->cur, true);
+            h->cur = 1 - h->cur;
+        }
+    } else {
+        int64_t k = 0;
+        if (nsteps >= 2) {
+            // two steps (A -> B -> A) per graph, one graph per starting buffer
+            if (!h->graph[h->cur]) {
+                cudaGraph_t gr;
+                CK(h, cudaStreamBeginCapture(h->ls, cudaStreamCaptureModeThreadLocal));
+                int kk = enqueue_step(h, h->cur, false);
+                kk += enqueue_step(h, 1 - h->cur, false);
+                CK(h, cudaStreamEndCapture(h->ls, &gr));
+                CK(h, cudaGraphInstantiate(&h->graph[h->cur], gr, 0));
+                cudaGraphDestroy(gr);
+                h->graph_kernels = kk;
+            }
+            for (; k + 2 <= nsteps; k += 2) {
+                CK(h, cudaGraphLaunch(h->graph[h->cur], h->ls));
+                h->launches += h->graph_kernels;
+            }
+        }
+        for (; k < nsteps; ++k) {
+            h->launches += enqueue_step(h, h->cur, false);
+            h->cur = 1 - h->cur;
+        }
+    }
+    CK(h, cudaGetLastError());
+    join_out(h);
+    return FSL_OK;
+}
+
+fsl_status fsl_sync(fsl_domain* h) {
+    if (!h) return FSL_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->ls));
+    if (h->timing && h->evused > 0) {
+        double tot = 0.0;
+        for (size_t k = 0; k + 1 < h->evused; k += 2) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, h->evpool[k], h->evpool[k + 1]);
+            tot += ms;
+        }
+        h->k1_ms = tot;
+        h->evused = 0;
+    }
+    return latch(h);
+}
+
+fsl_status fsl_set_timing(fsl_domain* h, int32_t on) {
+    if (!h) return FSL_ERR_ARG;
+    h->timing = on != 0;
+    h->k1_ms = 0.0;
+    h->evused = 0;
+    return FSL_OK;
+}
+
+double fsl_stream_collide_ms(const fsl_domain* h) { return h ? h->k1_ms : 0.0; }
+
+int64_t fsl_kernel_launches(const fsl_domain* h) { return h ? h->launches : 0; }
+
+const char* fsl_last_error(const fsl_domain* h) { return h ? h->err.c_str() : "null handle"; }
+
+static fsl_status compute_minidx(fsl_domain* h, int d) {
+    const Dom& D = h->hdoms[d];
+    CK(h, cudaMemsetAsync(h->minidx + D.slot_off, 0x7f, 4 * (size_t)D.slot_cap, h->ls));
+    launch_export_minid(h->id, D.off, D.n, h->minidx, h->ls);
+    h->launches += 1;
+    return FSL_OK;
+}
+
+fsl_status fsl_bubbles(fsl_domain* h, int32_t d, fsl_bubble* out, int64_t cap, int64_t* count) {
+    if (!h || d < 0 || d >= h->ndom || !count) return fail(h, FSL_ERR_ARG, "bad argument");
+    fsl_status st = ensure_initial(h);
+    if (st != FSL_OK) return st;
+    join_in(h);
+    st = compute_minidx(h, d);
+    if (st != FSL_OK) return st;
+    const Dom& D = h->hdoms[d];
+    const size_t C = (size_t)D.slot_cap;
+    std::vector<long long> vfx(C), vxfx(C), vsfx(C), nc(C);
+    std::vector<int> cp(C), mi(C);
+    CK(h, cudaMemcpyAsync(vfx.data(), h->vfx + D.slot_off, 8 * C, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaMemcpyAsync(vxfx.data(), h->vxfx + D.slot_off, 8 * C, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaMemcpyAsync(vsfx.data(), h->vsfx + D.slot_off, 8 * C, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaMemcpyAsync(nc.data(), h->ncells + D.slot_off, 8 * C, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaMemcpyAsync(cp.data(), h->constp + D.slot_off, 4 * C, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaMemcpyAsync(mi.data(), h->minidx + D.slot_off, 4 * C, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaStreamSynchronize(h->ls));
+    std::vector<fsl_bubble> rec;
+    const double unit = 2.3283064365386962890625e-10;
+    const double p0 = 1.0 / 3.0;
+    for (size_t s = 0; s < C; ++s) {
+        if (nc[s] <= 0) continue;
+        fsl_bubble b;
+        memset(&b, 0, sizeof(b));
+        b.id = mi[s];
+        double V = (double)(vfx[s] + vxfx[s]) * unit;
+        double Vs = (double)vsfx[s] * unit;
+        b.volume = V;
+        b.init_volume = Vs;
+        b.n_cells = nc[s];
+        b.const_pressure = cp[s];
+        b.extra_volume = (double)vxfx[s] * unit;
+        if (cp[s]) b.pressure = p0;
+        else if (V <= 1e-3) b.pressure = p0;
+        else b.pressure = (Vs / V) * p0;
+        rec.push_back(b);
+    }
+    std::sort(rec.begin(), rec.end(), [](const fsl_bubble& a, const fsl_bubble& b) { return a.id < b.id; });
+    *count = (int64_t)rec.size();
+    if (out) {
+        for (int64_t k = 0; k < cap && k < (int64_t)rec.size(); ++k) out[k] = rec[(size_t)k];
+    }
+    join_out(h);
+    return latch(h);
+}
+
+fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst, int32_t on_device) {
+    if (!h || d < 0 || d >= h->ndom || (mask & ~127u) || (mask && !dst)) return fail(h, FSL_ERR_ARG, "bad argument");
+    fsl_status st = ensure_initial(h);
+    if (st != FSL_OK) return st;
+    join_in(h);
+    const Dom& D = h->hdoms[d];
+    const size_t n = (size_t)D.n;
+    if (mask & FSL_F_ID) {
+        st = compute_minidx(h, d);
+        if (st != FSL_OK) return st;
+    }
+    // device targets: the caller's buffers, or temporaries copied out after
+    size_t sizes[7] = {n, 8 * n, 8 * n, 8 * n, 8 * n, 24 * n, 152 * n};
+    void* dev[7] = {nullptr};
+    std::vector<void*> tmp;
+    int k = 0;
+    for (int bit = 0; bit < 7; ++bit) {
+        if (!(mask & (1u << bit))) continue;
+        if (on_device) {
+            dev[bit] = dst[k];
+        } else {
+            void* p = nullptr;
+            CK(h, cudaMalloc(&p, sizes[bit]));
+            tmp.push_back(p);
+            dev[bit] = p;
+        }
+        ++k;
+    }
+    if (mask & (FSL_F_FLAGS | FSL_F_FILL | FSL_F_MASS | FSL_F_ID)) {
+        launch_export_cells(h->flag, h->phi, h->m, h->id, h->minidx, D.off, D.n, (uint8_t*)dev[0], (double*)dev[1],
+                            (double*)dev[2], (long long*)dev[3], nullptr, h->ls);
+        h->launches += 1;
+    }
+    if (mask & (FSL_F_RHO | FSL_F_U | FSL_F_PDF)) {
+        switch (h->precision) {
+        case FSL_P_FP64: launch_export_pdf<double>(h->f[h->cur], h->stride, D.off, D.n, (double*)dev[6], (double*)dev[4], (double*)dev[5], h->ls); break;
+        case FSL_P_FP32: launch_export_pdf<float>(h->f[h->cur], h->stride, D.off, D.n, (double*)dev[6], (double*)dev[4], (double*)dev[5], h->ls); break;
+        case FSL_P_F16S: launch_export_pdf<__half>(h->f[h->cur], h->stride, D.off, D.n, (double*)dev[6], (double*)dev[4], (double*)dev[5], h->ls); break;
+        default: launch_export_pdf<__nv_bfloat16>(h->f[h->cur], h->stride, D.off, D.n, (double*)dev[6], (double*)dev[4], (double*)dev[5], h->ls); break;
+        }
+        h->launches += 1;
+    }
+    CK(h, cudaGetLastError());
+    if (!on_device) {
+        k = 0;
+        for (int bit = 0; bit < 7; ++bit) {
+            if (!(mask & (1u << bit))) continue;
+            CK(h, cudaMemcpyAsync(dst[k], dev[bit], sizes[bit], cudaMemcpyDeviceToHost, h->ls));
+            ++k;
+        }
+    }
+    CK(h, cudaStreamSynchronize(h->ls));
+    for (void* p : tmp) cudaFree(p);
+    join_out(h);
+    return latch(h);
+}
+
+fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts) {
+    if (!h || d < 0 || d >= h->ndom || !counts) return fail(h, FSL_ERR_ARG, "bad argument");
+    join_in(h);
+    const Dom& D = h->hdoms[d];
+    CK(h, cudaMemsetAsync(h->counts, 0, 64, h->ls));
+    launch_export_cells(h->flag, h->phi, h->m, h->id, h->minidx, D.off, D.n, nullptr, nullptr, nullptr, nullptr,
+                        h->counts, h->ls);
+    h->launches += 1;
+    long long c[8];
+    CK(h, cudaMemcpyAsync(c, h->counts, 64, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaStreamSynchronize(h->ls));
+    for (int k = 0; k < 5; ++k) counts[k] = c[k];
+    join_out(h);
+    return latch(h);
+}
+
+fsl_status fsl_destroy(fsl_domain* h) {
+    if (!h) return FSL_ERR_ARG;
+    if (h->ls) cudaStreamSynchronize(h->ls);
+    for (int k = 0; k < 2; ++k)
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->ls) cudaStreamDestroy(h->ls);
+    delete h;
+    return FSL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,471 @@
+// fsl_core.cu -- precision-independent step kernels of the GB300 FSLBM
+// library (conversion phases A, C, D; connected-component labelling of the
+// bubbles; bubble-table rebuild; exports) and the FP64 instantiation of the
+// per-precision kernels.  Compiled without FMA contraction (-fmad=false) so
+// that every FP64 operation rounds where it is written, as in the oracle.
+//
+// Method: Anderl et al., arXiv:1604.01632, Sec. 2.2 (cell conversion, closed
+// interface layer), Sec. 2.3 (bubble volume per step, Eq. 13), Sec. 2.3.1
+// (merge: V* and V add), Sec. 2.3.2 (split: flood-fill colouring, daughters
+// keep the old pressure).  The paper's serial flood fill and its colour
+// unification across processes (Sec. 2.4.1) become one lock-free union-find
+// over the whole GPU lattice whose roots are the minimum cell index of each
+// component.
+#include <cuda_runtime.h>
+#include <limits.h>
+
+#include "fsl_device.cuh"
+#include "fsl_internal.h"
+
+namespace fsl {
+
+// 3x3x3 cube around a cell, bit k = (dx+1) + 3 (dy+1) + 9 (dz+1); bit 13 is the
+// centre.  c_adj18[k] = cells of the cube that are face or edge neighbours of
+// cell k (built on the host at load time).
+__constant__ unsigned c_adj18[27];
+__constant__ unsigned c_mask18;   // the 18 face/edge neighbours of the centre
+
+FSL_INSTANTIATE_FORM(double)
+
+// Sum v over the warp into base[key] with one atomic when every lane has the
+// same key; key < 0 contributes nothing.  Every lane of the warp must call.
+__device__ inline void warp_add(long long* base, int key, long long v) {
+    const unsigned full = 0xffffffffu;
+    const int k0 = __shfl_sync(full, key, 0);
+    if (__all_sync(full, key == k0)) {
+        if (k0 < 0) return;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd((unsigned long long*)&base[k0], (unsigned long long)v);
+    } else if (key >= 0 && v != 0) {
+        atomicAdd((unsigned long long*)&base[key], (unsigned long long)v);
+    }
+}
+
+// ------------------------------------------------------ conversion phases
+
+// C1 (phase A): filled interface cells claim their gas neighbours (NEWG) and
+// cancel emptied marks next to them.  Resets the per-step counters.
+__global__ void __launch_bounds__(FSL_BLOCK) k_convert_a(StepArgs A) {
+    if (blockIdx.x == 0) {
+        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
+            if (A.nif[d] > 0) A.pool[d] = 0;
+            A.nif[d] = 0;
+        }
+        if (threadIdx.x == 0) *A.trig = 0;
+    }
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const uint8_t t = A.flag[g];
+    const uint8_t mk = A.mark[g];
+    const bool gas = (t == GAS);
+    const bool emp = (t == IFC && mk == MK_EMPTIED);
+    if (!gas && !emp) return;
+    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+    const Cell c = make_cell(D, g);
+    bool hit = false;
+    for (int a = 1; a < 19 && !hit; ++a) {
+        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+        if (A.flag[z] == IFC && A.mark[z] == MK_FILLED) hit = true;
+    }
+    if (gas) {
+        const uint8_t nm = hit ? MK_NEWG : MK_NONE;
+        if (nm != mk) A.mark[g] = nm;
+    } else if (hit) {
+        A.mark[g] = MK_NONE;
+    }
+}
+
+// Local test that removing the filled cell at the centre of the cube cannot
+// split its bubble: the gas/interface cells among its 18 neighbours must stay
+// connected inside the cube (18-connectivity) without the centre.
+__device__ inline bool removal_is_local(unsigned fg) {
+    const unsigned targets = fg & c_mask18;
+    if (targets == 0) return true;
+    unsigned reach = targets & (~targets + 1u);   // lowest target
+    for (int it = 0; it < 27; ++it) {
+        unsigned grow = reach;
+        unsigned r = reach;
+        while (r) {
+            const int k = __ffs(r) - 1;
+            r &= r - 1;
+            grow |= c_adj18[k];
+        }
+        grow &= fg;
+        if (grow == reach) break;
+        reach = grow;
+    }
+    return (targets & ~reach) == 0;
+}
+
+// C3: excess mass of converted cells (filled: m - rho, emptied: m) split
+// equally among neighbours that are interface after conversion, else pooled;
+// count of interface cells; merge / split triggers.
+__global__ void __launch_bounds__(FSL_BLOCK) k_convert_c(StepArgs A) {
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const int d = A.blk_dom[blockIdx.x];
+    const uint8_t t = A.flag[g];
+    const uint8_t mk = A.mark[g];
+    const uint8_t nt = new_type(t, mk);
+    warp_add(A.nif, nt == IFC ? d : -1, 1);
+    const bool conv = (t == IFC && (mk == MK_FILLED || mk == MK_EMPTIED));
+    const bool newl = (t == LIQ && mk == MK_NEWL);
+    if (!conv && !newl) return;
+    const Dom& D = A.doms[d];
+    const Cell c = make_cell(D, g);
+    if (conv) {
+        const double mex = (mk == MK_FILLED) ? A.m[g] - A.rhoi[g] : A.m[g];
+        int k = 0;
+        for (int a = 1; a < 19; ++a) {
+            const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+            if (new_type(A.flag[z], A.mark[z]) == IFC) ++k;
+        }
+        if (k > 0) A.exs[g] = mex / (double)k;
+        else atomicAdd((unsigned long long*)&A.pool[d], (unsigned long long)__double2ll_rn(mex * 1099511627776.0));
+        if (mk == MK_FILLED) {
+            unsigned fgm = 0;
+            bool near_other = false;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (dx == 0 && dy == 0 && dz == 0) continue;
+                        const long long z = c.at(dx, dy, dz);
+                        const uint8_t tz = A.flag[z], mz = A.mark[z];
+                        const uint8_t ntz = new_type(tz, mz);
+                        if (ntz == GAS || ntz == IFC) fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+                        if (tz == IFC && (mz == MK_FILLED || mz == MK_CFILLED)) near_other = true;
+                    }
+            if (near_other || !removal_is_local(fgm)) atomicExch(A.trig, 1);
+        }
+        A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
+        return;
+    }
+    // new interface cell from liquid: a neighbour of another bubble merges
+    const int b = A.id[g];
+    for (int a = 1; a < 19; ++a) {
+        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+        const uint8_t ntz = new_type(A.flag[z], A.mark[z]);
+        if ((ntz == GAS || ntz == IFC) && A.id[z] != b) {
+            atomicExch(A.trig, 1);
+            break;
+        }
+    }
+}
+
+// C4: receivers pull the excess shares in direction order and the pool share,
+// phi = m / rho (Eq. 9), final cell types, incremental bubble volumes (fixed
+// point, so equal to the recomputed sum), reservoir drain.
+__global__ void __launch_bounds__(FSL_BLOCK) k_convert_d(StepArgs A) {
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const int d = A.blk_dom[blockIdx.x];
+    const uint8_t t = A.flag[g];
+    const uint8_t mk = A.mark[g];
+    const uint8_t nt = new_type(t, mk);
+    int key = -1;
+    long long dv = 0;
+    int ckey = -1;
+    long long dc = 0;
+    if (nt == IFC) {
+        const Dom& D = A.doms[d];
+        const Cell c = make_cell(D, g);
+        double s = A.m[g];
+        for (int a = 1; a < 19; ++a) {
+            const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+            const uint8_t mz = A.mark[z];
+            if (mz == MK_CFILLED || mz == MK_CEMPTIED) s = s + A.exs[z];
+        }
+        const long long nI = A.nif[d];
+        if (nI > 0) {
+            const double share = ((double)A.pool[d] * 9.094947017729282379150390625e-13) / (double)nI;
+            s = s + share;
+        }
+        const double phn = s / A.rhoi[g];
+        const long long told = volume_term(t, A.phi[g]);
+        A.m[g] = s;
+        A.phi[g] = phn;
+        if (t != IFC) A.flag[g] = IFC;
+        key = A.id[g];
+        dv = volume_term(IFC, phn) - told;
+        if (t == LIQ) { ckey = key; dc = 1; }
+        if (D.seed >= 0 && g - D.off == D.seed && key >= 0)
+            atomicAdd((unsigned long long*)&A.vxfx[key], (unsigned long long)(-D.rate_fx));
+    } else if (t == IFC && mk == MK_CFILLED) {
+        key = A.id[g];
+        dv = -volume_term(IFC, A.phi[g]);
+        ckey = key;
+        dc = -1;
+        A.flag[g] = LIQ;
+        A.phi[g] = 1.0;
+        A.id[g] = -1;
+    } else if (t == IFC && mk == MK_CEMPTIED) {
+        const Dom& D = A.doms[d];
+        key = A.id[g];
+        dv = FSL_VOL_ONE - volume_term(IFC, A.phi[g]);
+        A.flag[g] = GAS;
+        A.phi[g] = 0.0;
+        A.m[g] = 0.0;
+        if (D.seed >= 0 && g - D.off == D.seed && key >= 0)
+            atomicAdd((unsigned long long*)&A.vxfx[key], (unsigned long long)(-D.rate_fx));
+    } else if (t == GAS) {
+        const Dom& D = A.doms[d];
+        if (D.seed >= 0 && g - D.off == D.seed && A.id[g] >= 0)
+            atomicAdd((unsigned long long*)&A.vxfx[A.id[g]], (unsigned long long)(-D.rate_fx));
+    }
+    warp_add(A.vfx, dv != 0 ? key : -1, dv);
+    warp_add(A.ncells, ckey, dc);
+}
+
+// --------------------------------------------- connected-component labelling
+
+__device__ inline bool is_fg(uint8_t t) { return t == GAS || t == IFC; }
+
+__device__ inline int find_root(const int* L, int a, int cap, bool& ok) {
+    for (int it = 0; it < cap; ++it) {
+        const int p = L[a];
+        if (p == a) return a;
+        a = p;
+    }
+    ok = false;
+    return a;
+}
+
+// Lock-free union: always hook the larger root under the smaller one, so the
+// final root of every component is its minimum cell index.
+__device__ inline bool unite(int* L, int a, int b, int cap) {
+    bool ok = true;
+    for (int it = 0; it < cap && ok; ++it) {
+        a = find_root(L, a, cap, ok);
+        b = find_root(L, b, cap, ok);
+        if (!ok) return false;
+        if (a == b) return true;
+        if (a < b) { const int tt = a; a = b; b = tt; }
+        const int old = atomicMin(&L[a], b);
+        if (old == a) return true;
+        a = old;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_init(StepArgs A, CclArgs K) {
+    if (!K.initial && *A.trig == 0) return;
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    K.lab[g] = is_fg(A.flag[g]) ? (int)g : -1;
+    const long long nth = (long long)gridDim.x * FSL_BLOCK;
+    for (long long h = g; h < K.hcap; h += nth) {
+        K.hkeys[h] = ~0ull;
+        K.hvals[h] = 0;
+    }
+    for (long long s = g; s < K.nslots_total; s += nth) {
+        K.nvfx[s] = 0; K.nvxfx[s] = 0; K.nvsfx[s] = 0; K.nncells[s] = 0; K.nconstp[s] = 0;
+        K.croot[s] = -1;
+        K.vtot[s] = 0;
+        K.minc[s] = INT_MAX;
+    }
+    for (long long dd = g; dd < A.ndom; dd += nth) K.nslot[dd] = 0;
+}
+
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_hook(StepArgs A, CclArgs K) {
+    if (!K.initial && *A.trig == 0) return;
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    if (!is_fg(A.flag[g])) return;
+    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+    const Cell c = make_cell(D, g);
+    // the nine directions 1, 3, ..., 17 cover each neighbour pair once
+    for (int a = 1; a < 19; a += 2) {
+        const long long h = c.at(c_cx[a], c_cy[a], c_cz[a]);
+        if (is_fg(A.flag[h])) {
+            if (!unite(K.lab, (int)g, (int)h, K.max_iter)) {
+                set_status(A.status, ST_CCL);
+                return;
+            }
+        }
+    }
+}
+
+// Compress every cell onto its root; roots take a new bubble-table slot.
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_compress(StepArgs A, CclArgs K) {
+    if (!K.initial && *A.trig == 0) return;
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    if (!is_fg(A.flag[g])) return;
+    bool ok = true;
+    const int r = find_root(K.lab, (int)g, K.max_iter, ok);
+    if (!ok) { set_status(A.status, ST_CCL); return; }
+    K.lab[g] = r;
+    if (r == (int)g) {
+        const int d = A.blk_dom[blockIdx.x];
+        const Dom& D = A.doms[d];
+        const int k = atomicAdd(&K.nslot[d], 1);
+        if (k >= D.slot_cap) { set_status(A.status, ST_TABLE_FULL); K.aux[g] = -1; return; }
+        K.aux[g] = D.slot_off + k;
+        K.croot[D.slot_off + k] = r;
+    }
+}
+
+__device__ inline void hash_add(const CclArgs& K, unsigned long long key, long long v, int* status) {
+    unsigned long long h = key * 0x9E3779B97F4A7C15ull;
+    long long pos = (long long)(h >> 20) & (K.hcap - 1);
+    for (long long probe = 0; probe < K.hcap; ++probe) {
+        const unsigned long long prev = atomicCAS(&K.hkeys[pos], ~0ull, key);
+        if (prev == ~0ull || prev == key) {
+            atomicAdd((unsigned long long*)&K.hvals[pos], (unsigned long long)v);
+            return;
+        }
+        pos = (pos + 1) & (K.hcap - 1);
+    }
+    set_status(status, ST_TABLE_FULL);
+}
+
+// New volumes and cell counts per component, overlap volumes V_{c,b} of new
+// component c with old bubble b, new ids.
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_pairs(StepArgs A, CclArgs K) {
+    if (!K.initial && *A.trig == 0) return;
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const uint8_t t = A.flag[g];
+    int c = -1;
+    long long term = 0;
+    if (is_fg(t)) {
+        const int r = K.lab[g];
+        c = K.aux[r];
+        term = volume_term(t, A.phi[g]);
+    }
+    warp_add(K.nvfx, c, term);
+    warp_add(K.nncells, c, c >= 0 ? 1 : 0);
+    if (c < 0) return;
+    if (!K.initial && A.id[g] >= 0) {
+        const int b = A.id[g];
+        const unsigned long long key = ((unsigned long long)(unsigned)c << 32) | (unsigned)b;
+        hash_add(K, key, term, A.status);
+        atomicAdd((unsigned long long*)&K.vtot[b], (unsigned long long)term);
+        atomicMin(&K.minc[b], K.lab[g]);
+        const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+        if (D.seed >= 0 && g - D.off == D.seed) {
+            const long long x = A.vxfx[b];
+            hash_add(K, key, x, A.status);
+            atomicAdd((unsigned long long*)&K.vtot[b], (unsigned long long)x);
+            K.nvxfx[c] = x;
+        }
+    }
+    A.id[g] = c;
+}
+
+// V*_c = sum over b of V*_b V_{c,b} / V_b, V*_b copied when c holds all of b
+// (Secs. 2.3.1, 2.3.2); a component touching a constant-pressure bubble
+// stays constant-pressure.
+__global__ void k_ccl_table(StepArgs A, CclArgs K) {
+    if (K.initial || *A.trig == 0) return;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x; h < K.hcap; h += nth) {
+        const unsigned long long key = K.hkeys[h];
+        if (key == ~0ull) continue;
+        const int c = (int)(key >> 32);
+        const int b = (int)(key & 0xffffffffu);
+        const long long vcb = K.hvals[h];
+        const long long vt = K.vtot[b];
+        const long long vs = A.vsfx[b];
+        long long contrib;
+        if (vt == 0) contrib = (K.croot[c] == K.minc[b]) ? vs : 0;
+        else if (vcb == vt) contrib = vs;
+        else {
+            const double r = (double)vcb / (double)vt;
+            contrib = __double2ll_rn((double)vs * r);
+        }
+        atomicAdd((unsigned long long*)&K.nvsfx[c], (unsigned long long)contrib);
+        if (A.constp[b]) K.nconstp[c] = 1;
+    }
+}
+
+__global__ void k_ccl_install(StepArgs A, CclArgs K, long long* vsfx, int* constp) {
+    if (!K.initial && *A.trig == 0) return;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < K.nslots_total; s += nth) {
+        const int d = K.slot_dom[s];
+        const Dom& D = A.doms[d];
+        const int k = (int)(s - D.slot_off);
+        if (k < K.nslot[d]) {
+            A.vfx[s] = K.nvfx[s];
+            A.vxfx[s] = K.nvxfx[s];
+            vsfx[s] = K.initial ? K.nvfx[s] + K.nvxfx[s] : K.nvsfx[s];
+            A.ncells[s] = K.nncells[s];
+            constp[s] = K.nconstp[s];
+        } else {
+            A.vfx[s] = 0; A.vxfx[s] = 0; vsfx[s] = 0; A.ncells[s] = 0; constp[s] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ exports
+
+__global__ void k_export_minid(const int* id, long long off, int n, int* minidx) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int b = id[off + l];
+    if (b >= 0) atomicMin(&minidx[b], (int)l);
+}
+
+__global__ void k_export_cells(const uint8_t* flag, const double* phi, const double* m, const int* id,
+                               const int* minidx, long long off, int n, uint8_t* oflag, double* ophi, double* om,
+                               long long* oid, long long* counts) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const long long g = off + l;
+    if (oflag) oflag[l] = flag[g];
+    if (ophi) ophi[l] = phi[g];
+    if (om) om[l] = m[g];
+    if (oid) {
+        const int b = id[g];
+        oid[l] = b >= 0 ? (long long)minidx[b] : -1;
+    }
+    if (counts) atomicAdd((unsigned long long*)&counts[flag[g] < 5 ? flag[g] : 4], 1ull);
+}
+
+// ------------------------------------------------------------ host launches
+
+void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_a<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
+void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_c<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
+void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_d<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
+
+int launch_ccl(const StepArgs& A, const CclArgs& K, long long nb, long long* vsfx, int* constp, cudaStream_t s) {
+    k_ccl_init<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
+    k_ccl_hook<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
+    k_ccl_compress<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
+    k_ccl_pairs<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
+    const unsigned tb = (unsigned)((K.hcap + 255) / 256);
+    k_ccl_table<<<tb > 0 ? tb : 1, 256, 0, s>>>(A, K);
+    const unsigned ib = (unsigned)((K.nslots_total + 255) / 256);
+    k_ccl_install<<<ib > 0 ? ib : 1, 256, 0, s>>>(A, K, vsfx, constp);
+    return 6;
+}
+
+void launch_export_minid(const int* id, long long off, int n, int* minidx, cudaStream_t s) {
+    k_export_minid<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(id, off, n, minidx);
+}
+
+void launch_export_cells(const uint8_t* flag, const double* phi, const double* m, const int* id, const int* minidx,
+                         long long off, int n, uint8_t* oflag, double* ophi, double* om, long long* oid,
+                         long long* counts, cudaStream_t s) {
+    k_export_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flag, phi, m, id, minidx, off, n, oflag, ophi, om,
+                                                              oid, counts);
+}
+
+cudaError_t upload_tables() {
+    unsigned adj[27];
+    unsigned m18 = 0;
+    for (int k = 0; k < 27; ++k) {
+        const int kx = k % 3 - 1, ky = (k / 3) % 3 - 1, kz = k / 9 - 1;
+        const int dk = (kx != 0) + (ky != 0) + (kz != 0);
+        if (dk >= 1 && dk <= 2) m18 |= 1u << k;
+        unsigned a = 0;
+        for (int j = 0; j < 27; ++j) {
+            const int jx = j % 3 - 1, jy = (j / 3) % 3 - 1, jz = j / 9 - 1;
+            const int ax = jx - kx, ay = jy - ky, az = jz - kz;
+            const int dist = (ax != 0) + (ay != 0) + (az != 0);
+            if (ax < -1 || ax > 1 || ay < -1 || ay > 1 || az < -1 || az > 1) continue;
+            if (dist >= 1 && dist <= 2) a |= 1u << j;
+        }
+        adj[k] = a & ~(1u << 13);   // never walk through the removed centre
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_adj18, adj, sizeof(adj));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_mask18, &m18, sizeof(m18));
+}
+
+}  // namespace fsl

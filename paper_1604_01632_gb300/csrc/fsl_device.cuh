@@ -1,0 +1,586 @@
+// fsl_device.cuh -- device-side definitions of the GB300 FSLBM library:
+// lattice constants, cell/mark codes, per-domain descriptors, PDF storage
+// forms and the templated per-cell kernels (stream-collide and the second
+// conversion phase) that exist once per storage precision.
+//
+// Method: Anderl et al., arXiv:1604.01632.  Equation numbers count the
+// paper's displayed equations in order (Eq. 3 equilibrium, Eqs. 4-5 moments,
+// Eq. 6 collision, Eq. 7 streaming, Eq. 8 p = rho c_s^2, Eq. 9 m = phi rho,
+// Eq. 10 mass exchange, Eq. 11 reconstruction, Eq. 12 p_gas = p_V + dp,
+// Eq. 13 p_V = p0 V*/V, Eq. 15 dp = 2 sigma kappa).
+//
+// Layout in HBM: every per-cell array is indexed by a global cell number g;
+// domain d owns cells [off_d, off_d + n_d) in x-fastest order, padded to a
+// multiple of FSL_BLOCK cells with obstacle cells that belong to no lattice.
+// PDFs are structure-of-arrays, f[a * stride + g].
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#define FSL_BLOCK 256
+
+namespace fsl {
+
+enum : uint8_t { LIQ = 0, IFC = 1, GAS = 2, OBS = 3, LID = 4 };
+// Conversion marks (paper Sec. 2.2, cell conversion).  K1 writes NONE /
+// FILLED / EMPTIED on interface cells; phase A writes NEWG on gas cells and
+// clears EMPTIED next to FILLED; phase B writes NEWL / NONE on liquid cells;
+// phase C turns FILLED / EMPTIED into CFILLED / CEMPTIED (same meaning).
+enum : uint8_t { MK_NONE = 0, MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 3, MK_NEWL = 4,
+                 MK_CFILLED = 5, MK_CEMPTIED = 6 };
+
+// status codes latched by kernels (same values as fsl_status)
+enum { ST_GEOMETRY = -2, ST_NAN = -4, ST_CCL = -5, ST_TABLE_FULL = -6 };
+
+// Fixed-point scales: bubble volumes 2^-32 cells^3, pooled mass 2^-40.
+#define FSL_VOL_ONE 4294967296LL
+
+struct Dom {
+    int nx, ny, nz, n;          // lattice dims, n = nx*ny*nz
+    long long off;              // first global cell
+    int slot_off, slot_cap;     // bubble-table slot range
+    int seed;                   // reservoir seed cell (local index), -1 none
+    int normal_rule;
+    long long rate_fx;          // reservoir drain per step, fixed point
+    double omp, omm;            // omega+ = 1/tau, omega- (TRT) or omega+ (BGK)
+    double sigma2;              // 2 sigma
+    double g[3];                // gravity
+    double eps;                 // conversion threshold
+    double lid[3];              // lid velocity
+};
+
+// Everything a step kernel needs, passed by value.
+struct StepArgs {
+    const Dom* doms;
+    const int* blk_dom;         // block -> domain
+    long long stride;           // cells in the padded global lattice
+    const void* fsrc;           // PDFs after the previous step (post-collision)
+    void* fdst;                 // PDFs written by this step
+    uint8_t* flag;
+    uint8_t* mark;
+    double* m;                  // interface mass
+    double* phi;                // fill level
+    double* rhoi;               // density of interface cells at their last collision
+    double* exs;                // excess-mass share of converted cells
+    int* id;                    // bubble slot of gas/interface cells, -1 elsewhere
+    long long* vfx;             // bubble volume of the cells (slot)
+    long long* vxfx;            // bubble extra volume (slot)
+    const long long* vsfx;      // bubble V* (slot)
+    long long* ncells;          // bubble cell count (slot)
+    const int* constp;          // bubble constant-pressure flag (slot)
+    long long* pool;            // per-domain pooled excess mass, fixed point 2^-40
+    long long* nif;             // per-domain interface count after conversion
+    int* trig;                  // merge/split trigger (any domain)
+    int* status;
+    int ndom;
+};
+
+// D3Q19 velocities (one copy per translation unit)
+static __constant__ int c_cx[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static __constant__ int c_cy[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static __constant__ int c_cz[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+__host__ __device__ inline int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+__host__ __device__ inline double weight(int a) {
+    return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+__device__ inline void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// ------------------------------------------------------------ cell geometry
+
+// Coordinates of a cell and wrapped neighbour indices inside its domain.
+struct Cell {
+    int x, y, z;
+    int nx, ny, nz;
+    long long off;
+    __device__ inline long long at(int dx, int dy, int dz) const {
+        int xx = x + dx, yy = y + dy, zz = z + dz;
+        xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+        return off + (long long)xx + (long long)nx * ((long long)yy + (long long)ny * zz);
+    }
+    // any offset (used by the 5x5x5 curvature stencil on tiny lattices too)
+    __device__ inline long long at_far(int dx, int dy, int dz) const {
+        int xx = ((x + dx) % nx + nx) % nx;
+        int yy = ((y + dy) % ny + ny) % ny;
+        int zz = ((z + dz) % nz + nz) % nz;
+        return off + (long long)xx + (long long)nx * ((long long)yy + (long long)ny * zz);
+    }
+};
+
+__device__ inline Cell make_cell(const Dom& D, long long g) {
+    Cell c;
+    int l = (int)(g - D.off);
+    c.nx = D.nx; c.ny = D.ny; c.nz = D.nz; c.off = D.off;
+    c.x = l % D.nx;
+    int r = l / D.nx;
+    c.y = r % D.ny;
+    c.z = r / D.ny;
+    return c;
+}
+
+// ------------------------------------------------------------ storage forms
+
+template <typename T> struct Form;
+template <> struct Form<double> {
+    using C = double;
+    __device__ static inline double ld(const double* p, int) { return *p; }
+    __device__ static inline void st(double* p, int, double v) { *p = v; }
+};
+template <> struct Form<float> {
+    using C = float;
+    __device__ static inline float ld(const float* p, int) { return *p; }
+    __device__ static inline void st(float* p, int, float v) { *p = v; }
+};
+// shifted forms store f_a - w_a (rho0 = 1)
+template <> struct Form<__half> {
+    using C = float;
+    __device__ static inline float ld(const __half* p, int a) { return (float)weight(a) + __half2float(*p); }
+    __device__ static inline void st(__half* p, int a, float v) { *p = __float2half_rn(v - (float)weight(a)); }
+};
+template <> struct Form<__nv_bfloat16> {
+    using C = float;
+    __device__ static inline float ld(const __nv_bfloat16* p, int a) {
+        return (float)weight(a) + __bfloat162float(*p);
+    }
+    __device__ static inline void st(__nv_bfloat16* p, int a, float v) {
+        *p = __float2bfloat16_rn(v - (float)weight(a));
+    }
+};
+
+// ---------------------------------------------------------- LBM arithmetic
+// Written operation by operation in the same order as the oracle so that the
+// FP64 path (compiled without FMA contraction) rounds identically.
+
+template <typename C>
+__device__ inline C cdot(int a, C vx, C vy, C vz) {
+    return ((C)c_cx[a] * vx + (C)c_cy[a] * vy) + (C)c_cz[a] * vz;
+}
+
+// Moments (Eqs. 4-5).
+template <typename C>
+__device__ inline void moments(const C* f, C& rho, C& jx, C& jy, C& jz) {
+    C r = f[0];
+#pragma unroll
+    for (int a = 1; a < 19; ++a) r = r + f[a];
+    rho = r;
+    jx = f[1] - f[2] + f[7] - f[8] + f[9] - f[10] + f[11] - f[12] + f[13] - f[14];
+    jy = f[3] - f[4] + f[7] - f[8] - f[9] + f[10] + f[15] - f[16] + f[17] - f[18];
+    jz = f[5] - f[6] + f[11] - f[12] - f[13] + f[14] + f[15] - f[16] - f[17] + f[18];
+}
+
+// Equilibrium (Eq. 3), symmetric part +/- antisymmetric part per pair.
+template <typename C>
+__device__ inline void feq_all(C rho, C ux, C uy, C uz, C* out) {
+    C usq = ux * ux + uy * uy + uz * uz;
+    out[0] = ((C)weight(0) * rho) * ((C)1 - (C)1.5 * usq);
+#pragma unroll
+    for (int a = 1; a < 19; a += 2) {
+        C cu = cdot<C>(a, ux, uy, uz);
+        C wr = (C)weight(a) * rho;
+        C fp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * usq);
+        C fm = wr * ((C)3 * cu);
+        out[a] = fp + fm;
+        out[a + 1] = fp - fm;
+    }
+}
+
+// Two-relaxation-time collision with Guo forcing (Eq. 6); returns rho.
+template <typename C>
+__device__ inline C collide(const C* fin, C* fout, C omp, C omm, C gx, C gy, C gz) {
+    C rho, jx, jy, jz;
+    moments<C>(fin, rho, jx, jy, jz);
+    C Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
+    C ux = (jx + (C)0.5 * Fx) / rho;
+    C uy = (jy + (C)0.5 * Fy) / rho;
+    C uz = (jz + (C)0.5 * Fz) / rho;
+    C usq = ux * ux + uy * uy + uz * uz;
+    C uF = ux * Fx + uy * Fy + uz * Fz;
+    C cp = (C)1 - (C)0.5 * omp, cm = (C)1 - (C)0.5 * omm;
+    C feq0 = ((C)weight(0) * rho) * ((C)1 - (C)1.5 * usq);
+    C S0 = (C)weight(0) * ((C)-3 * uF);
+    fout[0] = (fin[0] - omp * (fin[0] - feq0)) + cp * S0;
+#pragma unroll
+    for (int a = 1; a < 19; a += 2) {
+        const int b = a + 1;
+        C w = (C)weight(a);
+        C cu = cdot<C>(a, ux, uy, uz);
+        C cF = cdot<C>(a, Fx, Fy, Fz);
+        C wr = w * rho;
+        C feqp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * usq);
+        C feqm = wr * ((C)3 * cu);
+        C fp = (C)0.5 * (fin[a] + fin[b]);
+        C fm = (C)0.5 * (fin[a] - fin[b]);
+        C Sp = w * (((C)9 * cu) * cF - (C)3 * uF);
+        C Sm = w * ((C)3 * cF);
+        C A = omp * (fp - feqp);
+        C B = omm * (fm - feqm);
+        C sp = cp * Sp, sm = cm * Sm;
+        fout[a] = (((fin[a] - A) - B) + sp) + sm;
+        fout[b] = (((fin[b] - A) + B) + sp) - sm;
+    }
+    return rho;
+}
+
+// --------------------------------------------------------- free surface
+
+__device__ inline double phi_stencil(const uint8_t* flag, const double* phi, long long j) {
+    uint8_t t = flag[j];
+    if (t == LIQ || t == OBS || t == LID) return 1.0;
+    if (t == GAS) return 0.0;
+    double v = phi[j];
+    return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+}
+
+// Parker-Youngs gradient of the fill level around (cx+ox, cy+oy, cz+oz):
+// central differences over the 3x3 cross-section, weights 4 / 2 / 1.
+template <typename C>
+__device__ inline void py_gradient(const Cell& c, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
+                                   C& gx, C& gy, C& gz) {
+    gx = (C)0; gy = (C)0; gz = (C)0;
+    for (int b = -1; b <= 1; ++b) {
+        for (int a = -1; a <= 1; ++a) {
+            C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
+            C px = (C)phi_stencil(flag, phi, c.at_far(ox + 1, oy + a, oz + b));
+            C mx = (C)phi_stencil(flag, phi, c.at_far(ox - 1, oy + a, oz + b));
+            gx = gx + W * (px - mx);
+            C py = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy + 1, oz + b));
+            C my = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy - 1, oz + b));
+            gy = gy + W * (py - my);
+            C pz = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy + b, oz + 1));
+            C mz = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy + b, oz - 1));
+            gz = gz + W * (pz - mz);
+        }
+    }
+}
+
+template <typename C>
+__device__ inline void unit_normal(const Cell& c, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
+                                   C& nx, C& ny, C& nz) {
+    C gx, gy, gz;
+    py_gradient<C>(c, ox, oy, oz, flag, phi, gx, gy, gz);
+    C q = gx * gx + gy * gy + gz * gz;
+    if (q > (C)0) {
+        C len = sqrt(q);
+        nx = -(gx / len); ny = -(gy / len); nz = -(gz / len);
+    } else {
+        nx = (C)0; ny = (C)0; nz = (C)0;
+    }
+}
+
+// kappa = 1/2 div(n_hat), central differences (Eq. 15).
+template <typename C>
+__device__ inline C curvature(const Cell& c, const uint8_t* flag, const double* phi) {
+    C px, py, pz, mx, my, mz;
+    unit_normal<C>(c, 1, 0, 0, flag, phi, px, py, pz);
+    unit_normal<C>(c, -1, 0, 0, flag, phi, mx, my, mz);
+    C dX = px - mx;
+    unit_normal<C>(c, 0, 1, 0, flag, phi, px, py, pz);
+    unit_normal<C>(c, 0, -1, 0, flag, phi, mx, my, mz);
+    C dY = py - my;
+    unit_normal<C>(c, 0, 0, 1, flag, phi, px, py, pz);
+    unit_normal<C>(c, 0, 0, -1, flag, phi, mx, my, mz);
+    C dZ = pz - mz;
+    return (C)0.25 * ((dX + dY) + dZ);
+}
+
+// Ideal-gas bubble pressure (Eq. 13), p0 = rho0 c_s^2 = 1/3 (Eq. 14).
+__device__ inline double bubble_pressure(long long vfx, long long vxfx, long long vsfx, int constp) {
+    const double p0 = 1.0 / 3.0;
+    if (constp) return p0;
+    double V = (double)(vfx + vxfx) * 2.3283064365386962890625e-10;
+    if (V <= 1e-3) return p0;
+    double Vs = (double)vsfx * 2.3283064365386962890625e-10;
+    return (Vs / V) * p0;
+}
+
+__device__ inline long long volume_term(uint8_t t, double phi) {
+    if (t == GAS) return FSL_VOL_ONE;
+    if (t == IFC) {
+        double c = phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);
+        return __double2ll_rn((1.0 - c) * 4294967296.0);
+    }
+    return 0;
+}
+
+__device__ inline uint8_t new_type(uint8_t t, uint8_t mk) {
+    if (t == IFC) {
+        if (mk == MK_FILLED || mk == MK_CFILLED) return LIQ;
+        if (mk == MK_EMPTIED || mk == MK_CEMPTIED) return GAS;
+        return IFC;
+    }
+    if (t == GAS && mk == MK_NEWG) return IFC;
+    if (t == LIQ && mk == MK_NEWL) return IFC;
+    return t;
+}
+
+// ================================================================ kernels
+
+// K1: stream with bounce-back (Eq. 7), mass exchange (Eq. 10) and free-
+// surface reconstruction (Eqs. 11-15) on interface cells, collision (Eq. 6),
+// marks for filled / emptied interface cells.  One thread per cell.
+template <typename T>
+__global__ void __launch_bounds__(FSL_BLOCK) k_stream_collide(StepArgs A) {
+    using C = typename Form<T>::C;
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const uint8_t t = A.flag[g];
+    if (t != LIQ && t != IFC) return;
+    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+    const Cell c = make_cell(D, g);
+    const long long S = A.stride;
+    const T* src = (const T*)A.fsrc;
+    T* dst = (T*)A.fdst;
+
+    C fin[19];
+    fin[0] = Form<T>::ld(src + g, 0);
+    if (t == LIQ) {
+#pragma unroll
+        for (int a = 1; a < 19; ++a) {
+            const int ab = opp(a);
+            const long long y = c.at(-c_cx[a], -c_cy[a], -c_cz[a]);
+            const uint8_t ty = A.flag[y];
+            if (ty == OBS) {
+                fin[a] = Form<T>::ld(src + (long long)ab * S + g, ab);
+            } else if (ty == LID) {
+                C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
+                fin[a] = Form<T>::ld(src + (long long)ab * S + g, ab) + ((C)6 * (C)weight(a)) * cuw;
+            } else {
+                if (ty == GAS) set_status(A.status, ST_GEOMETRY);
+                fin[a] = Form<T>::ld(src + (long long)a * S + y, a);
+            }
+        }
+        C fout[19];
+        C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+        if (!(rho == rho)) set_status(A.status, ST_NAN);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
+        return;
+    }
+
+    // interface cell
+    C fs[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) fs[a] = Form<T>::ld(src + (long long)a * S + g, a);
+    C rs, jsx, jsy, jsz;
+    moments<C>(fs, rs, jsx, jsy, jsz);
+    C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
+    C kappa = curvature<C>(c, A.flag, A.phi);
+    const int b = A.id[g];
+    double pv = b >= 0 ? bubble_pressure(A.vfx[b], A.vxfx[b], A.vsfx[b], A.constp[b]) : 1.0 / 3.0;
+    C pg = (C)pv + (C)D.sigma2 * kappa;
+    C rg = (C)3 * pg;
+    C fg[19];
+    feq_all<C>(rg, ugx, ugy, ugz, fg);
+    C gx, gy, gz;
+    py_gradient<C>(c, 0, 0, 0, A.flag, A.phi, gx, gy, gz);
+
+    const double phx = A.phi[g];
+    double dm = 0.0;
+#pragma unroll
+    for (int a = 1; a < 19; ++a) {
+        const int ab = opp(a);
+        const long long y = c.at(-c_cx[a], -c_cy[a], -c_cz[a]);
+        const uint8_t ty = A.flag[y];
+        if (ty == OBS) {
+            fin[a] = fs[ab];
+        } else if (ty == LID) {
+            C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
+            fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
+        } else if (ty == GAS) {
+            fin[a] = (fg[a] + fg[ab]) - fs[ab];
+        } else {
+            // the PDF streaming in from y = x - c_a; it is also f*_a(y), the
+            // f*_{abar}(x + c_abar) of the mass balance over link abar
+            C fy = Form<T>::ld(src + (long long)a * S + y, a);
+            fin[a] = fy;
+            if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
+        }
+    }
+    // mass exchange over the 18 links, in direction order (Eq. 10)
+#pragma unroll
+    for (int a = 1; a < 19; ++a) {
+        const int ab = opp(a);
+        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+        const uint8_t tz = A.flag[z];
+        if (tz == LIQ || tz == IFC) {
+            double fz = (double)Form<T>::ld(src + (long long)ab * S + z, ab);
+            double ex = fz - (double)fs[a];
+            if (tz == LIQ) dm = dm + ex;
+            else dm = dm + (0.5 * (phx + A.phi[z])) * ex;
+        }
+    }
+    const double mnew = A.m[g] + dm;
+    C fout[19];
+    C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+    if (!(rho == rho)) set_status(A.status, ST_NAN);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
+    const double r = (double)rho;
+    A.m[g] = mnew;
+    A.rhoi[g] = r;
+    uint8_t mk = MK_NONE;
+    if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
+    else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
+    A.mark[g] = mk;
+}
+
+// C2 (conversion phase B): remaining emptied cells turn their liquid
+// neighbours into interface (bubble of the first emptied neighbour in
+// direction order, m = rho); new interface cells from gas get f = f_eq of the
+// mean density and velocity of their liquid / non-emptied interface
+// neighbours, m = 0.  Stale marks of liquid cells are cleared.
+template <typename T>
+__global__ void __launch_bounds__(FSL_BLOCK) k_convert_b(StepArgs A) {
+    using C = typename Form<T>::C;
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const uint8_t t = A.flag[g];
+    if (t != LIQ && t != GAS) return;
+    const uint8_t mk = A.mark[g];
+    if (t == GAS && mk != MK_NEWG) return;
+    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+    const Cell c = make_cell(D, g);
+    const long long S = A.stride;
+    T* f = (T*)A.fdst;
+    if (t == LIQ) {
+        int best = -1;
+        for (int a = 1; a < 19 && best < 0; ++a) {
+            const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+            if (A.flag[z] == IFC && A.mark[z] == MK_EMPTIED) best = A.id[z];
+        }
+        if (best >= 0) {
+            double r = (double)Form<T>::ld(f + g, 0);
+            for (int a = 1; a < 19; ++a) r = r + (double)Form<T>::ld(f + (long long)a * S + g, a);
+            A.mark[g] = MK_NEWL;
+            A.id[g] = best;
+            A.m[g] = r;
+            A.rhoi[g] = r;
+        } else if (mk != MK_NONE) {
+            A.mark[g] = MK_NONE;
+        }
+        return;
+    }
+    // new interface cell from gas
+    C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
+    int cnt = 0;
+    for (int a = 1; a < 19; ++a) {
+        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+        const uint8_t tz = A.flag[z];
+        if (tz == LIQ || (tz == IFC && A.mark[z] != MK_EMPTIED)) {
+            C fo[19];
+#pragma unroll
+            for (int q = 0; q < 19; ++q) fo[q] = Form<T>::ld(f + (long long)q * S + z, q);
+            C r, jx, jy, jz;
+            moments<C>(fo, r, jx, jy, jz);
+            sr = sr + r;
+            sux = sux + jx / r;
+            suy = suy + jy / r;
+            suz = suz + jz / r;
+            ++cnt;
+        }
+    }
+    C rbar = sr / (C)cnt;
+    C ux = sux / (C)cnt, uy = suy / (C)cnt, uz = suz / (C)cnt;
+    C fe[19];
+    feq_all<C>(rbar, ux, uy, uz, fe);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) Form<T>::st(f + (long long)q * S + g, q, fe[q]);
+    A.m[g] = 0.0;
+    A.rhoi[g] = (double)rbar;
+}
+
+// Initial state: validate the closed interface layer, f = f_eq(rho, u),
+// m = phi rho on interface cells (Eq. 9).
+template <typename T>
+__global__ void __launch_bounds__(FSL_BLOCK) k_init_state(StepArgs A, int d, const uint8_t* flags_in,
+                                                         const double* fill, const double* rho, const double* u) {
+    using C = typename Form<T>::C;
+    const Dom& D = A.doms[d];
+    const long long l = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    if (l >= D.n) return;
+    const long long g = D.off + l;
+    const long long S = A.stride;
+    const uint8_t t = flags_in[l];
+    const Cell c = make_cell(D, g);
+    if (t > LID) { set_status(A.status, -1); return; }
+    if (t == LIQ) {
+        for (int a = 1; a < 19; ++a) {
+            // neighbours are read from the input (the device flag array is
+            // being written by other threads)
+            long long z = c.at(c_cx[a], c_cy[a], c_cz[a]) - D.off;
+            if (flags_in[z] == GAS) set_status(A.status, ST_GEOMETRY);
+        }
+    }
+    A.flag[g] = t;
+    A.mark[g] = MK_NONE;
+    A.id[g] = -1;
+    A.exs[g] = 0.0;
+    double ph = (t == LIQ) ? 1.0 : (t == IFC ? fill[l] : 0.0);
+    A.phi[g] = ph;
+    T* f = (T*)A.fdst;
+    if (t == LIQ || t == IFC) {
+        C fe[19];
+        feq_all<C>((C)rho[l], (C)u[l], (C)u[D.n + l], (C)u[2 * (long long)D.n + l], fe);
+        for (int a = 0; a < 19; ++a) Form<T>::st(f + (long long)a * S + g, a, fe[a]);
+        A.rhoi[g] = rho[l];
+        A.m[g] = (t == IFC) ? fill[l] * rho[l] : rho[l];
+    } else {
+        for (int a = 0; a < 19; ++a) Form<T>::st(f + (long long)a * S + g, a, (C)weight(a));
+        A.rhoi[g] = 0.0;
+        A.m[g] = 0.0;
+    }
+}
+
+// Export of the PDFs (unshifted, double) and of their density and velocity.
+template <typename T>
+__global__ void k_export_pdf(const T* f, long long S, long long off, int n, double* pdf, double* rho, double* u) {
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const long long g = off + l;
+    double fo[19];
+    for (int a = 0; a < 19; ++a) {
+        fo[a] = (double)Form<T>::ld(f + (long long)a * S + g, a);
+        if (pdf) pdf[(long long)a * n + l] = fo[a];
+    }
+    if (rho || u) {
+        double r, jx, jy, jz;
+        moments<double>(fo, r, jx, jy, jz);
+        if (rho) rho[l] = r;
+        if (u) {
+            u[l] = r != 0.0 ? jx / r : 0.0;
+            u[n + l] = r != 0.0 ? jy / r : 0.0;
+            u[2LL * n + l] = r != 0.0 ? jz / r : 0.0;
+        }
+    }
+}
+
+// Launch helpers instantiated once per storage form.
+template <typename T> void launch_stream_collide(const StepArgs& A, long long nblocks, cudaStream_t s);
+template <typename T> void launch_convert_b(const StepArgs& A, long long nblocks, cudaStream_t s);
+template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
+                                             const double* rho, const double* u, cudaStream_t s);
+template <typename T> void launch_export_pdf(const void* f, long long S, long long off, int n, double* pdf,
+                                             double* rho, double* u, cudaStream_t s);
+
+#define FSL_INSTANTIATE_FORM(T)                                                                              \
+    template <> void launch_stream_collide<T>(const StepArgs& A, long long nb, cudaStream_t s) {             \
+        k_stream_collide<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                          \
+    }                                                                                                        \
+    template <> void launch_convert_b<T>(const StepArgs& A, long long nb, cudaStream_t s) {                  \
+        k_convert_b<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                               \
+    }                                                                                                        \
+    template <> void launch_init_state<T>(const StepArgs& A, int d, int n, const uint8_t* fl,                \
+                                          const double* fill, const double* rho, const double* u,            \
+                                          cudaStream_t s) {                                                  \
+        k_init_state<T><<<(unsigned)((n + FSL_BLOCK - 1) / FSL_BLOCK), FSL_BLOCK, 0, s>>>(A, d, fl, fill,   \
+                                                                                          rho, u);           \
+    }                                                                                                        \
+    template <> void launch_export_pdf<T>(const void* f, long long S, long long off, int n, double* pdf,     \
+                                          double* rho, double* u, cudaStream_t s) {                          \
+        k_export_pdf<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>((const T*)f, S, off, n, pdf, rho, u);   \
+    }
+
+}  // namespace fsl

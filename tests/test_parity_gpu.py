@@ -1,0 +1,156 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.  FP64 storage: cell types and bubble ids bit-identical,
+PDFs, mass and fill level within 1e-12, bubble table V and V* identical in
+fixed point.  Reduced-precision storage: stated tolerances."""
+import numpy as np
+import pytest
+
+from paper_1604_01632_gb300 import scenarios as S
+
+from parity_util import compare_exact, gpu_state, macro, oracle_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsl():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_01632_gb300 import build, fsl as F
+    build.build()
+    return F
+
+
+def _pair(fsl, oracle_mod, sc, precision="fp64"):
+    sim = fsl.Simulation.from_scenarios([sc], precision=precision)
+    o = oracle_mod.Oracle.from_scenario(sc)
+    return sim, o
+
+
+def _run_compare(fsl, oracle_mod, sc, checkpoints, what):
+    sim, o = _pair(fsl, oracle_mod, sc)
+    compare_exact(gpu_state(sim), oracle_state(o), what=f"{what} init")
+    done = 0
+    for k in checkpoints:
+        sim.step(k - done)
+        o.step(k - done)
+        done = k
+        compare_exact(gpu_state(sim), oracle_state(o), what=f"{what} step {k}")
+    sim.sync()
+    assert o.status == 0
+    return sim, o
+
+
+def test_static_bubble_fp64_bitexact(fsl, oracle_mod):
+    """32^3 periodic box, bubble R = 8, sigma = 1e-3, BGK tau = 0.8, 200 steps."""
+    sc = S.static_bubble()
+    _run_compare(fsl, oracle_mod, sc, [1, 2, 3, 50, 200], "static bubble")
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_bubbles_with_conversions(fsl, oracle_mod, seed):
+    """Moving liquid with several bubbles: conversions every step, merges and
+    splits; state compared after every step for the first 10, then sparser."""
+    sc = S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=seed)
+    _run_compare(fsl, oracle_mod, sc, list(range(1, 11)) + [20, 40, 80], f"random bubbles {seed}")
+
+
+def test_thread_breakup_split(fsl, oracle_mod):
+    sc = S.gas_thread(nx=48, ny=20, nz=20, radius=3.0, amp=0.25, wavelength=24, sigma=0.05, steps=0)
+    sim, o = _run_compare(fsl, oracle_mod, sc, [50, 80, 85, 88, 89, 90, 92, 100, 150], "thread breakup")
+    assert len(o.bubbles()) == 2
+
+
+def test_buoyant_merge(fsl, oracle_mod):
+    nx, ny, nz, g = 16, 16, 32, 5e-4
+    shape = (nz, ny, nx)
+    cen = np.array([[8.0, 8.0, 24.5], [8.0, 8.0, 13.5]])
+    fill = S.liquid_fraction(shape, S._spheres_sdf(cen, np.array([4.0, 4.0])))
+    flags = S.classify(fill, obstacle=S._wall_shell(shape, axes=(2,)))
+    x, y, z = S._centres(shape)
+    sc = S._finish("merge", flags, fill, rho=1.0 + 3.0 * g * (nz - 1 - z), collision=S.TRT, sigma=0.002,
+                   gravity=(0.0, 0.0, -g))
+    sim, o = _run_compare(fsl, oracle_mod, sc, [100, 200, 240, 245, 246, 247, 248, 250, 300], "buoyant merge")
+    assert len(o.bubbles()) == 1
+
+
+def test_droplet_in_atmosphere_and_reservoir(fsl, oracle_mod):
+    n, R = 24, 6.0
+    fill = S.liquid_fraction((n, n, n), lambda x, y, z: R - np.sqrt((x - 12) ** 2 + (y - 12) ** 2 + (z - 12) ** 2))
+    sc = S._finish("drop", S.classify(fill), fill, sigma=2e-3, collision=S.TRT, sources=[(0, 0.0, 0.0, 1)])
+    _run_compare(fsl, oracle_mod, sc, [1, 10, 60], "droplet")
+    sc2 = S.static_bubble(n=24, radius=5.0, sigma=2e-3)
+    sc2.sources = [(sc2.linear(12, 12, 12), 100.0, 0.5, 0)]
+    _run_compare(fsl, oracle_mod, sc2, [1, 10, 60], "reservoir")
+
+
+def test_gravity_lid_and_ragged_sizes(fsl, oracle_mod):
+    """Odd domain sizes (not a multiple of the 256-cell block), gravity, a moving lid."""
+    nx, ny, nz = 13, 11, 17
+    shape = (nz, ny, nx)
+    fill = S.liquid_fraction(shape, S._spheres_sdf(np.array([[6.5, 5.5, 7.0]]), np.array([3.2])))
+    obs = np.zeros(shape, bool)
+    obs[0] = True
+    lid = np.zeros(shape, bool)
+    lid[nz - 1] = True
+    flags = S.classify(fill, obstacle=obs, lid=lid)
+    sc = S._finish("lid", flags, fill, collision=S.TRT, sigma=3e-3, gravity=(0.0, 0.0, -2e-5), lid=(0.05, 0.0, 0.0))
+    _run_compare(fsl, oracle_mod, sc, [1, 5, 30, 120], "lid")
+
+
+def test_batched_domains_match_separate_oracles(fsl, oracle_mod):
+    scs = [S.random_bubbles(20, 16, 12, n_bubbles=3, r_min=2.5, r_max=4.0, u_max=0.05, sigma=4e-3, seed=s)
+           for s in range(3)]
+    scs.append(S.static_bubble(n=16, radius=4.0))
+    sim = fsl.Simulation.from_scenarios(scs, precision="fp64")
+    oras = [oracle_mod.Oracle.from_scenario(s) for s in scs]
+    for k in (1, 7, 40):
+        sim.step(k if k == 1 else k - prev)
+        for o in oras:
+            o.step(k if k == 1 else k - prev)
+        prev = k
+        for d, o in enumerate(oras):
+            compare_exact(gpu_state(sim, d), oracle_state(o), what=f"domain {d} step {k}")
+
+
+def test_full_size_gas_thread_sampled(fsl, oracle_mod):
+    """The full 256x64x64 gas-thread lattice (the benchmark workload) for a few
+    steps in FP64: identical to the oracle."""
+    sc = S.gas_thread()
+    _run_compare(fsl, oracle_mod, sc, [1, 3], "gas thread 256x64x64")
+
+
+def test_geometry_error_is_reported(fsl):
+    sc = S.static_bubble(n=16, radius=4.0)
+    bad = sc.flags.copy().reshape(-1)
+    # a liquid cell next to a gas cell breaks the closed interface layer
+    gas = np.nonzero(bad == S.GAS)[0][0]
+    itf = np.nonzero(bad == S.INTERFACE)[0]
+    bad[itf] = S.LIQUID
+    sim = fsl.Simulation([sc.params()], precision="fp64")
+    with pytest.raises(fsl.FslError) as e:
+        sim.init_geometry(0, bad, sc.fill, sc.rho, sc.u)
+    assert e.value.status == -2
+    assert gas >= 0
+
+
+@pytest.mark.parametrize("precision,tol_u,tol_rho,tol_v", [("fp32", 1e-6, 1e-6, 1e-6), ("f16s", 2e-4, 2e-4, 1e-3),
+                                                            ("bf16s", 2e-3, 2e-3, 1e-2)])
+def test_reduced_precision_static_bubble(fsl, oracle_mod, precision, tol_u, tol_rho, tol_v):
+    """FP32 collide with FP32 / FP16-shifted / BF16-shifted storage against the FP64
+    oracle on the static bubble (200 steps): L-infinity errors of rho and u on fluid
+    cells and the relative error of the bubble volume."""
+    sc = S.static_bubble()
+    sim, o = _pair(fsl, oracle_mod, sc, precision)
+    sim.step(200)
+    o.step(200)
+    g, r = gpu_state(sim), oracle_state(o)
+    fl = np.isin(r["flags"], (S.LIQUID, S.INTERFACE)) & np.isin(g["flags"], (S.LIQUID, S.INTERFACE))
+    rg, ug = macro(g["f"][:, fl])
+    rr, ur = macro(r["f"][:, fl])
+    assert np.abs(rg - rr).max() < tol_rho
+    assert np.abs(ug - ur).max() < tol_u
+    assert len(g["bubbles"]) == len(r["bubbles"]) == 1
+    assert abs(g["bubbles"]["volume"][0] / r["bubbles"]["volume"][0] - 1.0) < tol_v
+    assert (g["flags"] == r["flags"]).mean() > 0.999
