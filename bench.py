@@ -1,0 +1,333 @@
+"""Benchmark of one FSLBM step (all sub-steps of the method) on GB300.
+
+Workload (default): the gas-thread breakup lattice, 256x64x64 cells, periodic in
+x with no-slip walls elsewhere, gas cylinder of radius 8 (1 + 0.1 sin(2 pi x /
+64)), TRT (Lambda = 3/16, tau = 0.8), sigma = 5e-3, FP16-shifted PDF storage
+with FP32 collision; seeded synthetic geometry.
+
+One step = stream/bounce-back + mass exchange + reconstruction + collision,
+the conversion phases with excess-mass redistribution, the bubble-volume
+update, and the merge/split labelling when triggered.  Inputs are resident in
+HBM when the timed region starts; the L2 cache (129 MB) is flushed before every
+timed step (the working set of this lattice fits in L2) and only the steps are
+timed, with CUDA events on the stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16s]
+    python bench.py --impl reference      # the FP64 CPU oracle on the host cores
+
+Under torchrun every rank advances its own independent copy of the lattice
+(weak scaling, no collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FSLBM MLUPS & HBM roofline fraction: FP16-store/batched vs plain FP32/FP64"
+UNIT = "MLUPS"
+BYTES = {"fp64": 8, "fp32": 4, "f16s": 2, "bf16s": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "f16s": "f32", "bf16s": "f32"}
+KERNEL = "k_stream_collide"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1604_01632_gb300", "csrc", f) for f in
+                  ("fsl_device.cuh", "fsl_fast.cu", "fsl_core.cu")]
+
+
+def workload(name: str):
+    from paper_1604_01632_gb300 import scenarios as S
+    if name == "gas_thread":
+        return S.gas_thread(), "gas_thread 256x64x64 TRT sigma=5e-3 R=8(1+0.1 sin(2 pi x/64))"
+    if name == "static_bubble":
+        return S.static_bubble(), "static_bubble 32^3 BGK R=8 sigma=1e-3"
+    raise ValueError(name)
+
+
+def algorithmic_bytes(counts, s: int) -> float:
+    """Minimum bytes one stream-collide launch moves: every cell's type byte;
+    19 PDFs read and 19 written per liquid or interface cell; per interface cell
+    its mass (read + write), fill level, density and mark (37 B)."""
+    n_all = float(sum(counts))
+    n_liq, n_if = float(counts[0]), float(counts[1])
+    return n_all * 1.0 + (n_liq + n_if) * 38.0 * s + n_if * 37.0
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(precision: str, wl: str):
+    """DRAM bytes per stream-collide launch from the committed ncu summary, if it
+    was taken on the current kernel source for this precision and workload."""
+    try:
+        rec = json.load(open(PROFILE_TRAFFIC))
+    except Exception:
+        return None
+    ent = rec.get(f"{wl}:{precision}")
+    if not ent or ent.get("kernel_sha") != kernel_sha():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    from paper_1604_01632_gb300 import fsl
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    sc, wl_desc = workload(args.workload)
+    n = sc.n
+    stream = torch.cuda.current_stream()
+
+    def make(precision):
+        return fsl.Simulation.from_scenarios([sc], precision=precision, stream=int(stream.cuda_stream))
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = float(meas_peaks["hbm_gbs"]) if meas_peaks else 6800.0
+
+    def timed_steps(sim, K, W, timing=True):
+        sim.set_timing(timing)
+        for _ in range(W):
+            flush.zero_()
+            sim.step(1)
+        sim.sync()
+        sim.set_timing(timing)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        l0 = sim.launches
+        r0 = sim.labelling_runs
+        c0 = sim.cell_counts(0)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record()
+            sim.step(1)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        sim.sync()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        k1 = sim.stream_collide_ms()
+        launches = sim.launches - l0
+        c1 = sim.cell_counts(0)
+        return ms, k1, launches, (np.asarray(c0) + np.asarray(c1)) / 2.0, sim.labelling_runs - r0
+
+    # headline: the requested precision
+    sim = make(args.precision)
+    clk = Clocks(dev)
+    clk.start()
+    ms, k1_ms, launches, counts, lruns = timed_steps(sim, args.steps, args.warmup)
+    clocks = clk.stop()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n * args.steps * world / (ms_max * 1e-3) / 1e6
+    s = BYTES[args.precision]
+    abytes = algorithmic_bytes(counts, s)
+    k1_avg = k1_ms / args.steps
+    achieved = abytes / (k1_avg * 1e-3) / 1e9
+    traffic = traffic_per_launch(args.precision, args.workload)
+    sim.close()
+
+    variants = {}
+    if not args.no_variants:
+        for prec in ("fp32", "bf16s", "fp64"):
+            if prec == args.precision:
+                continue
+            v = make(prec)
+            vms, vk1, _, vc, _ = timed_steps(v, max(5, args.steps // 2), args.warmup)
+            kk = max(5, args.steps // 2)
+            vb = algorithmic_bytes(vc, BYTES[prec])
+            variants[prec] = {"mlups": round(n * kk / (vms * 1e-3) / 1e6, 1),
+                              "stream_collide_gbs": round(vb / (vk1 / kk * 1e-3) / 1e9, 1),
+                              "stream_collide_frac": round(vb / (vk1 / kk * 1e-3) / 1e9 / peak, 3)}
+            v.close()
+
+    # end to end through the C ABI from host buffers: upload the initial state,
+    # K steps, read back the fields and the bubble table
+    e2e = None
+    if not args.no_e2e:
+        flags = np.ascontiguousarray(sc.flags.reshape(-1))
+        fill = np.ascontiguousarray(sc.fill.reshape(-1))
+        rho = np.ascontiguousarray(sc.rho.reshape(-1))
+        u = np.ascontiguousarray(sc.u.reshape(-1))
+        sim = fsl.Simulation([sc.params()], precision=args.precision, stream=int(stream.cuda_stream))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init_geometry(0, flags, fill, rho, u)
+        sim.step(args.steps)
+        out = sim.fields(0, ("flags", "fill", "id", "rho", "u"))
+        bub = sim.bubbles(0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h2d = flags.nbytes + fill.nbytes + rho.nbytes + u.nbytes
+        d2h = sum(a.nbytes for a in out.values()) + bub.nbytes
+        e2e = {"value": round(n * args.steps * world / dt / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps)}
+        sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(sc, steps=args.cpu_steps)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": wl_desc, "cells": n, "storage": args.precision,
+                       "l2": "flushed (256 MB write) before every timed step; steps timed by CUDA events",
+                       "parallelism": f"replicas x{world}",
+                       "labelling_runs_per_step": round(lruns / args.steps, 3),
+                       "cell_counts_liquid_interface_gas_obstacle": [int(c) for c in counts[:4]]},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": KERNEL, "algorithmic_bytes_per_launch": int(abytes),
+                         "avg_launch_ms": round(k1_avg, 5), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "variants": variants,
+        }
+        print(json.dumps(line))
+
+
+def cpu_baseline(sc, steps: int):
+    """The FP64 oracle as it stands, single-threaded on a host core, on a bounded
+    sample (`steps` steps of the same lattice)."""
+    from oracle import oracle
+    o = oracle.Oracle.from_scenario(sc)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(sc.n * steps / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the full {sc.nx}x{sc.ny}x{sc.nz} lattice ({dt:.1f} s)"}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    sc, wl_desc = workload(args.workload)
+    from oracle import oracle
+    o = oracle.Oracle.from_scenario(sc)
+    steps = max(1, args.steps)
+    o.step(max(0, args.warmup))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    value = sc.n * steps / dt / 1e6
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl_desc, "cells": sc.n, "storage": "fp64"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} timed steps of the full lattice after {args.warmup} untimed"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fsl", choices=["fsl", "reference"])
+    ap.add_argument("--precision", default="f16s", choices=list(BYTES))
+    ap.add_argument("--workload", default="gas_thread")
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    from paper_1604_01632_gb300 import build
+    build.build()
+    run_gpu(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,11 @@ const char* fsl_last_error(const fsl_domain* h);
  * their kernels). */
 int64_t fsl_kernel_launches(const fsl_domain* h);
 
+/* Number of merge/split labelling passes run since initialisation (the pass
+ * runs only in steps whose conversions may have changed a bubble's
+ * connectivity); synchronises.  -1 on error. */
+int64_t fsl_labelling_runs(fsl_domain* h);
+
 /* Device time of the stream-collide kernels of the last fsl_step call, in
  * milliseconds, summed over its steps (0 when timing is off).  Timing is
  * switched on with fsl_set_timing(h, 1); it brackets each stream-collide

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -29,6 +30,8 @@ struct fsl_domain {
     size_t fbytes = 8;            // bytes per stored PDF
     cudaStream_t user = nullptr;  // caller's stream (may be the legacy default)
     cudaStream_t ls = nullptr;    // library stream (capturable)
+    cudaStream_t ls2 = nullptr;   // second stream, used only to capture the labelling body
+    int ifblocks = 1216;          // grid of the interface kernel (8 blocks of 128 per SM)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
     std::vector<Dom> hdoms;
@@ -52,6 +55,8 @@ struct fsl_domain {
     long long *pool = nullptr, *nif = nullptr;
     int* trig = nullptr;
     int* status = nullptr;
+    int *ilist = nullptr, *icount = nullptr, *clist = nullptr, *ccount = nullptr, *anymark = nullptr;
+    long long* icnt = nullptr;
     // labelling scratch
     int *lab = nullptr, *aux = nullptr;
     unsigned long long* hkeys = nullptr;
@@ -62,12 +67,16 @@ struct fsl_domain {
     long long* vtot = nullptr;
     int* minidx = nullptr;
     long long* counts = nullptr;
+    long long* runs = nullptr;
 
     std::vector<bool> inited;
     bool need_initial_ccl = true;
     bool stepped = false;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int graph_kernels = 0;
+    // step graphs: [starting buffer][kind]; kind 0 = two steps, 1 = one step,
+    // 2 = one step with event-record nodes around the stream-collide kernels
+    cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    cudaGraphNode_t rec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int graph_kernels[3] = {0, 0, 0};
     long long launches = 0;
     bool timing = false;
     std::vector<cudaEvent_t> evpool;
@@ -129,6 +138,13 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.trig = h->trig;
     A.status = h->status;
     A.ndom = h->ndom;
+    A.ilist = h->ilist;
+    A.icount = h->icount;
+    A.clist = h->clist;
+    A.ccount = h->ccount;
+    A.anymark = h->anymark;
+    A.icnt = h->icnt;
+    A.cond = 0;
     return A;
 }
 
@@ -150,6 +166,7 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     K.nslot = h->nslot;
     K.slot_dom = h->d_slot_dom;
     K.nslots_total = h->nslots;
+    K.runs = h->runs;
     K.initial = initial;
     // find() walks strictly decreasing indices and every retry of unite()
     // follows a link made by another thread, so both loops end; the caps only
@@ -158,46 +175,55 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     return K;
 }
 
-void launch_k1(fsl_domain* h, const StepArgs& A) {
+void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_stream_collide<double>(A, h->nblocks, h->ls); break;
-    case FSL_P_FP32: launch_stream_collide<float>(A, h->nblocks, h->ls); break;
-    case FSL_P_F16S: launch_stream_collide<__half>(A, h->nblocks, h->ls); break;
-    default: launch_stream_collide<__nv_bfloat16>(A, h->nblocks, h->ls); break;
+    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st); break;
+    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st); break;
+    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st); break;
+    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st); break;
     }
 }
 
-void launch_cb(fsl_domain* h, const StepArgs& A) {
+void launch_cb(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_convert_b<double>(A, h->nblocks, h->ls); break;
-    case FSL_P_FP32: launch_convert_b<float>(A, h->nblocks, h->ls); break;
-    case FSL_P_F16S: launch_convert_b<__half>(A, h->nblocks, h->ls); break;
-    default: launch_convert_b<__nv_bfloat16>(A, h->nblocks, h->ls); break;
+    case FSL_P_FP64: launch_convert_b<double>(A, h->nblocks, st); break;
+    case FSL_P_FP32: launch_convert_b<float>(A, h->nblocks, st); break;
+    case FSL_P_F16S: launch_convert_b<__half>(A, h->nblocks, st); break;
+    default: launch_convert_b<__nv_bfloat16>(A, h->nblocks, st); break;
     }
 }
 
-// One time step from buffer src into 1 - src.  Returns the kernels launched.
-int enqueue_step(fsl_domain* h, int src, bool timed) {
-    StepArgs A = step_args(h, src);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (timed) {
-        while (h->evpool.size() < h->evused + 2) {
-            cudaEvent_t e;
-            cudaEventCreate(&e);
-            h->evpool.push_back(e);
-        }
-        e0 = h->evpool[h->evused++];
-        e1 = h->evpool[h->evused++];
-        cudaEventRecord(e0, h->ls);
-    }
-    launch_k1(h, A);
-    if (timed) cudaEventRecord(e1, h->ls);
+// Stream-collide and the four conversion phases of one step (6 kernels).
+// With e0/e1 the stream-collide pair is bracketed by event records (captured
+// as event-record nodes when the stream is capturing; their nodes go to rec).
+int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e1, cudaGraphNode_t* rec) {
+    auto last_node = [&](int k) {
+        if (!rec) return;
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if (cudaStreamGetCaptureInfo(h->ls, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess && nd == 1)
+            rec[k] = deps[0];
+    };
+    if (e0) { cudaEventRecord(e0, h->ls); last_node(0); }
+    launch_k1(h, A, h->ls);
+    if (e1) { cudaEventRecord(e1, h->ls); last_node(1); }
     launch_convert_a(A, h->nblocks, h->ls);
-    launch_cb(h, A);
+    launch_cb(h, A, h->ls);
     launch_convert_c(A, h->nblocks, h->ls);
     launch_convert_d(A, h->nblocks, h->ls);
-    int k = 5 + launch_ccl(A, ccl_args(h, 0), h->nblocks, h->vsfx, h->constp, h->ls);
-    return k;
+    return 6;
+}
+
+std::pair<cudaEvent_t, cudaEvent_t> next_events(fsl_domain* h) {
+    while (h->evpool.size() < h->evused + 2) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->evpool.push_back(e);
+    }
+    cudaEvent_t a = h->evpool[h->evused++];
+    cudaEvent_t b = h->evpool[h->evused++];
+    return {a, b};
 }
 
 // Order library work after the caller's stream, and the caller after it.
@@ -231,7 +257,81 @@ fsl_status ensure_initial(fsl_domain* h) {
         if (!h->inited[d]) return fail(h, FSL_ERR_ARG, "every domain must be initialised first");
     StepArgs A = step_args(h, h->cur);
     h->launches += launch_ccl(A, ccl_args(h, 1), h->nblocks, h->vsfx, h->constp, h->ls);
+    CK(h, cudaMemsetAsync(h->icount, 0, sizeof(int), h->ls));
+    CK(h, cudaMemsetAsync(h->icnt, 0, 8 * (size_t)h->ndom, h->ls));
+    launch_build_ilist(A, h->nblocks, h->ls);
+    h->launches += 1;
+    CK(h, cudaGetLastError());
     h->need_initial_ccl = false;
+    return FSL_OK;
+}
+
+// One or two steps starting from buffer `start` as one graph.  After each
+// step's conversion kernels a conditional node runs the labelling only when
+// the step set the merge/split trigger (the last conversion kernel sets the
+// condition).  kind 2 brackets the stream-collide kernels with event-record
+// nodes whose events are swapped before every launch.
+fsl_status build_graph(fsl_domain* h, int start, int kind) {
+    const int nsteps = kind == 0 ? 2 : 1;
+    cudaGraph_t G = nullptr;
+    CK(h, cudaGraphCreate(&G, 0));
+    cudaGraphConditionalHandle hc[2];
+    for (int j = 0; j < nsteps; ++j)
+        CK(h, cudaGraphConditionalHandleCreate(&hc[j], G, 0, cudaGraphCondAssignDefault));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (kind == 2) {
+        auto ev = next_events(h);
+        e0 = ev.first;
+        e1 = ev.second;
+    }
+    CK(h, cudaStreamBeginCaptureToGraph(h->ls, G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    int kk = 0;
+    for (int j = 0; j < nsteps; ++j) {
+        StepArgs A = step_args(h, j == 0 ? start : 1 - start);
+        A.cond = hc[j];
+        kk += enqueue_main(h, A, e0, e1, kind == 2 ? h->rec[start] : nullptr);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        CK(h, cudaStreamGetCaptureInfo(h->ls, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = hc[j];
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t cn;
+        CK(h, cudaGraphAddNode(&cn, G, deps, nullptr, nd, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        CK(h, cudaStreamBeginCaptureToGraph(h->ls2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        launch_ccl(A, ccl_args(h, 0), h->nblocks, h->vsfx, h->constp, h->ls2);
+        cudaGraph_t tmp = nullptr;
+        CK(h, cudaStreamEndCapture(h->ls2, &tmp));
+        CK(h, cudaStreamUpdateCaptureDependencies(h->ls, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    }
+    cudaGraph_t out = nullptr;
+    CK(h, cudaStreamEndCapture(h->ls, &out));
+    if (kind == 2 && (!h->rec[start][0] || !h->rec[start][1])) {
+        cudaGraphDestroy(G);
+        return fail(h, FSL_ERR_CUDA, "event-record nodes not found in the captured step");
+    }
+    CK(h, cudaGraphInstantiate(&h->graph[start][kind], G, 0));
+    cudaGraphDestroy(G);
+    h->graph_kernels[kind] = kk;   // the labelling kernels run only on trigger steps
+    if (kind == 2) h->evused -= 2;  // the capture events are placeholders
+    return FSL_OK;
+}
+
+fsl_status launch_graph(fsl_domain* h, int kind) {
+    if (!h->graph[h->cur][kind]) {
+        fsl_status gs = build_graph(h, h->cur, kind);
+        if (gs != FSL_OK) return gs;
+    }
+    if (kind == 2) {
+        auto ev = next_events(h);
+        CK(h, cudaGraphExecEventRecordNodeSetEvent(h->graph[h->cur][2], h->rec[h->cur][0], ev.first));
+        CK(h, cudaGraphExecEventRecordNodeSetEvent(h->graph[h->cur][2], h->rec[h->cur][1], ev.second));
+    }
+    CK(h, cudaGraphLaunch(h->graph[h->cur][kind], h->ls));
+    h->launches += h->graph_kernels[kind];
     return FSL_OK;
 }
 
@@ -292,6 +392,13 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     cudaError_t e = upload_tables();
     if (e != cudaSuccess) { fsl_status st = cuda_fail(h, e, "tables"); delete h; return st; }
     e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ls2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms > 0) h->ifblocks = 8 * sms;
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
     const size_t N = (size_t)h->stride, NS = (size_t)h->nslots;
@@ -317,6 +424,12 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->nif, 8 * n_domains);
     AL(h->trig, sizeof(int));
     AL(h->status, sizeof(int));
+    AL(h->ilist, 4 * N);
+    AL(h->icount, sizeof(int));
+    AL(h->clist, 4 * N);
+    AL(h->ccount, sizeof(int));
+    AL(h->anymark, sizeof(int));
+    AL(h->icnt, 8 * n_domains);
     AL(h->lab, 4 * N);
     AL(h->aux, 4 * N);
     AL(h->hkeys, 8 * (size_t)hc);
@@ -332,6 +445,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->nslot, 4 * n_domains);
     AL(h->minidx, 4 * NS);
     AL(h->counts, 8 * 8);
+    AL(h->runs, 8);
 #undef AL
     if (e != cudaSuccess) {
         fsl_status st = (e == cudaErrorMemoryAllocation) ? FSL_ERR_OOM : FSL_ERR_CUDA;
@@ -355,6 +469,11 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->nif, 0, 8 * n_domains);
     if (e == cudaSuccess) e = cudaMemset(h->trig, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->icount, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->ccount, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->anymark, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->icnt, 0, 8 * n_domains);
+    if (e == cudaSuccess) e = cudaMemset(h->runs, 0, 8);
     if (e == cudaSuccess) e = cudaMemset(h->vfx, 0, 8 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->vxfx, 0, 8 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->vsfx, 0, 8 * NS);
@@ -447,32 +566,21 @@ fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
     if (st != FSL_OK) return st;
     h->stepped = true;
     join_in(h);
+    int64_t k = 0;
     if (h->timing) {
-        for (int64_t k = 0; k < nsteps; ++k) {
-            h->launches += enqueue_step(h, h->cur, true);
+        for (; k < nsteps; ++k) {
+            st = launch_graph(h, 2);
+            if (st != FSL_OK) return st;
             h->cur = 1 - h->cur;
         }
     } else {
-        int64_t k = 0;
-        if (nsteps >= 2) {
-            // two steps (A -> B -> A) per graph, one graph per starting buffer
-            if (!h->graph[h->cur]) {
-                cudaGraph_t gr;
-                CK(h, cudaStreamBeginCapture(h->ls, cudaStreamCaptureModeThreadLocal));
-                int kk = enqueue_step(h, h->cur, false);
-                kk += enqueue_step(h, 1 - h->cur, false);
-                CK(h, cudaStreamEndCapture(h->ls, &gr));
-                CK(h, cudaGraphInstantiate(&h->graph[h->cur], gr, 0));
-                cudaGraphDestroy(gr);
-                h->graph_kernels = kk;
-            }
-            for (; k + 2 <= nsteps; k += 2) {
-                CK(h, cudaGraphLaunch(h->graph[h->cur], h->ls));
-                h->launches += h->graph_kernels;
-            }
+        for (; k + 2 <= nsteps; k += 2) {
+            st = launch_graph(h, 0);
+            if (st != FSL_OK) return st;
         }
-        for (; k < nsteps; ++k) {
-            h->launches += enqueue_step(h, h->cur, false);
+        if (k < nsteps) {
+            st = launch_graph(h, 1);
+            if (st != FSL_OK) return st;
             h->cur = 1 - h->cur;
         }
     }
@@ -508,6 +616,14 @@ fsl_status fsl_set_timing(fsl_domain* h, int32_t on) {
 double fsl_stream_collide_ms(const fsl_domain* h) { return h ? h->k1_ms : 0.0; }
 
 int64_t fsl_kernel_launches(const fsl_domain* h) { return h ? h->launches : 0; }
+
+int64_t fsl_labelling_runs(fsl_domain* h) {
+    if (!h) return -1;
+    long long r = 0;
+    if (cudaStreamSynchronize(h->ls) != cudaSuccess) return -1;
+    if (cudaMemcpy(&r, h->runs, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return r;
+}
 
 const char* fsl_last_error(const fsl_domain* h) { return h ? h->err.c_str() : "null handle"; }
 
@@ -643,12 +759,14 @@ fsl_status fsl_destroy(fsl_domain* h) {
     if (!h) return FSL_ERR_ARG;
     if (h->ls) cudaStreamSynchronize(h->ls);
     for (int k = 0; k < 2; ++k)
-        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        for (int j = 0; j < 3; ++j)
+            if (h->graph[k][j]) cudaGraphExecDestroy(h->graph[k][j]);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ls) cudaStreamDestroy(h->ls);
+    if (h->ls2) cudaStreamDestroy(h->ls2);
     delete h;
     return FSL_OK;
 }

@@ -42,20 +42,47 @@ __device__ inline void warp_add(long long* base, int key, long long v) {
     }
 }
 
+// Append v to list for every lane with pred set, one atomic per warp.  Every
+// lane of the warp must call.
+__device__ inline void warp_append(int* list, int* count, bool pred, int v) {
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, pred);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
 // ------------------------------------------------------ conversion phases
 
 // C1 (phase A): filled interface cells claim their gas neighbours (NEWG) and
-// cancel emptied marks next to them.  Resets the per-step counters.
+// cancel emptied marks next to them.  First clears the marks left on the cells
+// converted in the previous step and resets the per-step counters; the rest
+// is skipped in steps without marks.
 __global__ void __launch_bounds__(FSL_BLOCK) k_convert_a(StepArgs A) {
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const long long nth = (long long)gridDim.x * FSL_BLOCK;
+    const int nc = *A.ccount;
+    for (long long i = g; i < nc; i += nth) A.mark[A.clist[i]] = MK_NONE;
+    const int any = *A.anymark;
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
             if (A.nif[d] > 0) A.pool[d] = 0;
-            A.nif[d] = 0;
+            // without conversions the interface count is the one the previous
+            // step ended with
+            A.nif[d] = any ? 0 : A.icnt[d];
+            A.icnt[d] = 0;
         }
-        if (threadIdx.x == 0) *A.trig = 0;
+        if (threadIdx.x == 0) {
+            *A.trig = 0;
+            *A.icount = 0;
+        }
     }
-    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const uint8_t t = A.flag[g];
+    if (!any) return;
+    const uint8_t t = ctype(A.flag[g]);
     const uint8_t mk = A.mark[g];
     const bool gas = (t == GAS);
     const bool emp = (t == IFC && mk == MK_EMPTIED);
@@ -64,15 +91,10 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_a(StepArgs A) {
     const Cell c = make_cell(D, g);
     bool hit = false;
     for (int a = 1; a < 19 && !hit; ++a) {
-        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
-        if (A.flag[z] == IFC && A.mark[z] == MK_FILLED) hit = true;
+        const long long z = c.at(cx(a), cy(a), cz(a));
+        if (ctype(A.flag[z]) == IFC && A.mark[z] == MK_FILLED) hit = true;
     }
-    if (gas) {
-        const uint8_t nm = hit ? MK_NEWG : MK_NONE;
-        if (nm != mk) A.mark[g] = nm;
-    } else if (hit) {
-        A.mark[g] = MK_NONE;
-    }
+    if (hit) A.mark[g] = gas ? MK_NEWG : MK_NONE;
 }
 
 // Local test that removing the filled cell at the centre of the cube cannot
@@ -99,15 +121,20 @@ __device__ inline bool removal_is_local(unsigned fg) {
 
 // C3: excess mass of converted cells (filled: m - rho, emptied: m) split
 // equally among neighbours that are interface after conversion, else pooled;
-// count of interface cells; merge / split triggers.
+// count of interface cells; merge / split triggers.  A filled cell leaves
+// the bubble; taking the filled cells away one at a time in index order, each
+// removal must pass the local test with the lower-index filled cells already
+// gone and the higher-index ones still present, or the labelling runs.
 __global__ void __launch_bounds__(FSL_BLOCK) k_convert_c(StepArgs A) {
+    if (*A.anymark == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     const int d = A.blk_dom[blockIdx.x];
-    const uint8_t t = A.flag[g];
+    const uint8_t t = ctype(A.flag[g]);
     const uint8_t mk = A.mark[g];
     const uint8_t nt = new_type(t, mk);
     warp_add(A.nif, nt == IFC ? d : -1, 1);
     const bool conv = (t == IFC && (mk == MK_FILLED || mk == MK_EMPTIED));
+    warp_append(A.clist, A.ccount, conv, (int)g);
     const bool newl = (t == LIQ && mk == MK_NEWL);
     if (!conv && !newl) return;
     const Dom& D = A.doms[d];
@@ -116,25 +143,25 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_c(StepArgs A) {
         const double mex = (mk == MK_FILLED) ? A.m[g] - A.rhoi[g] : A.m[g];
         int k = 0;
         for (int a = 1; a < 19; ++a) {
-            const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
-            if (new_type(A.flag[z], A.mark[z]) == IFC) ++k;
+            const long long z = c.at(cx(a), cy(a), cz(a));
+            if (new_type(ctype(A.flag[z]), A.mark[z]) == IFC) ++k;
         }
         if (k > 0) A.exs[g] = mex / (double)k;
         else atomicAdd((unsigned long long*)&A.pool[d], (unsigned long long)__double2ll_rn(mex * 1099511627776.0));
         if (mk == MK_FILLED) {
             unsigned fgm = 0;
-            bool near_other = false;
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
                         if (dx == 0 && dy == 0 && dz == 0) continue;
                         const long long z = c.at(dx, dy, dz);
-                        const uint8_t tz = A.flag[z], mz = A.mark[z];
+                        const uint8_t tz = ctype(A.flag[z]), mz = A.mark[z];
                         const uint8_t ntz = new_type(tz, mz);
-                        if (ntz == GAS || ntz == IFC) fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-                        if (tz == IFC && (mz == MK_FILLED || mz == MK_CFILLED)) near_other = true;
+                        const bool later_filled = (tz == IFC && (mz == MK_FILLED || mz == MK_CFILLED) && z > g);
+                        if (ntz == GAS || ntz == IFC || later_filled)
+                            fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
                     }
-            if (near_other || !removal_is_local(fgm)) atomicExch(A.trig, 1);
+            if (!removal_is_local(fgm)) atomicExch(A.trig, 1);
         }
         A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
         return;
@@ -142,8 +169,8 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_c(StepArgs A) {
     // new interface cell from liquid: a neighbour of another bubble merges
     const int b = A.id[g];
     for (int a = 1; a < 19; ++a) {
-        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
-        const uint8_t ntz = new_type(A.flag[z], A.mark[z]);
+        const long long z = c.at(cx(a), cy(a), cz(a));
+        const uint8_t ntz = new_type(ctype(A.flag[z]), A.mark[z]);
         if ((ntz == GAS || ntz == IFC) && A.id[z] != b) {
             atomicExch(A.trig, 1);
             break;
@@ -153,11 +180,13 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_c(StepArgs A) {
 
 // C4: receivers pull the excess shares in direction order and the pool share,
 // phi = m / rho (Eq. 9), final cell types, incremental bubble volumes (fixed
-// point, so equal to the recomputed sum), reservoir drain.
+// point, so equal to the recomputed sum), reservoir drain; the interface list
+// of the next step; the graph condition of the labelling.
 __global__ void __launch_bounds__(FSL_BLOCK) k_convert_d(StepArgs A) {
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     const int d = A.blk_dom[blockIdx.x];
-    const uint8_t t = A.flag[g];
+    const uint8_t f = A.flag[g];
+    const uint8_t t = ctype(f);
     const uint8_t mk = A.mark[g];
     const uint8_t nt = new_type(t, mk);
     int key = -1;
@@ -169,7 +198,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_d(StepArgs A) {
         const Cell c = make_cell(D, g);
         double s = A.m[g];
         for (int a = 1; a < 19; ++a) {
-            const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
+            const long long z = c.at(cx(a), cy(a), cz(a));
             const uint8_t mz = A.mark[z];
             if (mz == MK_CFILLED || mz == MK_CEMPTIED) s = s + A.exs[z];
         }
@@ -182,7 +211,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_d(StepArgs A) {
         const long long told = volume_term(t, A.phi[g]);
         A.m[g] = s;
         A.phi[g] = phn;
-        if (t != IFC) A.flag[g] = IFC;
+        if (t != IFC) A.flag[g] = (uint8_t)((f & ~K_TYPE) | IFC);
         key = A.id[g];
         dv = volume_term(IFC, phn) - told;
         if (t == LIQ) { ckey = key; dc = 1; }
@@ -193,14 +222,14 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_d(StepArgs A) {
         dv = -volume_term(IFC, A.phi[g]);
         ckey = key;
         dc = -1;
-        A.flag[g] = LIQ;
+        A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
         A.phi[g] = 1.0;
         A.id[g] = -1;
     } else if (t == IFC && mk == MK_CEMPTIED) {
         const Dom& D = A.doms[d];
         key = A.id[g];
         dv = FSL_VOL_ONE - volume_term(IFC, A.phi[g]);
-        A.flag[g] = GAS;
+        A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
         A.phi[g] = 0.0;
         A.m[g] = 0.0;
         if (D.seed >= 0 && g - D.off == D.seed && key >= 0)
@@ -212,17 +241,36 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_d(StepArgs A) {
     }
     warp_add(A.vfx, dv != 0 ? key : -1, dv);
     warp_add(A.ncells, ckey, dc);
+    warp_add(A.icnt, nt == IFC ? d : -1, 1);
+    warp_append(A.ilist, A.icount, nt == IFC, (int)g);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *A.anymark = 0;
+        if (A.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond, *A.trig ? 1u : 0u);
+    }
+}
+
+// Interface list and per-domain interface counts of the initial state.
+__global__ void __launch_bounds__(FSL_BLOCK) k_build_ilist(StepArgs A) {
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const int d = A.blk_dom[blockIdx.x];
+    const bool itf = ctype(A.flag[g]) == IFC;
+    warp_add(A.icnt, itf ? d : -1, 1);
+    warp_append(A.ilist, A.icount, itf, (int)g);
 }
 
 // --------------------------------------------- connected-component labelling
 
-__device__ inline bool is_fg(uint8_t t) { return t == GAS || t == IFC; }
+__device__ inline bool is_fg(uint8_t f) { return ctype(f) == GAS || ctype(f) == IFC; }
 
-__device__ inline int find_root(const int* L, int a, int cap, bool& ok) {
+// Root of a; halves the path on the way (each cell is pointed at its
+// grandparent, still one of its ancestors, so the trees keep their roots).
+__device__ inline int find_root(int* L, int a, int cap, bool& ok) {
     for (int it = 0; it < cap; ++it) {
         const int p = L[a];
         if (p == a) return a;
-        a = p;
+        const int gp = L[p];
+        if (gp != p) L[a] = gp;
+        a = gp;
     }
     ok = false;
     return a;
@@ -271,7 +319,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_hook(StepArgs A, CclArgs K) {
     const Cell c = make_cell(D, g);
     // the nine directions 1, 3, ..., 17 cover each neighbour pair once
     for (int a = 1; a < 19; a += 2) {
-        const long long h = c.at(c_cx[a], c_cy[a], c_cz[a]);
+        const long long h = c.at(cx(a), cy(a), cz(a));
         if (is_fg(A.flag[h])) {
             if (!unite(K.lab, (int)g, (int)h, K.max_iter)) {
                 set_status(A.status, ST_CCL);
@@ -319,10 +367,10 @@ __device__ inline void hash_add(const CclArgs& K, unsigned long long key, long l
 __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_pairs(StepArgs A, CclArgs K) {
     if (!K.initial && *A.trig == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const uint8_t t = A.flag[g];
+    const uint8_t t = ctype(A.flag[g]);
     int c = -1;
     long long term = 0;
-    if (is_fg(t)) {
+    if (t == GAS || t == IFC) {
         const int r = K.lab[g];
         c = K.aux[r];
         term = volume_term(t, A.phi[g]);
@@ -375,6 +423,7 @@ __global__ void k_ccl_table(StepArgs A, CclArgs K) {
 
 __global__ void k_ccl_install(StepArgs A, CclArgs K, long long* vsfx, int* constp) {
     if (!K.initial && *A.trig == 0) return;
+    if (!K.initial && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)K.runs, 1ull);
     const long long nth = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < K.nslots_total; s += nth) {
         const int d = K.slot_dom[s];
@@ -405,16 +454,23 @@ __global__ void k_export_cells(const uint8_t* flag, const double* phi, const dou
                                const int* minidx, long long off, int n, uint8_t* oflag, double* ophi, double* om,
                                long long* oid, long long* counts) {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (counts) {
+        const int t = l < n ? (int)ctype(flag[off + l]) : -1;
+        for (int k = 0; k < 5; ++k) {
+            const unsigned m5 = __ballot_sync(0xffffffffu, t == k);
+            if ((threadIdx.x & 31) == 0 && m5) atomicAdd((unsigned long long*)&counts[k], (unsigned long long)__popc(m5));
+        }
+        return;
+    }
     if (l >= n) return;
     const long long g = off + l;
-    if (oflag) oflag[l] = flag[g];
+    if (oflag) oflag[l] = ctype(flag[g]);
     if (ophi) ophi[l] = phi[g];
     if (om) om[l] = m[g];
     if (oid) {
         const int b = id[g];
         oid[l] = b >= 0 ? (long long)minidx[b] : -1;
     }
-    if (counts) atomicAdd((unsigned long long*)&counts[flag[g] < 5 ? flag[g] : 4], 1ull);
 }
 
 // ------------------------------------------------------------ host launches
@@ -422,6 +478,7 @@ __global__ void k_export_cells(const uint8_t* flag, const double* phi, const dou
 void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_a<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
 void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_c<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
 void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_d<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
+void launch_build_ilist(const StepArgs& A, long long nb, cudaStream_t s) { k_build_ilist<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
 
 int launch_ccl(const StepArgs& A, const CclArgs& K, long long nb, long long* vsfx, int* constp, cudaStream_t s) {
     k_ccl_init<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);

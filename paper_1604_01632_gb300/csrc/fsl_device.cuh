@@ -23,7 +23,11 @@
 
 namespace fsl {
 
+// Cell types live in bits 0-2 of the flag byte; bit 3 (K_WALL) marks a cell
+// with an obstacle or lid among its 18 neighbours (walls never change).
 enum : uint8_t { LIQ = 0, IFC = 1, GAS = 2, OBS = 3, LID = 4 };
+enum : uint8_t { K_TYPE = 7, K_WALL = 8 };
+__host__ __device__ inline uint8_t ctype(uint8_t f) { return (uint8_t)(f & K_TYPE); }
 // Conversion marks (paper Sec. 2.2, cell conversion).  K1 writes NONE /
 // FILLED / EMPTIED on interface cells; phase A writes NEWG on gas cells and
 // clears EMPTIED next to FILLED; phase B writes NEWL / NONE on liquid cells;
@@ -75,12 +79,28 @@ struct StepArgs {
     int* trig;                  // merge/split trigger (any domain)
     int* status;
     int ndom;
+    int* ilist;                 // interface cells of the current step
+    int* icount;
+    int* clist;                 // cells converted in the previous step (stale marks)
+    int* ccount;
+    int* anymark;               // some interface cell was marked filled / emptied
+    long long* icnt;            // per-domain interface count at the end of the step
+    unsigned long long cond;    // graph conditional handle set to the trigger (0: none)
 };
 
-// D3Q19 velocities (one copy per translation unit)
-static __constant__ int c_cx[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-static __constant__ int c_cy[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-static __constant__ int c_cz[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+// D3Q19 velocities; constexpr so that unrolled loops fold them into offsets
+__host__ __device__ constexpr int cx(int a) {
+    return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+           : ((a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int a) {
+    return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+           : ((a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0);
+}
+__host__ __device__ constexpr int cz(int a) {
+    return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+           : ((a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0);
+}
 
 __host__ __device__ inline int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 __host__ __device__ inline double weight(int a) {
@@ -158,7 +178,7 @@ template <> struct Form<__nv_bfloat16> {
 
 template <typename C>
 __device__ inline C cdot(int a, C vx, C vy, C vz) {
-    return ((C)c_cx[a] * vx + (C)c_cy[a] * vy) + (C)c_cz[a] * vz;
+    return ((C)cx(a) * vx + (C)cy(a) * vy) + (C)cz(a) * vz;
 }
 
 // Moments (Eqs. 4-5).
@@ -228,66 +248,6 @@ __device__ inline C collide(const C* fin, C* fout, C omp, C omm, C gx, C gy, C g
 
 // --------------------------------------------------------- free surface
 
-__device__ inline double phi_stencil(const uint8_t* flag, const double* phi, long long j) {
-    uint8_t t = flag[j];
-    if (t == LIQ || t == OBS || t == LID) return 1.0;
-    if (t == GAS) return 0.0;
-    double v = phi[j];
-    return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
-}
-
-// Parker-Youngs gradient of the fill level around (cx+ox, cy+oy, cz+oz):
-// central differences over the 3x3 cross-section, weights 4 / 2 / 1.
-template <typename C>
-__device__ inline void py_gradient(const Cell& c, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
-                                   C& gx, C& gy, C& gz) {
-    gx = (C)0; gy = (C)0; gz = (C)0;
-    for (int b = -1; b <= 1; ++b) {
-        for (int a = -1; a <= 1; ++a) {
-            C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
-            C px = (C)phi_stencil(flag, phi, c.at_far(ox + 1, oy + a, oz + b));
-            C mx = (C)phi_stencil(flag, phi, c.at_far(ox - 1, oy + a, oz + b));
-            gx = gx + W * (px - mx);
-            C py = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy + 1, oz + b));
-            C my = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy - 1, oz + b));
-            gy = gy + W * (py - my);
-            C pz = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy + b, oz + 1));
-            C mz = (C)phi_stencil(flag, phi, c.at_far(ox + a, oy + b, oz - 1));
-            gz = gz + W * (pz - mz);
-        }
-    }
-}
-
-template <typename C>
-__device__ inline void unit_normal(const Cell& c, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
-                                   C& nx, C& ny, C& nz) {
-    C gx, gy, gz;
-    py_gradient<C>(c, ox, oy, oz, flag, phi, gx, gy, gz);
-    C q = gx * gx + gy * gy + gz * gz;
-    if (q > (C)0) {
-        C len = sqrt(q);
-        nx = -(gx / len); ny = -(gy / len); nz = -(gz / len);
-    } else {
-        nx = (C)0; ny = (C)0; nz = (C)0;
-    }
-}
-
-// kappa = 1/2 div(n_hat), central differences (Eq. 15).
-template <typename C>
-__device__ inline C curvature(const Cell& c, const uint8_t* flag, const double* phi) {
-    C px, py, pz, mx, my, mz;
-    unit_normal<C>(c, 1, 0, 0, flag, phi, px, py, pz);
-    unit_normal<C>(c, -1, 0, 0, flag, phi, mx, my, mz);
-    C dX = px - mx;
-    unit_normal<C>(c, 0, 1, 0, flag, phi, px, py, pz);
-    unit_normal<C>(c, 0, -1, 0, flag, phi, mx, my, mz);
-    C dY = py - my;
-    unit_normal<C>(c, 0, 0, 1, flag, phi, px, py, pz);
-    unit_normal<C>(c, 0, 0, -1, flag, phi, mx, my, mz);
-    C dZ = pz - mz;
-    return (C)0.25 * ((dX + dY) + dZ);
-}
-
 // Ideal-gas bubble pressure (Eq. 13), p0 = rho0 c_s^2 = 1/3 (Eq. 14).
 __device__ inline double bubble_pressure(long long vfx, long long vxfx, long long vsfx, int constp) {
     const double p0 = 1.0 / 3.0;
@@ -320,127 +280,263 @@ __device__ inline uint8_t new_type(uint8_t t, uint8_t mk) {
 
 // ================================================================ kernels
 
-// K1: stream with bounce-back (Eq. 7), mass exchange (Eq. 10) and free-
-// surface reconstruction (Eqs. 11-15) on interface cells, collision (Eq. 6),
-// marks for filled / emptied interface cells.  One thread per cell.
+// Wrapped +-1 neighbour offsets of one cell, for the streaming pull.
+struct Pull {
+    long long g;
+    int ox[3], oy[3], oz[3];   // offset for a step of -1, 0, +1 along each axis
+    __device__ inline long long at(int dx, int dy, int dz) const { return g + ox[dx + 1] + oy[dy + 1] + oz[dz + 1]; }
+};
+
+__device__ inline Pull make_pull(const Dom& D, long long g) {
+    Pull p;
+    p.g = g;
+    const int l = (int)(g - D.off);
+    const int x = l % D.nx, r = l / D.nx;
+    const int y = r % D.ny, z = r / D.ny;
+    const int sy = D.nx, sz = D.nx * D.ny;
+    p.ox[0] = x == 0 ? D.nx - 1 : -1;
+    p.ox[1] = 0;
+    p.ox[2] = x == D.nx - 1 ? -(D.nx - 1) : 1;
+    p.oy[0] = y == 0 ? (D.ny - 1) * sy : -sy;
+    p.oy[1] = 0;
+    p.oy[2] = y == D.ny - 1 ? -(D.ny - 1) * sy : sy;
+    p.oz[0] = z == 0 ? (D.nz - 1) * sz : -sz;
+    p.oz[1] = 0;
+    p.oz[2] = z == D.nz - 1 ? -(D.nz - 1) * sz : sz;
+    return p;
+}
+
+// K1L: stream with half-way bounce-back (Eq. 7) and collide (Eq. 6) for
+// liquid cells.  Only cells flagged as touching a wall read the types of
+// their neighbours; a liquid cell never touches gas (closed interface layer).
 template <typename T>
-__global__ void __launch_bounds__(FSL_BLOCK) k_stream_collide(StepArgs A) {
+__global__ void __launch_bounds__(FSL_BLOCK) k_stream_liquid(StepArgs A) {
     using C = typename Form<T>::C;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const uint8_t t = A.flag[g];
-    if (t != LIQ && t != IFC) return;
+    const uint8_t f = A.flag[g];
+    if (ctype(f) != LIQ) return;
     const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
-    const Cell c = make_cell(D, g);
+    const Pull P = make_pull(D, g);
     const long long S = A.stride;
-    const T* src = (const T*)A.fsrc;
-    T* dst = (T*)A.fdst;
-
+    const T* __restrict__ src = (const T*)A.fsrc;
+    T* __restrict__ dst = (T*)A.fdst;
     C fin[19];
     fin[0] = Form<T>::ld(src + g, 0);
-    if (t == LIQ) {
+    if (!(f & K_WALL)) {
+#pragma unroll
+        for (int a = 1; a < 19; ++a) fin[a] = Form<T>::ld(src + (long long)a * S + P.at(-cx(a), -cy(a), -cz(a)), a);
+    } else {
 #pragma unroll
         for (int a = 1; a < 19; ++a) {
             const int ab = opp(a);
-            const long long y = c.at(-c_cx[a], -c_cy[a], -c_cz[a]);
-            const uint8_t ty = A.flag[y];
+            const long long y = P.at(-cx(a), -cy(a), -cz(a));
+            const uint8_t ty = ctype(A.flag[y]);
             if (ty == OBS) {
                 fin[a] = Form<T>::ld(src + (long long)ab * S + g, ab);
             } else if (ty == LID) {
                 C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
                 fin[a] = Form<T>::ld(src + (long long)ab * S + g, ab) + ((C)6 * (C)weight(a)) * cuw;
             } else {
-                if (ty == GAS) set_status(A.status, ST_GEOMETRY);
                 fin[a] = Form<T>::ld(src + (long long)a * S + y, a);
             }
         }
-        C fout[19];
-        C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
-        if (!(rho == rho)) set_status(A.status, ST_NAN);
-#pragma unroll
-        for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
-        return;
     }
-
-    // interface cell
-    C fs[19];
-#pragma unroll
-    for (int a = 0; a < 19; ++a) fs[a] = Form<T>::ld(src + (long long)a * S + g, a);
-    C rs, jsx, jsy, jsz;
-    moments<C>(fs, rs, jsx, jsy, jsz);
-    C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
-    C kappa = curvature<C>(c, A.flag, A.phi);
-    const int b = A.id[g];
-    double pv = b >= 0 ? bubble_pressure(A.vfx[b], A.vxfx[b], A.vsfx[b], A.constp[b]) : 1.0 / 3.0;
-    C pg = (C)pv + (C)D.sigma2 * kappa;
-    C rg = (C)3 * pg;
-    C fg[19];
-    feq_all<C>(rg, ugx, ugy, ugz, fg);
-    C gx, gy, gz;
-    py_gradient<C>(c, 0, 0, 0, A.flag, A.phi, gx, gy, gz);
-
-    const double phx = A.phi[g];
-    double dm = 0.0;
-#pragma unroll
-    for (int a = 1; a < 19; ++a) {
-        const int ab = opp(a);
-        const long long y = c.at(-c_cx[a], -c_cy[a], -c_cz[a]);
-        const uint8_t ty = A.flag[y];
-        if (ty == OBS) {
-            fin[a] = fs[ab];
-        } else if (ty == LID) {
-            C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
-            fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
-        } else if (ty == GAS) {
-            fin[a] = (fg[a] + fg[ab]) - fs[ab];
-        } else {
-            // the PDF streaming in from y = x - c_a; it is also f*_a(y), the
-            // f*_{abar}(x + c_abar) of the mass balance over link abar
-            C fy = Form<T>::ld(src + (long long)a * S + y, a);
-            fin[a] = fy;
-            if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
-        }
-    }
-    // mass exchange over the 18 links, in direction order (Eq. 10)
-#pragma unroll
-    for (int a = 1; a < 19; ++a) {
-        const int ab = opp(a);
-        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
-        const uint8_t tz = A.flag[z];
-        if (tz == LIQ || tz == IFC) {
-            double fz = (double)Form<T>::ld(src + (long long)ab * S + z, ab);
-            double ex = fz - (double)fs[a];
-            if (tz == LIQ) dm = dm + ex;
-            else dm = dm + (0.5 * (phx + A.phi[z])) * ex;
-        }
-    }
-    const double mnew = A.m[g] + dm;
     C fout[19];
     C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
     if (!(rho == rho)) set_status(A.status, ST_NAN);
 #pragma unroll
     for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
-    const double r = (double)rho;
-    A.m[g] = mnew;
-    A.rhoi[g] = r;
-    uint8_t mk = MK_NONE;
-    if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
-    else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
-    A.mark[g] = mk;
+}
+
+// Wrapped coordinates x-2..x+2 (and y, z) of one interface cell, for the
+// 5x5x5 fill-level stencil of the curvature.
+struct Stencil {
+    int X[5], Y[5], Z[5];
+    int nx;
+    long long nxy, off;
+    __device__ inline long long at(int dx, int dy, int dz) const {
+        return off + X[dx + 2] + (long long)nx * Y[dy + 2] + nxy * Z[dz + 2];
+    }
+};
+
+__device__ inline Stencil make_stencil(const Dom& D, long long g) {
+    Stencil s;
+    const int l = (int)(g - D.off);
+    const int x = l % D.nx, r = l / D.nx;
+    const int y = r % D.ny, z = r / D.ny;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        s.X[k] = ((x + k - 2) % D.nx + D.nx) % D.nx;
+        s.Y[k] = ((y + k - 2) % D.ny + D.ny) % D.ny;
+        s.Z[k] = ((z + k - 2) % D.nz + D.nz) % D.nz;
+    }
+    s.nx = D.nx;
+    s.nxy = (long long)D.nx * D.ny;
+    s.off = D.off;
+    return s;
+}
+
+__device__ inline double phi_stencil(const uint8_t* flag, const double* phi, long long j) {
+    const uint8_t t = ctype(flag[j]);
+    if (t == LIQ || t == OBS || t == LID) return 1.0;
+    if (t == GAS) return 0.0;
+    const double v = phi[j];
+    return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+}
+
+// Parker-Youngs gradient of the fill level around offset (ox, oy, oz):
+// central differences over the 3x3 cross-section, weights 4 / 2 / 1.
+template <typename C>
+__device__ inline void py_gradient(const Stencil& s, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
+                                   C& gx, C& gy, C& gz) {
+    gx = (C)0; gy = (C)0; gz = (C)0;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) {
+            const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
+            const C px = (C)phi_stencil(flag, phi, s.at(ox + 1, oy + a, oz + b));
+            const C mx = (C)phi_stencil(flag, phi, s.at(ox - 1, oy + a, oz + b));
+            gx = gx + W * (px - mx);
+            const C py = (C)phi_stencil(flag, phi, s.at(ox + a, oy + 1, oz + b));
+            const C my = (C)phi_stencil(flag, phi, s.at(ox + a, oy - 1, oz + b));
+            gy = gy + W * (py - my);
+            const C pz = (C)phi_stencil(flag, phi, s.at(ox + a, oy + b, oz + 1));
+            const C mz = (C)phi_stencil(flag, phi, s.at(ox + a, oy + b, oz - 1));
+            gz = gz + W * (pz - mz);
+        }
+    }
+}
+
+template <typename C>
+__device__ inline void unit_normal(const Stencil& s, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
+                                   C& nx, C& ny, C& nz) {
+    C gx, gy, gz;
+    py_gradient<C>(s, ox, oy, oz, flag, phi, gx, gy, gz);
+    const C q = gx * gx + gy * gy + gz * gz;
+    if (q > (C)0) {
+        const C len = sqrt(q);
+        nx = -(gx / len); ny = -(gy / len); nz = -(gz / len);
+    } else {
+        nx = (C)0; ny = (C)0; nz = (C)0;
+    }
+}
+
+// kappa = 1/2 div(n_hat), central differences (Eq. 15).
+template <typename C>
+__device__ inline C curvature(const Stencil& s, const uint8_t* flag, const double* phi) {
+    C px, py, pz, mx, my, mz;
+    unit_normal<C>(s, 1, 0, 0, flag, phi, px, py, pz);
+    unit_normal<C>(s, -1, 0, 0, flag, phi, mx, my, mz);
+    const C dX = px - mx;
+    unit_normal<C>(s, 0, 1, 0, flag, phi, px, py, pz);
+    unit_normal<C>(s, 0, -1, 0, flag, phi, mx, my, mz);
+    const C dY = py - my;
+    unit_normal<C>(s, 0, 0, 1, flag, phi, px, py, pz);
+    unit_normal<C>(s, 0, 0, -1, flag, phi, mx, my, mz);
+    const C dZ = pz - mz;
+    return (C)0.25 * ((dX + dY) + dZ);
+}
+
+// K1I: interface cells, from the list of interface cells built at the end of
+// the previous step: stream with bounce-back, mass exchange over the 18 links
+// (Eq. 10), reconstruction of the PDFs coming from the gas side with the gas
+// density 3 (p_V + 2 sigma kappa) of the cell's bubble (Eqs. 8, 11-15),
+// collide, then the filled / emptied marks.
+template <typename T>
+__global__ void __launch_bounds__(128) k_stream_interface(StepArgs A) {
+    using C = typename Form<T>::C;
+    const int cnt = *A.icount;
+    const long long S = A.stride;
+    const T* __restrict__ src = (const T*)A.fsrc;
+    T* __restrict__ dst = (T*)A.fdst;
+    bool marked = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const long long g = A.ilist[i];
+        const Dom& D = A.doms[A.blk_dom[g / FSL_BLOCK]];
+        const Stencil st = make_stencil(D, g);
+        C fs[19];
+#pragma unroll
+        for (int a = 0; a < 19; ++a) fs[a] = Form<T>::ld(src + (long long)a * S + g, a);
+        C rs, jsx, jsy, jsz;
+        moments<C>(fs, rs, jsx, jsy, jsz);
+        const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
+        const C kappa = curvature<C>(st, A.flag, A.phi);
+        const int b = A.id[g];
+        const double pv = b >= 0 ? bubble_pressure(A.vfx[b], A.vxfx[b], A.vsfx[b], A.constp[b]) : 1.0 / 3.0;
+        const C pg = (C)pv + (C)D.sigma2 * kappa;
+        const C rg = (C)3 * pg;
+        C fg[19];
+        feq_all<C>(rg, ugx, ugy, ugz, fg);
+        C gx, gy, gz;
+        py_gradient<C>(st, 0, 0, 0, A.flag, A.phi, gx, gy, gz);
+
+        C fin[19];
+        fin[0] = fs[0];
+#pragma unroll
+        for (int a = 1; a < 19; ++a) {
+            const int ab = opp(a);
+            const long long y = st.at(-cx(a), -cy(a), -cz(a));
+            const uint8_t ty = ctype(A.flag[y]);
+            if (ty == OBS) {
+                fin[a] = fs[ab];
+            } else if (ty == LID) {
+                const C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
+                fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
+            } else if (ty == GAS) {
+                fin[a] = (fg[a] + fg[ab]) - fs[ab];
+            } else {
+                fin[a] = Form<T>::ld(src + (long long)a * S + y, a);
+                if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
+            }
+        }
+        // mass exchange over the 18 links, in direction order (Eq. 10)
+        const double phx = A.phi[g];
+        double dm = 0.0;
+#pragma unroll
+        for (int a = 1; a < 19; ++a) {
+            const int ab = opp(a);
+            const long long z = st.at(cx(a), cy(a), cz(a));
+            const uint8_t tz = ctype(A.flag[z]);
+            if (tz == LIQ || tz == IFC) {
+                const double fz = (double)Form<T>::ld(src + (long long)ab * S + z, ab);
+                const double ex = fz - (double)fs[a];
+                if (tz == LIQ) dm = dm + ex;
+                else dm = dm + (0.5 * (phx + A.phi[z])) * ex;
+            }
+        }
+        const double mnew = A.m[g] + dm;
+        C fout[19];
+        const C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+        if (!(rho == rho)) set_status(A.status, ST_NAN);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
+        const double r = (double)rho;
+        A.m[g] = mnew;
+        A.rhoi[g] = r;
+        uint8_t mk = MK_NONE;
+        if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
+        else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
+        A.mark[g] = mk;
+        marked |= (mk != MK_NONE);
+    }
+    if (__any_sync(0xffffffffu, marked) && (threadIdx.x & 31) == 0) *A.anymark = 1;
 }
 
 // C2 (conversion phase B): remaining emptied cells turn their liquid
 // neighbours into interface (bubble of the first emptied neighbour in
 // direction order, m = rho); new interface cells from gas get f = f_eq of the
 // mean density and velocity of their liquid / non-emptied interface
-// neighbours, m = 0.  Stale marks of liquid cells are cleared.
+// neighbours, m = 0.  Skipped in steps without marks.
 template <typename T>
 __global__ void __launch_bounds__(FSL_BLOCK) k_convert_b(StepArgs A) {
     using C = typename Form<T>::C;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.ccount = 0;   // C1 has cleared the stale marks
+    if (*A.anymark == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const uint8_t t = A.flag[g];
+    const uint8_t t = ctype(A.flag[g]);
     if (t != LIQ && t != GAS) return;
-    const uint8_t mk = A.mark[g];
-    if (t == GAS && mk != MK_NEWG) return;
+    if (t == GAS && A.mark[g] != MK_NEWG) return;
     const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
     const Cell c = make_cell(D, g);
     const long long S = A.stride;
@@ -448,8 +544,8 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_b(StepArgs A) {
     if (t == LIQ) {
         int best = -1;
         for (int a = 1; a < 19 && best < 0; ++a) {
-            const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
-            if (A.flag[z] == IFC && A.mark[z] == MK_EMPTIED) best = A.id[z];
+            const long long z = c.at(cx(a), cy(a), cz(a));
+            if (ctype(A.flag[z]) == IFC && A.mark[z] == MK_EMPTIED) best = A.id[z];
         }
         if (best >= 0) {
             double r = (double)Form<T>::ld(f + g, 0);
@@ -458,8 +554,6 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_b(StepArgs A) {
             A.id[g] = best;
             A.m[g] = r;
             A.rhoi[g] = r;
-        } else if (mk != MK_NONE) {
-            A.mark[g] = MK_NONE;
         }
         return;
     }
@@ -467,8 +561,8 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_convert_b(StepArgs A) {
     C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
     int cnt = 0;
     for (int a = 1; a < 19; ++a) {
-        const long long z = c.at(c_cx[a], c_cy[a], c_cz[a]);
-        const uint8_t tz = A.flag[z];
+        const long long z = c.at(cx(a), cy(a), cz(a));
+        const uint8_t tz = ctype(A.flag[z]);
         if (tz == LIQ || (tz == IFC && A.mark[z] != MK_EMPTIED)) {
             C fo[19];
 #pragma unroll
@@ -506,15 +600,15 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_init_state(StepArgs A, int d, con
     const uint8_t t = flags_in[l];
     const Cell c = make_cell(D, g);
     if (t > LID) { set_status(A.status, -1); return; }
-    if (t == LIQ) {
-        for (int a = 1; a < 19; ++a) {
-            // neighbours are read from the input (the device flag array is
-            // being written by other threads)
-            long long z = c.at(c_cx[a], c_cy[a], c_cz[a]) - D.off;
-            if (flags_in[z] == GAS) set_status(A.status, ST_GEOMETRY);
-        }
+    bool wall = false;
+    for (int a = 1; a < 19; ++a) {
+        // neighbours are read from the input (the device flag array is being
+        // written by other threads)
+        const long long z = c.at(cx(a), cy(a), cz(a)) - D.off;
+        if (t == LIQ && flags_in[z] == GAS) set_status(A.status, ST_GEOMETRY);
+        if (flags_in[z] == OBS || flags_in[z] == LID) wall = true;
     }
-    A.flag[g] = t;
+    A.flag[g] = (uint8_t)(t | (wall ? K_WALL : 0));
     A.mark[g] = MK_NONE;
     A.id[g] = -1;
     A.exs[g] = 0.0;
@@ -558,7 +652,7 @@ __global__ void k_export_pdf(const T* f, long long S, long long off, int n, doub
 }
 
 // Launch helpers instantiated once per storage form.
-template <typename T> void launch_stream_collide(const StepArgs& A, long long nblocks, cudaStream_t s);
+template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, cudaStream_t s);
 template <typename T> void launch_convert_b(const StepArgs& A, long long nblocks, cudaStream_t s);
 template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
                                              const double* rho, const double* u, cudaStream_t s);
@@ -566,8 +660,9 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
                                              double* rho, double* u, cudaStream_t s);
 
 #define FSL_INSTANTIATE_FORM(T)                                                                              \
-    template <> void launch_stream_collide<T>(const StepArgs& A, long long nb, cudaStream_t s) {             \
-        k_stream_collide<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                          \
+    template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, cudaStream_t s) {            \
+        k_stream_liquid<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                           \
+        k_stream_interface<T><<<(unsigned)ifb, 128, 0, s>>>(A);                                             \
     }                                                                                                        \
     template <> void launch_convert_b<T>(const StepArgs& A, long long nb, cudaStream_t s) {                  \
         k_convert_b<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                               \

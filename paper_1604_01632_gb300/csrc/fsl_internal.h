@@ -28,6 +28,7 @@ struct CclArgs {
     int* nslot;                  // per domain: slots in use
     const int* slot_dom;         // slot -> domain
     long long nslots_total;
+    long long* runs;             // labelling passes run after initialisation
     int initial;                 // 1: first labelling after initialisation (V* = V)
     int max_iter;                // cap on union / find loops
 };
@@ -35,6 +36,7 @@ struct CclArgs {
 void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s);
 void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s);
 void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s);
+void launch_build_ilist(const StepArgs& A, long long nb, cudaStream_t s);
 int launch_ccl(const StepArgs& A, const CclArgs& K, long long nb, long long* vsfx, int* constp, cudaStream_t s);
 void launch_export_minid(const int* id, long long off, int n, int* minidx, cudaStream_t s);
 void launch_export_cells(const uint8_t* flag, const double* phi, const double* m, const int* id, const int* minidx,

@@ -105,10 +105,11 @@ def test_batched_domains_match_separate_oracles(fsl, oracle_mod):
     scs.append(S.static_bubble(n=16, radius=4.0))
     sim = fsl.Simulation.from_scenarios(scs, precision="fp64")
     oras = [oracle_mod.Oracle.from_scenario(s) for s in scs]
+    prev = 0
     for k in (1, 7, 40):
-        sim.step(k if k == 1 else k - prev)
+        sim.step(k - prev)
         for o in oras:
-            o.step(k if k == 1 else k - prev)
+            o.step(k - prev)
         prev = k
         for d, o in enumerate(oras):
             compare_exact(gpu_state(sim, d), oracle_state(o), what=f"domain {d} step {k}")
@@ -135,7 +136,10 @@ def test_geometry_error_is_reported(fsl):
     assert gas >= 0
 
 
-@pytest.mark.parametrize("precision,tol_u,tol_rho,tol_v", [("fp32", 1e-6, 1e-6, 1e-6), ("f16s", 2e-4, 2e-4, 1e-3),
+# FP32 stores f itself (values ~w_a), so each step rounds at ~1e-8 and the
+# density drifts by a few 1e-6 over 200 steps; the shifted 16-bit forms store
+# only f_a - w_a and round that small deviation instead
+@pytest.mark.parametrize("precision,tol_u,tol_rho,tol_v", [("fp32", 3e-5, 3e-5, 1e-4), ("f16s", 2e-4, 2e-4, 1e-3),
                                                             ("bf16s", 2e-3, 2e-3, 1e-2)])
 def test_reduced_precision_static_bubble(fsl, oracle_mod, precision, tol_u, tol_rho, tol_v):
     """FP32 collide with FP32 / FP16-shifted / BF16-shifted storage against the FP64
@@ -149,6 +153,9 @@ def test_reduced_precision_static_bubble(fsl, oracle_mod, precision, tol_u, tol_
     fl = np.isin(r["flags"], (S.LIQUID, S.INTERFACE)) & np.isin(g["flags"], (S.LIQUID, S.INTERFACE))
     rg, ug = macro(g["f"][:, fl])
     rr, ur = macro(r["f"][:, fl])
+    print(f"{precision}: |drho| {np.abs(rg - rr).max():.3e} |du| {np.abs(ug - ur).max():.3e} "
+          f"dV/V {abs(g['bubbles']['volume'][0] / r['bubbles']['volume'][0] - 1.0):.3e} "
+          f"flag agreement {(g['flags'] == r['flags']).mean():.6f}")
     assert np.abs(rg - rr).max() < tol_rho
     assert np.abs(ug - ur).max() < tol_u
     assert len(g["bubbles"]) == len(r["bubbles"]) == 1
