@@ -148,7 +148,10 @@ def run_gpu(args, rank: int, world: int):
     stream = torch.cuda.current_stream()
 
     def make(precision):
-        return fsl.Simulation.from_scenarios([sc], precision=precision, stream=int(stream.cuda_stream))
+        sim = fsl.Simulation.from_scenarios([sc], precision=precision, stream=int(stream.cuda_stream))
+        if args.no_graphs:
+            sim.set_graphs(False)
+        return sim
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -308,6 +311,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true", help="direct kernel launches (for ncu)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

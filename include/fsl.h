@@ -157,6 +157,13 @@ int64_t fsl_labelling_runs(fsl_domain* h);
 fsl_status fsl_set_timing(fsl_domain* h, int32_t on);
 double fsl_stream_collide_ms(const fsl_domain* h);
 
+/* on = 1 (default): fsl_step replays CUDA graphs of one or two steps in which
+ * the labelling runs as a conditional node; on = 0: every kernel is a separate
+ * launch and the labelling kernels return at once in steps without a trigger
+ * (for profilers that cannot look inside graphs with conditional nodes).
+ * Results are identical. */
+fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
+
 /* Counts of the cell types of domain d (array of 5), synchronises. */
 fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts);
 

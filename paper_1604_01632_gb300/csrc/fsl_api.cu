@@ -55,7 +55,10 @@ struct fsl_domain {
     long long *pool = nullptr, *nif = nullptr;
     int* trig = nullptr;
     int* status = nullptr;
-    int *ilist = nullptr, *icount = nullptr, *clist = nullptr, *ccount = nullptr, *anymark = nullptr;
+    int* ilist[2] = {nullptr, nullptr};   // interface list read by a step starting from buffer k
+    int* icount[2] = {nullptr, nullptr};
+    int *mlist = nullptr, *mcount = nullptr, *glist = nullptr, *gcount = nullptr, *llist = nullptr, *lcount = nullptr;
+    int *cstep = nullptr, *stepno = nullptr;
     long long* icnt = nullptr;
     // labelling scratch
     int *lab = nullptr, *aux = nullptr;
@@ -76,9 +79,11 @@ struct fsl_domain {
     // 2 = one step with event-record nodes around the stream-collide kernels
     cudaGraphExec_t graph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     cudaGraphNode_t rec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraph_t timed_src[2] = {nullptr, nullptr};   // kept: its nodes name the event records
     int graph_kernels[3] = {0, 0, 0};
     long long launches = 0;
     bool timing = false;
+    bool graphs = true;           // false: every kernel a separate launch (profilers)
     std::vector<cudaEvent_t> evpool;
     size_t evused = 0;
     double k1_ms = 0.0;
@@ -138,11 +143,18 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.trig = h->trig;
     A.status = h->status;
     A.ndom = h->ndom;
-    A.ilist = h->ilist;
-    A.icount = h->icount;
-    A.clist = h->clist;
-    A.ccount = h->ccount;
-    A.anymark = h->anymark;
+    A.ilist = h->ilist[src];
+    A.icount = h->icount[src];
+    A.ilist_next = h->ilist[1 - src];
+    A.icount_next = h->icount[1 - src];
+    A.mlist = h->mlist;
+    A.mcount = h->mcount;
+    A.glist = h->glist;
+    A.gcount = h->gcount;
+    A.llist = h->llist;
+    A.lcount = h->lcount;
+    A.cstep = h->cstep;
+    A.stepno = h->stepno;
     A.icnt = h->icnt;
     A.cond = 0;
     return A;
@@ -186,10 +198,10 @@ void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
 
 void launch_cb(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_convert_b<double>(A, h->nblocks, st); break;
-    case FSL_P_FP32: launch_convert_b<float>(A, h->nblocks, st); break;
-    case FSL_P_F16S: launch_convert_b<__half>(A, h->nblocks, st); break;
-    default: launch_convert_b<__nv_bfloat16>(A, h->nblocks, st); break;
+    case FSL_P_FP64: launch_convert_b<double>(A, h->ifblocks, st); break;
+    case FSL_P_FP32: launch_convert_b<float>(A, h->ifblocks, st); break;
+    case FSL_P_F16S: launch_convert_b<__half>(A, h->ifblocks, st); break;
+    default: launch_convert_b<__nv_bfloat16>(A, h->ifblocks, st); break;
     }
 }
 
@@ -205,13 +217,19 @@ int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e
         if (cudaStreamGetCaptureInfo(h->ls, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess && nd == 1)
             rec[k] = deps[0];
     };
-    if (e0) { cudaEventRecord(e0, h->ls); last_node(0); }
+    // while capturing (rec given) the records are external, so that the
+    // capture turns them into event-record nodes
+    auto record = [&](cudaEvent_t e) {
+        if (rec) cudaEventRecordWithFlags(e, h->ls, cudaEventRecordExternal);
+        else cudaEventRecord(e, h->ls);
+    };
+    if (e0) { record(e0); last_node(0); }
     launch_k1(h, A, h->ls);
-    if (e1) { cudaEventRecord(e1, h->ls); last_node(1); }
-    launch_convert_a(A, h->nblocks, h->ls);
+    if (e1) { record(e1); last_node(1); }
+    launch_convert_a(A, h->ifblocks, h->ls);
     launch_cb(h, A, h->ls);
-    launch_convert_c(A, h->nblocks, h->ls);
-    launch_convert_d(A, h->nblocks, h->ls);
+    launch_convert_c(A, h->ifblocks, h->ls);
+    launch_convert_d(A, h->ifblocks, h->ls);
     return 6;
 }
 
@@ -257,7 +275,7 @@ fsl_status ensure_initial(fsl_domain* h) {
         if (!h->inited[d]) return fail(h, FSL_ERR_ARG, "every domain must be initialised first");
     StepArgs A = step_args(h, h->cur);
     h->launches += launch_ccl(A, ccl_args(h, 1), h->nblocks, h->vsfx, h->constp, h->ls);
-    CK(h, cudaMemsetAsync(h->icount, 0, sizeof(int), h->ls));
+    CK(h, cudaMemsetAsync(h->icount[h->cur], 0, sizeof(int), h->ls));
     CK(h, cudaMemsetAsync(h->icnt, 0, 8 * (size_t)h->ndom, h->ls));
     launch_build_ilist(A, h->nblocks, h->ls);
     h->launches += 1;
@@ -314,7 +332,8 @@ fsl_status build_graph(fsl_domain* h, int start, int kind) {
         return fail(h, FSL_ERR_CUDA, "event-record nodes not found in the captured step");
     }
     CK(h, cudaGraphInstantiate(&h->graph[start][kind], G, 0));
-    cudaGraphDestroy(G);
+    if (kind == 2) h->timed_src[start] = G;
+    else cudaGraphDestroy(G);
     h->graph_kernels[kind] = kk;   // the labelling kernels run only on trigger steps
     if (kind == 2) h->evused -= 2;  // the capture events are placeholders
     return FSL_OK;
@@ -424,11 +443,18 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->nif, 8 * n_domains);
     AL(h->trig, sizeof(int));
     AL(h->status, sizeof(int));
-    AL(h->ilist, 4 * N);
-    AL(h->icount, sizeof(int));
-    AL(h->clist, 4 * N);
-    AL(h->ccount, sizeof(int));
-    AL(h->anymark, sizeof(int));
+    AL(h->ilist[0], 4 * N);
+    AL(h->ilist[1], 4 * N);
+    AL(h->icount[0], sizeof(int));
+    AL(h->icount[1], sizeof(int));
+    AL(h->mlist, 4 * N);
+    AL(h->mcount, sizeof(int));
+    AL(h->glist, 4 * N);
+    AL(h->gcount, sizeof(int));
+    AL(h->llist, 4 * N);
+    AL(h->lcount, sizeof(int));
+    AL(h->cstep, 4 * N);
+    AL(h->stepno, sizeof(int));
     AL(h->icnt, 8 * n_domains);
     AL(h->lab, 4 * N);
     AL(h->aux, 4 * N);
@@ -469,9 +495,13 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->nif, 0, 8 * n_domains);
     if (e == cudaSuccess) e = cudaMemset(h->trig, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(h->icount, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(h->ccount, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(h->anymark, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->icount[0], 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->icount[1], 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->mcount, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->gcount, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->lcount, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->stepno, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->cstep, 0xff, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->icnt, 0, 8 * n_domains);
     if (e == cudaSuccess) e = cudaMemset(h->runs, 0, 8);
     if (e == cudaSuccess) e = cudaMemset(h->vfx, 0, 8 * NS);
@@ -567,7 +597,22 @@ fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
     h->stepped = true;
     join_in(h);
     int64_t k = 0;
-    if (h->timing) {
+    if (!h->graphs) {
+        // direct launches; the labelling kernels return at once unless the
+        // step set the trigger
+        for (; k < nsteps; ++k) {
+            StepArgs A = step_args(h, h->cur);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (h->timing) {
+                auto ev = next_events(h);
+                e0 = ev.first;
+                e1 = ev.second;
+            }
+            h->launches += enqueue_main(h, A, e0, e1, nullptr);
+            h->launches += launch_ccl(A, ccl_args(h, 0), h->nblocks, h->vsfx, h->constp, h->ls);
+            h->cur = 1 - h->cur;
+        }
+    } else if (h->timing) {
         for (; k < nsteps; ++k) {
             st = launch_graph(h, 2);
             if (st != FSL_OK) return st;
@@ -614,6 +659,12 @@ fsl_status fsl_set_timing(fsl_domain* h, int32_t on) {
 }
 
 double fsl_stream_collide_ms(const fsl_domain* h) { return h ? h->k1_ms : 0.0; }
+
+fsl_status fsl_set_graphs(fsl_domain* h, int32_t on) {
+    if (!h) return FSL_ERR_ARG;
+    h->graphs = on != 0;
+    return FSL_OK;
+}
 
 int64_t fsl_kernel_launches(const fsl_domain* h) { return h ? h->launches : 0; }
 
@@ -761,6 +812,8 @@ fsl_status fsl_destroy(fsl_domain* h) {
     for (int k = 0; k < 2; ++k)
         for (int j = 0; j < 3; ++j)
             if (h->graph[k][j]) cudaGraphExecDestroy(h->graph[k][j]);
+    for (int k = 0; k < 2; ++k)
+        if (h->timed_src[k]) cudaGraphDestroy(h->timed_src[k]);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     if (h->ev_in) cudaEventDestroy(h->ev_in);

@@ -42,59 +42,47 @@ __device__ inline void warp_add(long long* base, int key, long long v) {
     }
 }
 
-// Append v to list for every lane with pred set, one atomic per warp.  Every
-// lane of the warp must call.
-__device__ inline void warp_append(int* list, int* count, bool pred, int v) {
-    const unsigned full = 0xffffffffu;
-    const unsigned m = __ballot_sync(full, pred);
-    if (m == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(full, base, leader);
-    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = v;
-}
-
 // ------------------------------------------------------ conversion phases
+// All four phases work on compact lists (marked cells, new interface cells,
+// interface cells), so their cost follows the interface, not the lattice.
 
-// C1 (phase A): filled interface cells claim their gas neighbours (NEWG) and
-// cancel emptied marks next to them.  First clears the marks left on the cells
-// converted in the previous step and resets the per-step counters; the rest
-// is skipped in steps without marks.
-__global__ void __launch_bounds__(FSL_BLOCK) k_convert_a(StepArgs A) {
-    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const long long nth = (long long)gridDim.x * FSL_BLOCK;
-    const int nc = *A.ccount;
-    for (long long i = g; i < nc; i += nth) A.mark[A.clist[i]] = MK_NONE;
-    const int any = *A.anymark;
+// C1 (phase A), over the marked list: a filled cell turns each gas neighbour
+// into interface (the neighbour's first filled neighbour in direction order
+// claims it, so it is listed once) and cancels the emptied marks next to it.
+__global__ void __launch_bounds__(128) k_convert_a(StepArgs A) {
     if (blockIdx.x == 0) {
-        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
-            if (A.nif[d] > 0) A.pool[d] = 0;
-            // without conversions the interface count is the one the previous
-            // step ended with
-            A.nif[d] = any ? 0 : A.icnt[d];
-            A.icnt[d] = 0;
-        }
-        if (threadIdx.x == 0) {
-            *A.trig = 0;
-            *A.icount = 0;
+        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
+        if (threadIdx.x == 0) *A.icount_next = 0;
+    }
+    const int nm = *A.mcount;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < nm; base += stride) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < nm;
+        const long long p = valid ? A.mlist[i] : 0;
+        const bool filled = valid && A.mark[p] == MK_FILLED;
+        const int d = valid ? A.blk_dom[p / FSL_BLOCK] : 0;
+        const Dom& D = A.doms[d];
+        const Cell c = make_cell(D, valid ? p : D.off);
+        for (int a = 1; a < 19; ++a) {
+            bool claim = false;
+            long long z = 0;
+            if (filled) {
+                z = c.at(cx(a), cy(a), cz(a));
+                const uint8_t tz = ctype(A.flag[z]);
+                if (tz == GAS) {
+                    if (first_marked(A, D, z, MK_FILLED) == p) {
+                        claim = true;
+                        A.mark[z] = MK_NEWG;
+                        atomicAdd((unsigned long long*)&A.nif[d], 1ull);
+                    }
+                } else if (tz == IFC && A.mark[z] == MK_EMPTIED) {
+                    A.mark[z] = MK_NONE;
+                }
+            }
+            list_append(A.glist, A.gcount, claim, (int)z);
         }
     }
-    if (!any) return;
-    const uint8_t t = ctype(A.flag[g]);
-    const uint8_t mk = A.mark[g];
-    const bool gas = (t == GAS);
-    const bool emp = (t == IFC && mk == MK_EMPTIED);
-    if (!gas && !emp) return;
-    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
-    const Cell c = make_cell(D, g);
-    bool hit = false;
-    for (int a = 1; a < 19 && !hit; ++a) {
-        const long long z = c.at(cx(a), cy(a), cz(a));
-        if (ctype(A.flag[z]) == IFC && A.mark[z] == MK_FILLED) hit = true;
-    }
-    if (hit) A.mark[g] = gas ? MK_NEWG : MK_NONE;
 }
 
 // Local test that removing the filled cell at the centre of the cube cannot
@@ -119,132 +107,148 @@ __device__ inline bool removal_is_local(unsigned fg) {
     return (targets & ~reach) == 0;
 }
 
-// C3: excess mass of converted cells (filled: m - rho, emptied: m) split
-// equally among neighbours that are interface after conversion, else pooled;
-// count of interface cells; merge / split triggers.  A filled cell leaves
-// the bubble; taking the filled cells away one at a time in index order, each
+// C3, over the marked list and the new-from-liquid list: excess mass of
+// converted cells (filled: m - rho, emptied: m) split equally among the
+// neighbours that are interface after conversion, else pooled; merge / split
+// triggers.  Taking the filled cells away one at a time in index order, each
 // removal must pass the local test with the lower-index filled cells already
 // gone and the higher-index ones still present, or the labelling runs.
-__global__ void __launch_bounds__(FSL_BLOCK) k_convert_c(StepArgs A) {
-    if (*A.anymark == 0) return;
-    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const int d = A.blk_dom[blockIdx.x];
-    const uint8_t t = ctype(A.flag[g]);
-    const uint8_t mk = A.mark[g];
-    const uint8_t nt = new_type(t, mk);
-    warp_add(A.nif, nt == IFC ? d : -1, 1);
-    const bool conv = (t == IFC && (mk == MK_FILLED || mk == MK_EMPTIED));
-    warp_append(A.clist, A.ccount, conv, (int)g);
-    const bool newl = (t == LIQ && mk == MK_NEWL);
-    if (!conv && !newl) return;
-    const Dom& D = A.doms[d];
-    const Cell c = make_cell(D, g);
-    if (conv) {
-        const double mex = (mk == MK_FILLED) ? A.m[g] - A.rhoi[g] : A.m[g];
-        int k = 0;
+__global__ void __launch_bounds__(128) k_convert_c(StepArgs A) {
+    const int nm = *A.mcount, nl = *A.lcount;
+    const int total = nm + nl;
+    const int step = *A.stepno;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const long long g = i < nm ? A.mlist[i] : A.llist[i - nm];
+        const int d = A.blk_dom[g / FSL_BLOCK];
+        const Dom& D = A.doms[d];
+        const Cell c = make_cell(D, g);
+        const uint8_t mk = A.mark[g];
+        if (i < nm) {
+            if (mk != MK_FILLED && mk != MK_EMPTIED) continue;   // emptied mark cancelled in phase A
+            const double mex = (mk == MK_FILLED) ? A.m[g] - A.rhoi[g] : A.m[g];
+            int k = 0;
+            for (int a = 1; a < 19; ++a) {
+                const long long z = c.at(cx(a), cy(a), cz(a));
+                if (new_type(ctype(A.flag[z]), A.mark[z]) == IFC) ++k;
+            }
+            if (k > 0) A.exs[g] = mex / (double)k;
+            else atomicAdd((unsigned long long*)&A.pool[d], (unsigned long long)__double2ll_rn(mex * 1099511627776.0));
+            if (mk == MK_FILLED) {
+                unsigned fgm = 0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (dx == 0 && dy == 0 && dz == 0) continue;
+                            const long long z = c.at(dx, dy, dz);
+                            const uint8_t tz = ctype(A.flag[z]), mz = A.mark[z];
+                            const uint8_t ntz = new_type(tz, mz);
+                            const bool later_filled = (tz == IFC && (mz == MK_FILLED || mz == MK_CFILLED) && z > g);
+                            if (ntz == GAS || ntz == IFC || later_filled)
+                                fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+                        }
+                if (!removal_is_local(fgm)) atomicExch(A.trig, 1);
+            }
+            A.cstep[g] = step;
+            A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
+            atomicAdd((unsigned long long*)&A.nif[d], (unsigned long long)-1LL);
+            continue;
+        }
+        // new interface cell from liquid: a neighbour of another bubble merges
+        const int b = A.id[g];
         for (int a = 1; a < 19; ++a) {
             const long long z = c.at(cx(a), cy(a), cz(a));
-            if (new_type(ctype(A.flag[z]), A.mark[z]) == IFC) ++k;
-        }
-        if (k > 0) A.exs[g] = mex / (double)k;
-        else atomicAdd((unsigned long long*)&A.pool[d], (unsigned long long)__double2ll_rn(mex * 1099511627776.0));
-        if (mk == MK_FILLED) {
-            unsigned fgm = 0;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (dx == 0 && dy == 0 && dz == 0) continue;
-                        const long long z = c.at(dx, dy, dz);
-                        const uint8_t tz = ctype(A.flag[z]), mz = A.mark[z];
-                        const uint8_t ntz = new_type(tz, mz);
-                        const bool later_filled = (tz == IFC && (mz == MK_FILLED || mz == MK_CFILLED) && z > g);
-                        if (ntz == GAS || ntz == IFC || later_filled)
-                            fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
-                    }
-            if (!removal_is_local(fgm)) atomicExch(A.trig, 1);
-        }
-        A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
-        return;
-    }
-    // new interface cell from liquid: a neighbour of another bubble merges
-    const int b = A.id[g];
-    for (int a = 1; a < 19; ++a) {
-        const long long z = c.at(cx(a), cy(a), cz(a));
-        const uint8_t ntz = new_type(ctype(A.flag[z]), A.mark[z]);
-        if ((ntz == GAS || ntz == IFC) && A.id[z] != b) {
-            atomicExch(A.trig, 1);
-            break;
+            const uint8_t ntz = new_type(ctype(A.flag[z]), A.mark[z]);
+            if ((ntz == GAS || ntz == IFC) && A.id[z] != b) {
+                atomicExch(A.trig, 1);
+                break;
+            }
         }
     }
 }
 
-// C4: receivers pull the excess shares in direction order and the pool share,
-// phi = m / rho (Eq. 9), final cell types, incremental bubble volumes (fixed
-// point, so equal to the recomputed sum), reservoir drain; the interface list
-// of the next step; the graph condition of the labelling.
-__global__ void __launch_bounds__(FSL_BLOCK) k_convert_d(StepArgs A) {
-    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const int d = A.blk_dom[blockIdx.x];
-    const uint8_t f = A.flag[g];
-    const uint8_t t = ctype(f);
-    const uint8_t mk = A.mark[g];
-    const uint8_t nt = new_type(t, mk);
-    int key = -1;
-    long long dv = 0;
-    int ckey = -1;
-    long long dc = 0;
-    if (nt == IFC) {
-        const Dom& D = A.doms[d];
-        const Cell c = make_cell(D, g);
-        double s = A.m[g];
-        for (int a = 1; a < 19; ++a) {
-            const long long z = c.at(cx(a), cy(a), cz(a));
-            const uint8_t mz = A.mark[z];
-            if (mz == MK_CFILLED || mz == MK_CEMPTIED) s = s + A.exs[z];
+// C4, over the interface list and the two new-interface lists: receivers pull
+// the excess shares of converted neighbours in direction order and the pool
+// share, phi = m / rho (Eq. 9); converted cells take their new type; bubble
+// volumes change by exact fixed-point differences; the interface list of the
+// next step; reservoir drain; the graph condition of the labelling.
+__global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
+    const int ni = *A.icount, ng = *A.gcount, nl = *A.lcount;
+    const int total = ni + ng + nl;
+    const int step = *A.stepno;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < total;
+        long long g = 0;
+        if (valid) g = i < ni ? A.ilist[i] : (i < ni + ng ? A.glist[i - ni] : A.llist[i - ni - ng]);
+        const int d = valid ? A.blk_dom[g / FSL_BLOCK] : 0;
+        int key = -1;
+        long long dv = 0;
+        int ckey = -1;
+        long long dc = 0;
+        bool keep = false;
+        if (valid) {
+            const uint8_t f = A.flag[g];
+            const uint8_t t = ctype(f);
+            const uint8_t mk = A.mark[g];
+            key = A.id[g];
+            if (t == IFC && mk == MK_CFILLED) {
+                dv = -volume_term(IFC, A.phi[g]);
+                ckey = key;
+                dc = -1;
+                A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
+                A.phi[g] = 1.0;
+                A.id[g] = -1;
+                A.mark[g] = MK_NONE;
+            } else if (t == IFC && mk == MK_CEMPTIED) {
+                dv = FSL_VOL_ONE - volume_term(IFC, A.phi[g]);
+                A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
+                A.phi[g] = 0.0;
+                A.m[g] = 0.0;
+                A.mark[g] = MK_NONE;
+            } else {
+                const Dom& D = A.doms[d];
+                const Cell c = make_cell(D, g);
+                double s = A.m[g];
+                for (int a = 1; a < 19; ++a) {
+                    const long long z = c.at(cx(a), cy(a), cz(a));
+                    if (A.cstep[z] == step) s = s + A.exs[z];
+                }
+                const long long nI = A.nif[d];
+                if (nI > 0) {
+                    const double share = ((double)A.pool[d] * 9.094947017729282379150390625e-13) / (double)nI;
+                    s = s + share;
+                }
+                const double phn = s / A.rhoi[g];
+                const long long told = volume_term(t, A.phi[g]);
+                A.m[g] = s;
+                A.phi[g] = phn;
+                if (t != IFC) A.flag[g] = (uint8_t)((f & ~K_TYPE) | IFC);
+                dv = volume_term(IFC, phn) - told;
+                if (t == LIQ) { ckey = key; dc = 1; }
+                keep = true;
+            }
         }
-        const long long nI = A.nif[d];
-        if (nI > 0) {
-            const double share = ((double)A.pool[d] * 9.094947017729282379150390625e-13) / (double)nI;
-            s = s + share;
-        }
-        const double phn = s / A.rhoi[g];
-        const long long told = volume_term(t, A.phi[g]);
-        A.m[g] = s;
-        A.phi[g] = phn;
-        if (t != IFC) A.flag[g] = (uint8_t)((f & ~K_TYPE) | IFC);
-        key = A.id[g];
-        dv = volume_term(IFC, phn) - told;
-        if (t == LIQ) { ckey = key; dc = 1; }
-        if (D.seed >= 0 && g - D.off == D.seed && key >= 0)
-            atomicAdd((unsigned long long*)&A.vxfx[key], (unsigned long long)(-D.rate_fx));
-    } else if (t == IFC && mk == MK_CFILLED) {
-        key = A.id[g];
-        dv = -volume_term(IFC, A.phi[g]);
-        ckey = key;
-        dc = -1;
-        A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
-        A.phi[g] = 1.0;
-        A.id[g] = -1;
-    } else if (t == IFC && mk == MK_CEMPTIED) {
-        const Dom& D = A.doms[d];
-        key = A.id[g];
-        dv = FSL_VOL_ONE - volume_term(IFC, A.phi[g]);
-        A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
-        A.phi[g] = 0.0;
-        A.m[g] = 0.0;
-        if (D.seed >= 0 && g - D.off == D.seed && key >= 0)
-            atomicAdd((unsigned long long*)&A.vxfx[key], (unsigned long long)(-D.rate_fx));
-    } else if (t == GAS) {
-        const Dom& D = A.doms[d];
-        if (D.seed >= 0 && g - D.off == D.seed && A.id[g] >= 0)
-            atomicAdd((unsigned long long*)&A.vxfx[A.id[g]], (unsigned long long)(-D.rate_fx));
+        warp_add(A.vfx, dv != 0 ? key : -1, dv);
+        warp_add(A.ncells, ckey, dc);
+        warp_add(A.icnt, keep ? d : -1, 1);
+        list_append(A.ilist_next, A.icount_next, keep, (int)g);
     }
-    warp_add(A.vfx, dv != 0 ? key : -1, dv);
-    warp_add(A.ncells, ckey, dc);
-    warp_add(A.icnt, nt == IFC ? d : -1, 1);
-    warp_append(A.ilist, A.icount, nt == IFC, (int)g);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *A.anymark = 0;
+        // reservoir drain of every domain whose seed cell is still gas or
+        // interface (types read through the marks, which stay consistent
+        // while other threads update the flags)
+        for (int d = 0; d < A.ndom; ++d) {
+            const Dom& D = A.doms[d];
+            if (D.seed < 0) continue;
+            const long long gs = D.off + D.seed;
+            const uint8_t nt = new_type(ctype(A.flag[gs]), A.mark[gs]);
+            const int b = A.id[gs];
+            if ((nt == GAS || nt == IFC) && b >= 0)
+                atomicAdd((unsigned long long*)&A.vxfx[b], (unsigned long long)(-D.rate_fx));
+        }
+        *A.mcount = 0;
         if (A.cond) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond, *A.trig ? 1u : 0u);
     }
 }
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_build_ilist(StepArgs A) {
     const int d = A.blk_dom[blockIdx.x];
     const bool itf = ctype(A.flag[g]) == IFC;
     warp_add(A.icnt, itf ? d : -1, 1);
-    warp_append(A.ilist, A.icount, itf, (int)g);
+    list_append(A.ilist, A.icount, itf, (int)g);
 }
 
 // --------------------------------------------- connected-component labelling
@@ -475,9 +479,9 @@ __global__ void k_export_cells(const uint8_t* flag, const double* phi, const dou
 
 // ------------------------------------------------------------ host launches
 
-void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_a<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
-void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_c<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
-void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_d<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
+void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_a<<<(unsigned)nb, 128, 0, s>>>(A); }
+void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_c<<<(unsigned)nb, 128, 0, s>>>(A); }
+void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_d<<<(unsigned)nb, 128, 0, s>>>(A); }
 void launch_build_ilist(const StepArgs& A, long long nb, cudaStream_t s) { k_build_ilist<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
 
 int launch_ccl(const StepArgs& A, const CclArgs& K, long long nb, long long* vsfx, int* constp, cudaStream_t s) {

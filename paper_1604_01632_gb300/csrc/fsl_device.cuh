@@ -79,11 +79,18 @@ struct StepArgs {
     int* trig;                  // merge/split trigger (any domain)
     int* status;
     int ndom;
-    int* ilist;                 // interface cells of the current step
+    int* ilist;                 // interface cells at the start of this step
     int* icount;
-    int* clist;                 // cells converted in the previous step (stale marks)
-    int* ccount;
-    int* anymark;               // some interface cell was marked filled / emptied
+    int* ilist_next;            // interface cells after this step's conversion (C4)
+    int* icount_next;
+    int* mlist;                 // interface cells marked filled / emptied (K1I)
+    int* mcount;
+    int* glist;                 // gas cells that become interface (phase A)
+    int* gcount;
+    int* llist;                 // liquid cells that become interface (phase B)
+    int* lcount;
+    int* cstep;                 // step number at which each cell was last converted
+    int* stepno;                // device step counter
     long long* icnt;            // per-domain interface count at the end of the step
     unsigned long long cond;    // graph conditional handle set to the trigger (0: none)
 };
@@ -108,6 +115,20 @@ __host__ __device__ inline double weight(int a) {
 }
 
 __device__ inline void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// Append v to list for every lane with pred set, one atomic per warp.  Every
+// lane of the warp must call.
+__device__ inline void list_append(int* list, int* count, bool pred, int v) {
+    const unsigned full = 0xffffffffu;
+    const unsigned m = __ballot_sync(full, pred);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(full, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
 
 // ------------------------------------------------------------ cell geometry
 
@@ -384,35 +405,58 @@ __device__ inline double phi_stencil(const uint8_t* flag, const double* phi, lon
     return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
 }
 
-// Parker-Youngs gradient of the fill level around offset (ox, oy, oz):
-// central differences over the 3x3 cross-section, weights 4 / 2 / 1.
+// The 81 cells of the 5x5x5 neighbourhood that the gradients at the cell and
+// at its six face neighbours read: the 3x3x3 cube (slots 0-26) plus, on each
+// of the six faces, the 3x3 patch two cells away (slots 27-80).
+__host__ __device__ constexpr int stencil_slot(int dx, int dy, int dz) {
+    return (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
+               ? (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+               : (dx == 2 ? 27 + (dy + 1) + 3 * (dz + 1)
+                  : dx == -2 ? 36 + (dy + 1) + 3 * (dz + 1)
+                  : dy == 2 ? 45 + (dx + 1) + 3 * (dz + 1)
+                  : dy == -2 ? 54 + (dx + 1) + 3 * (dz + 1)
+                  : dz == 2 ? 63 + (dx + 1) + 3 * (dy + 1)
+                            : 72 + (dx + 1) + 3 * (dy + 1));
+}
+
+__host__ __device__ inline void stencil_offset(int k, int& dx, int& dy, int& dz) {
+    if (k < 27) {
+        dx = k % 3 - 1; dy = (k / 3) % 3 - 1; dz = k / 9 - 1;
+        return;
+    }
+    const int f = (k - 27) / 9, r = (k - 27) % 9;
+    const int a = r % 3 - 1, b = r / 3 - 1;
+    switch (f) {
+    case 0: dx = 2; dy = a; dz = b; break;
+    case 1: dx = -2; dy = a; dz = b; break;
+    case 2: dx = a; dy = 2; dz = b; break;
+    case 3: dx = a; dy = -2; dz = b; break;
+    case 4: dx = a; dy = b; dz = 2; break;
+    default: dx = a; dy = b; dz = -2; break;
+    }
+}
+
+// Parker-Youngs gradient at offset (ox, oy, oz) from the preloaded fill levels
+// (same operations, same order as the direct form below).
 template <typename C>
-__device__ inline void py_gradient(const Stencil& s, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
-                                   C& gx, C& gy, C& gz) {
+__device__ inline void py_gradient_from(const C* ph, int ox, int oy, int oz, C& gx, C& gy, C& gz) {
     gx = (C)0; gy = (C)0; gz = (C)0;
 #pragma unroll
     for (int b = -1; b <= 1; ++b) {
 #pragma unroll
         for (int a = -1; a <= 1; ++a) {
             const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
-            const C px = (C)phi_stencil(flag, phi, s.at(ox + 1, oy + a, oz + b));
-            const C mx = (C)phi_stencil(flag, phi, s.at(ox - 1, oy + a, oz + b));
-            gx = gx + W * (px - mx);
-            const C py = (C)phi_stencil(flag, phi, s.at(ox + a, oy + 1, oz + b));
-            const C my = (C)phi_stencil(flag, phi, s.at(ox + a, oy - 1, oz + b));
-            gy = gy + W * (py - my);
-            const C pz = (C)phi_stencil(flag, phi, s.at(ox + a, oy + b, oz + 1));
-            const C mz = (C)phi_stencil(flag, phi, s.at(ox + a, oy + b, oz - 1));
-            gz = gz + W * (pz - mz);
+            gx = gx + W * (ph[stencil_slot(ox + 1, oy + a, oz + b)] - ph[stencil_slot(ox - 1, oy + a, oz + b)]);
+            gy = gy + W * (ph[stencil_slot(ox + a, oy + 1, oz + b)] - ph[stencil_slot(ox + a, oy - 1, oz + b)]);
+            gz = gz + W * (ph[stencil_slot(ox + a, oy + b, oz + 1)] - ph[stencil_slot(ox + a, oy + b, oz - 1)]);
         }
     }
 }
 
 template <typename C>
-__device__ inline void unit_normal(const Stencil& s, int ox, int oy, int oz, const uint8_t* flag, const double* phi,
-                                   C& nx, C& ny, C& nz) {
+__device__ inline void unit_normal_from(const C* ph, int ox, int oy, int oz, C& nx, C& ny, C& nz) {
     C gx, gy, gz;
-    py_gradient<C>(s, ox, oy, oz, flag, phi, gx, gy, gz);
+    py_gradient_from<C>(ph, ox, oy, oz, gx, gy, gz);
     const C q = gx * gx + gy * gy + gz * gz;
     if (q > (C)0) {
         const C len = sqrt(q);
@@ -424,16 +468,16 @@ __device__ inline void unit_normal(const Stencil& s, int ox, int oy, int oz, con
 
 // kappa = 1/2 div(n_hat), central differences (Eq. 15).
 template <typename C>
-__device__ inline C curvature(const Stencil& s, const uint8_t* flag, const double* phi) {
+__device__ inline C curvature_from(const C* ph) {
     C px, py, pz, mx, my, mz;
-    unit_normal<C>(s, 1, 0, 0, flag, phi, px, py, pz);
-    unit_normal<C>(s, -1, 0, 0, flag, phi, mx, my, mz);
+    unit_normal_from<C>(ph, 1, 0, 0, px, py, pz);
+    unit_normal_from<C>(ph, -1, 0, 0, mx, my, mz);
     const C dX = px - mx;
-    unit_normal<C>(s, 0, 1, 0, flag, phi, px, py, pz);
-    unit_normal<C>(s, 0, -1, 0, flag, phi, mx, my, mz);
+    unit_normal_from<C>(ph, 0, 1, 0, px, py, pz);
+    unit_normal_from<C>(ph, 0, -1, 0, mx, my, mz);
     const C dY = py - my;
-    unit_normal<C>(s, 0, 0, 1, flag, phi, px, py, pz);
-    unit_normal<C>(s, 0, 0, -1, flag, phi, mx, my, mz);
+    unit_normal_from<C>(ph, 0, 0, 1, px, py, pz);
+    unit_normal_from<C>(ph, 0, 0, -1, mx, my, mz);
     const C dZ = pz - mz;
     return (C)0.25 * ((dX + dY) + dZ);
 }
@@ -446,144 +490,189 @@ __device__ inline C curvature(const Stencil& s, const uint8_t* flag, const doubl
 template <typename T>
 __global__ void __launch_bounds__(128) k_stream_interface(StepArgs A) {
     using C = typename Form<T>::C;
+    if (blockIdx.x == 0) {
+        // per-step counters; the previous step's kernels are done with them
+        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
+            if (A.nif[d] > 0) A.pool[d] = 0;   // the pool was shared out last step
+            A.nif[d] = A.icnt[d];
+        }
+        if (threadIdx.x == 0) {
+            *A.stepno += 1;
+            *A.gcount = 0;
+            *A.lcount = 0;
+            *A.trig = 0;
+        }
+    }
     const int cnt = *A.icount;
     const long long S = A.stride;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
-    bool marked = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
-        const long long g = A.ilist[i];
-        const Dom& D = A.doms[A.blk_dom[g / FSL_BLOCK]];
-        const Stencil st = make_stencil(D, g);
-        C fs[19];
-#pragma unroll
-        for (int a = 0; a < 19; ++a) fs[a] = Form<T>::ld(src + (long long)a * S + g, a);
-        C rs, jsx, jsy, jsz;
-        moments<C>(fs, rs, jsx, jsy, jsz);
-        const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
-        const C kappa = curvature<C>(st, A.flag, A.phi);
-        const int b = A.id[g];
-        const double pv = b >= 0 ? bubble_pressure(A.vfx[b], A.vxfx[b], A.vsfx[b], A.constp[b]) : 1.0 / 3.0;
-        const C pg = (C)pv + (C)D.sigma2 * kappa;
-        const C rg = (C)3 * pg;
-        C fg[19];
-        feq_all<C>(rg, ugx, ugy, ugz, fg);
-        C gx, gy, gz;
-        py_gradient<C>(st, 0, 0, 0, A.flag, A.phi, gx, gy, gz);
-
-        C fin[19];
-        fin[0] = fs[0];
-#pragma unroll
-        for (int a = 1; a < 19; ++a) {
-            const int ab = opp(a);
-            const long long y = st.at(-cx(a), -cy(a), -cz(a));
-            const uint8_t ty = ctype(A.flag[y]);
-            if (ty == OBS) {
-                fin[a] = fs[ab];
-            } else if (ty == LID) {
-                const C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
-                fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
-            } else if (ty == GAS) {
-                fin[a] = (fg[a] + fg[ab]) - fs[ab];
-            } else {
-                fin[a] = Form<T>::ld(src + (long long)a * S + y, a);
-                if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
-            }
-        }
-        // mass exchange over the 18 links, in direction order (Eq. 10)
-        const double phx = A.phi[g];
-        double dm = 0.0;
-#pragma unroll
-        for (int a = 1; a < 19; ++a) {
-            const int ab = opp(a);
-            const long long z = st.at(cx(a), cy(a), cz(a));
-            const uint8_t tz = ctype(A.flag[z]);
-            if (tz == LIQ || tz == IFC) {
-                const double fz = (double)Form<T>::ld(src + (long long)ab * S + z, ab);
-                const double ex = fz - (double)fs[a];
-                if (tz == LIQ) dm = dm + ex;
-                else dm = dm + (0.5 * (phx + A.phi[z])) * ex;
-            }
-        }
-        const double mnew = A.m[g] + dm;
-        C fout[19];
-        const C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
-        if (!(rho == rho)) set_status(A.status, ST_NAN);
-#pragma unroll
-        for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
-        const double r = (double)rho;
-        A.m[g] = mnew;
-        A.rhoi[g] = r;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < cnt; base += stride) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < cnt;
+        const long long g = valid ? A.ilist[i] : 0;
         uint8_t mk = MK_NONE;
-        if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
-        else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
-        A.mark[g] = mk;
-        marked |= (mk != MK_NONE);
+        if (valid) {
+            const Dom& D = A.doms[A.blk_dom[g / FSL_BLOCK]];
+            const Stencil st = make_stencil(D, g);
+            C fs[19];
+#pragma unroll
+            for (int a = 0; a < 19; ++a) fs[a] = Form<T>::ld(src + (long long)a * S + g, a);
+            C rs, jsx, jsy, jsz;
+            moments<C>(fs, rs, jsx, jsy, jsz);
+            const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
+            // fill levels of the 81 cells the seven gradients need, loaded once
+            C ph[81];
+#pragma unroll
+            for (int k = 0; k < 81; ++k) {
+                int dx, dy, dz;
+                stencil_offset(k, dx, dy, dz);
+                ph[k] = (C)phi_stencil(A.flag, A.phi, st.at(dx, dy, dz));
+            }
+            const C kappa = curvature_from<C>(ph);
+            C gx, gy, gz;
+            py_gradient_from<C>(ph, 0, 0, 0, gx, gy, gz);
+            const int b = A.id[g];
+            const double pv = b >= 0 ? bubble_pressure(A.vfx[b], A.vxfx[b], A.vsfx[b], A.constp[b]) : 1.0 / 3.0;
+            const C pg = (C)pv + (C)D.sigma2 * kappa;
+            const C rg = (C)3 * pg;
+            C fg[19];
+            feq_all<C>(rg, ugx, ugy, ugz, fg);
+
+            C fin[19];
+            fin[0] = fs[0];
+#pragma unroll
+            for (int a = 1; a < 19; ++a) {
+                const int ab = opp(a);
+                const long long y = st.at(-cx(a), -cy(a), -cz(a));
+                const uint8_t ty = ctype(A.flag[y]);
+                if (ty == OBS) {
+                    fin[a] = fs[ab];
+                } else if (ty == LID) {
+                    const C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
+                    fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
+                } else if (ty == GAS) {
+                    fin[a] = (fg[a] + fg[ab]) - fs[ab];
+                } else {
+                    fin[a] = Form<T>::ld(src + (long long)a * S + y, a);
+                    if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
+                }
+            }
+            // mass exchange over the 18 links, in direction order (Eq. 10)
+            const double phx = A.phi[g];
+            double dm = 0.0;
+#pragma unroll
+            for (int a = 1; a < 19; ++a) {
+                const int ab = opp(a);
+                const long long z = st.at(cx(a), cy(a), cz(a));
+                const uint8_t tz = ctype(A.flag[z]);
+                if (tz == LIQ || tz == IFC) {
+                    const double fz = (double)Form<T>::ld(src + (long long)ab * S + z, ab);
+                    const double ex = fz - (double)fs[a];
+                    if (tz == LIQ) dm = dm + ex;
+                    else dm = dm + (0.5 * (phx + A.phi[z])) * ex;
+                }
+            }
+            const double mnew = A.m[g] + dm;
+            C fout[19];
+            const C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+            if (!(rho == rho)) set_status(A.status, ST_NAN);
+#pragma unroll
+            for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
+            const double r = (double)rho;
+            A.m[g] = mnew;
+            A.rhoi[g] = r;
+            if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
+            else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
+            A.mark[g] = mk;
+        }
+        list_append(A.mlist, A.mcount, mk != MK_NONE, (int)g);
     }
-    if (__any_sync(0xffffffffu, marked) && (threadIdx.x & 31) == 0) *A.anymark = 1;
 }
 
-// C2 (conversion phase B): remaining emptied cells turn their liquid
-// neighbours into interface (bubble of the first emptied neighbour in
-// direction order, m = rho); new interface cells from gas get f = f_eq of the
-// mean density and velocity of their liquid / non-emptied interface
-// neighbours, m = 0.  Skipped in steps without marks.
+// First neighbour of cell z (direction order) that is an interface cell
+// carrying mark `want`, or -1.
+__device__ inline long long first_marked(const StepArgs& A, const Dom& D, long long z, uint8_t want) {
+    const Cell c = make_cell(D, z);
+    for (int a = 1; a < 19; ++a) {
+        const long long w = c.at(cx(a), cy(a), cz(a));
+        if (ctype(A.flag[w]) == IFC && A.mark[w] == want) return w;
+    }
+    return -1;
+}
+
+// C2 (conversion phase B), over the marked list and the new-from-gas list.
+// An emptied cell that kept its mark turns each liquid neighbour into
+// interface when it is that neighbour's first emptied neighbour in direction
+// order (so each new cell is claimed once, by the bubble of its first emptied
+// neighbour; m = rho of its own PDFs).  A new interface cell from gas gets
+// f = f_eq of the mean density and velocity of its liquid and non-emptied
+// interface neighbours, m = 0.
 template <typename T>
-__global__ void __launch_bounds__(FSL_BLOCK) k_convert_b(StepArgs A) {
+__global__ void __launch_bounds__(128) k_convert_b(StepArgs A) {
     using C = typename Form<T>::C;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *A.ccount = 0;   // C1 has cleared the stale marks
-    if (*A.anymark == 0) return;
-    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const uint8_t t = ctype(A.flag[g]);
-    if (t != LIQ && t != GAS) return;
-    if (t == GAS && A.mark[g] != MK_NEWG) return;
-    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
-    const Cell c = make_cell(D, g);
+    const int nm = *A.mcount, ng = *A.gcount;
+    const int total = nm + ng;
     const long long S = A.stride;
     T* f = (T*)A.fdst;
-    if (t == LIQ) {
-        int best = -1;
-        for (int a = 1; a < 19 && best < 0; ++a) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < total;
+        long long p = 0;
+        if (valid) p = i < nm ? A.mlist[i] : A.glist[i - nm];
+        const int d = valid ? A.blk_dom[p / FSL_BLOCK] : 0;
+        const Dom& D = A.doms[d];
+        const bool emptied = valid && i < nm && A.mark[p] == MK_EMPTIED;
+        const Cell c = make_cell(D, valid ? p : D.off);
+        for (int a = 1; a < 19; ++a) {
+            bool claim = false;
+            long long z = 0;
+            if (emptied) {
+                z = c.at(cx(a), cy(a), cz(a));
+                if (ctype(A.flag[z]) == LIQ && first_marked(A, D, z, MK_EMPTIED) == p) {
+                    claim = true;
+                    double r = (double)Form<T>::ld(f + z, 0);
+                    for (int q = 1; q < 19; ++q) r = r + (double)Form<T>::ld(f + (long long)q * S + z, q);
+                    A.mark[z] = MK_NEWL;
+                    A.id[z] = A.id[p];
+                    A.m[z] = r;
+                    A.rhoi[z] = r;
+                    atomicAdd((unsigned long long*)&A.nif[d], 1ull);
+                }
+            }
+            list_append(A.llist, A.lcount, claim, (int)z);
+        }
+        if (!valid || i < nm) continue;
+        // new interface cell from gas
+        C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
+        int cnt = 0;
+        for (int a = 1; a < 19; ++a) {
             const long long z = c.at(cx(a), cy(a), cz(a));
-            if (ctype(A.flag[z]) == IFC && A.mark[z] == MK_EMPTIED) best = A.id[z];
-        }
-        if (best >= 0) {
-            double r = (double)Form<T>::ld(f + g, 0);
-            for (int a = 1; a < 19; ++a) r = r + (double)Form<T>::ld(f + (long long)a * S + g, a);
-            A.mark[g] = MK_NEWL;
-            A.id[g] = best;
-            A.m[g] = r;
-            A.rhoi[g] = r;
-        }
-        return;
-    }
-    // new interface cell from gas
-    C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
-    int cnt = 0;
-    for (int a = 1; a < 19; ++a) {
-        const long long z = c.at(cx(a), cy(a), cz(a));
-        const uint8_t tz = ctype(A.flag[z]);
-        if (tz == LIQ || (tz == IFC && A.mark[z] != MK_EMPTIED)) {
-            C fo[19];
+            const uint8_t tz = ctype(A.flag[z]);
+            if (tz == LIQ || (tz == IFC && A.mark[z] != MK_EMPTIED)) {
+                C fo[19];
 #pragma unroll
-            for (int q = 0; q < 19; ++q) fo[q] = Form<T>::ld(f + (long long)q * S + z, q);
-            C r, jx, jy, jz;
-            moments<C>(fo, r, jx, jy, jz);
-            sr = sr + r;
-            sux = sux + jx / r;
-            suy = suy + jy / r;
-            suz = suz + jz / r;
-            ++cnt;
+                for (int q = 0; q < 19; ++q) fo[q] = Form<T>::ld(f + (long long)q * S + z, q);
+                C r, jx, jy, jz;
+                moments<C>(fo, r, jx, jy, jz);
+                sr = sr + r;
+                sux = sux + jx / r;
+                suy = suy + jy / r;
+                suz = suz + jz / r;
+                ++cnt;
+            }
         }
-    }
-    C rbar = sr / (C)cnt;
-    C ux = sux / (C)cnt, uy = suy / (C)cnt, uz = suz / (C)cnt;
-    C fe[19];
-    feq_all<C>(rbar, ux, uy, uz, fe);
+        const C rbar = sr / (C)cnt;
+        const C ux = sux / (C)cnt, uy = suy / (C)cnt, uz = suz / (C)cnt;
+        C fe[19];
+        feq_all<C>(rbar, ux, uy, uz, fe);
 #pragma unroll
-    for (int q = 0; q < 19; ++q) Form<T>::st(f + (long long)q * S + g, q, fe[q]);
-    A.m[g] = 0.0;
-    A.rhoi[g] = (double)rbar;
+        for (int q = 0; q < 19; ++q) Form<T>::st(f + (long long)q * S + p, q, fe[q]);
+        A.m[p] = 0.0;
+        A.rhoi[p] = (double)rbar;
+    }
 }
 
 // Initial state: validate the closed interface layer, f = f_eq(rho, u),
@@ -665,7 +754,7 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         k_stream_interface<T><<<(unsigned)ifb, 128, 0, s>>>(A);                                             \
     }                                                                                                        \
     template <> void launch_convert_b<T>(const StepArgs& A, long long nb, cudaStream_t s) {                  \
-        k_convert_b<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                               \
+        k_convert_b<T><<<(unsigned)nb, 128, 0, s>>>(A);                                                     \
     }                                                                                                        \
     template <> void launch_init_state<T>(const StepArgs& A, int d, int n, const uint8_t* fl,                \
                                           const double* fill, const double* rho, const double* u,            \

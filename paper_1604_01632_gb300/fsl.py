@@ -27,7 +27,7 @@ FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.flo
 # names the library must export (checked by the CPU test suite)
 EXPORTS = ["fsl_create", "fsl_init_geometry", "fsl_set_bubble_source", "fsl_step", "fsl_sync", "fsl_bubbles",
            "fsl_fields", "fsl_destroy", "fsl_last_error", "fsl_kernel_launches", "fsl_set_timing",
-           "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs"]
+           "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs"]
 
 
 class FslError(RuntimeError):
@@ -90,6 +90,8 @@ def load_library():
     L.fsl_set_timing.argtypes = [vp, i32]
     L.fsl_stream_collide_ms.restype = dbl
     L.fsl_stream_collide_ms.argtypes = [vp]
+    L.fsl_set_graphs.restype = i32
+    L.fsl_set_graphs.argtypes = [vp, i32]
     L.fsl_labelling_runs.restype = i64
     L.fsl_labelling_runs.argtypes = [vp]
     L.fsl_cell_counts.restype = i32
@@ -241,6 +243,9 @@ class Simulation:
 
     def set_timing(self, on: bool):
         self._check(self.L.fsl_set_timing(self._h, 1 if on else 0))
+
+    def set_graphs(self, on: bool):
+        self._check(self.L.fsl_set_graphs(self._h, 1 if on else 0))
 
     def stream_collide_ms(self) -> float:
         return float(self.L.fsl_stream_collide_ms(self._h))
