@@ -31,6 +31,10 @@ struct fsl_domain {
     cudaStream_t user = nullptr;  // caller's stream (may be the legacy default)
     cudaStream_t ls = nullptr;    // library stream (capturable)
     cudaStream_t ls2 = nullptr;   // second stream, used only to capture the labelling body
+    cudaStream_t ls3 = nullptr;   // interface kernels, concurrent with the liquid kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    void* nrm = nullptr;
+    int nrm_cap = 0;
     int ifblocks = 1216;          // grid of the interface kernel (8 blocks of 128 per SM)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
@@ -156,6 +160,8 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.cstep = h->cstep;
     A.stepno = h->stepno;
     A.icnt = h->icnt;
+    A.nrm = h->nrm;
+    A.nrm_cap = h->nrm_cap;
     A.cond = 0;
     return A;
 }
@@ -189,10 +195,10 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
 
 void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st); break;
-    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st); break;
-    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st); break;
-    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st); break;
+    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
+    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
+    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
+    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
     }
 }
 
@@ -392,6 +398,9 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         D.sigma2 = 2.0 * p.sigma;
         for (int k = 0; k < 3; ++k) { D.g[k] = p.gravity[k]; D.lid[k] = p.lid_velocity[k]; }
         D.eps = p.eps;
+        div_magic(p.nx, D.mgx, D.shx);
+        div_magic(p.ny, D.mgy, D.shy);
+        D.has_force = (p.gravity[0] != 0.0 || p.gravity[1] != 0.0 || p.gravity[2] != 0.0) ? 1 : 0;
         h->hdoms.push_back(D);
         long long padded = (n + FSL_BLOCK - 1) / FSL_BLOCK * FSL_BLOCK;
         for (long long b = 0; b < padded / FSL_BLOCK; ++b) h->blk_dom.push_back(d);
@@ -412,6 +421,9 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e != cudaSuccess) { fsl_status st = cuda_fail(h, e, "tables"); delete h; return st; }
     e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ls2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ls3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -456,6 +468,10 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->cstep, 4 * N);
     AL(h->stepno, sizeof(int));
     AL(h->icnt, 8 * n_domains);
+    // interface-list entries whose normals fit in the scratch (one eighth of
+    // the lattice, at least 64 Ki); more interface cells latch TABLE_FULL
+    h->nrm_cap = (int)std::min<long long>(h->stride, std::max<long long>(65536, h->stride / 8));
+    AL(h->nrm, (size_t)h->nrm_cap * 21 * (precision == FSL_P_FP64 ? 8 : 4));
     AL(h->lab, 4 * N);
     AL(h->aux, 4 * N);
     AL(h->hkeys, 8 * (size_t)hc);
@@ -820,6 +836,9 @@ fsl_status fsl_destroy(fsl_domain* h) {
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ls) cudaStreamDestroy(h->ls);
     if (h->ls2) cudaStreamDestroy(h->ls2);
+    if (h->ls3) cudaStreamDestroy(h->ls3);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return FSL_OK;
 }

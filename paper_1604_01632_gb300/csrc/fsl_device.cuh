@@ -53,7 +53,30 @@ struct Dom {
     double g[3];                // gravity
     double eps;                 // conversion threshold
     double lid[3];              // lid velocity
+    unsigned mgx, mgy;          // x = l - nx*(l/nx) etc. by multiply-high: l/nx = umulhi(l, mgx) >> shx
+    int shx, shy;               // (shift -1: the divisor is 1)
+    int has_force;              // gravity is not zero
 };
+
+// Invariant-divisor division for 0 <= n < 2^31: with s = ceil(log2 d) and
+// m = ceil(2^(31+s) / d) < 2^32, n / d = (n * m) >> (31 + s) (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994).
+__host__ inline void div_magic(int d, unsigned& m, int& sh) {
+    int s = 0;
+    while ((1LL << s) < d) ++s;
+    const unsigned long long num = 1ULL << (31 + s);
+    m = (unsigned)((num + (unsigned long long)d - 1) / (unsigned long long)d);
+    sh = s - 1;
+}
+__device__ inline int fast_div(int n, unsigned m, int sh) {
+    return sh < 0 ? n : (int)(__umulhi((unsigned)n, m) >> sh);
+}
+__device__ inline void local_xyz(const Dom& D, int l, int& x, int& y, int& z) {
+    const int q = fast_div(l, D.mgx, D.shx);
+    x = l - q * D.nx;
+    z = fast_div(q, D.mgy, D.shy);
+    y = q - z * D.ny;
+}
 
 // Everything a step kernel needs, passed by value.
 struct StepArgs {
@@ -92,6 +115,8 @@ struct StepArgs {
     int* cstep;                 // step number at which each cell was last converted
     int* stepno;                // device step counter
     long long* icnt;            // per-domain interface count at the end of the step
+    void* nrm;                  // per interface-list entry: gradient + six normals (21 values)
+    int nrm_cap;                // list entries nrm can hold
     unsigned long long cond;    // graph conditional handle set to the trigger (0: none)
 };
 
@@ -155,12 +180,8 @@ struct Cell {
 
 __device__ inline Cell make_cell(const Dom& D, long long g) {
     Cell c;
-    int l = (int)(g - D.off);
     c.nx = D.nx; c.ny = D.ny; c.nz = D.nz; c.off = D.off;
-    c.x = l % D.nx;
-    int r = l / D.nx;
-    c.y = r % D.ny;
-    c.z = r / D.ny;
+    local_xyz(D, (int)(g - D.off), c.x, c.y, c.z);
     return c;
 }
 
@@ -231,40 +252,65 @@ __device__ inline void feq_all(C rho, C ux, C uy, C uz, C* out) {
 }
 
 // Two-relaxation-time collision with Guo forcing (Eq. 6); returns rho.
-template <typename C>
+// Without a force every forcing term is an exact zero, so the FORCE = false
+// form drops them (same results).  The FP32 form multiplies by 1/rho.
+template <typename C, bool FORCE>
 __device__ inline C collide(const C* fin, C* fout, C omp, C omm, C gx, C gy, C gz) {
     C rho, jx, jy, jz;
     moments<C>(fin, rho, jx, jy, jz);
-    C Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
-    C ux = (jx + (C)0.5 * Fx) / rho;
-    C uy = (jy + (C)0.5 * Fy) / rho;
-    C uz = (jz + (C)0.5 * Fz) / rho;
-    C usq = ux * ux + uy * uy + uz * uz;
-    C uF = ux * Fx + uy * Fy + uz * Fz;
-    C cp = (C)1 - (C)0.5 * omp, cm = (C)1 - (C)0.5 * omm;
-    C feq0 = ((C)weight(0) * rho) * ((C)1 - (C)1.5 * usq);
-    C S0 = (C)weight(0) * ((C)-3 * uF);
-    fout[0] = (fin[0] - omp * (fin[0] - feq0)) + cp * S0;
+    C Fx = (C)0, Fy = (C)0, Fz = (C)0;
+    C ux, uy, uz;
+    if constexpr (FORCE) {
+        Fx = rho * gx; Fy = rho * gy; Fz = rho * gz;
+        jx = jx + (C)0.5 * Fx;
+        jy = jy + (C)0.5 * Fy;
+        jz = jz + (C)0.5 * Fz;
+    }
+    if constexpr (sizeof(C) == 4) {
+        const C ir = (C)1 / rho;
+        ux = jx * ir; uy = jy * ir; uz = jz * ir;
+    } else {
+        ux = jx / rho; uy = jy / rho; uz = jz / rho;
+    }
+    const C usq = ux * ux + uy * uy + uz * uz;
+    const C cp = (C)1 - (C)0.5 * omp, cm = (C)1 - (C)0.5 * omm;
+    const C feq0 = ((C)weight(0) * rho) * ((C)1 - (C)1.5 * usq);
+    fout[0] = fin[0] - omp * (fin[0] - feq0);
+    C uF = (C)0;
+    if constexpr (FORCE) {
+        uF = ux * Fx + uy * Fy + uz * Fz;
+        const C S0 = (C)weight(0) * ((C)-3 * uF);
+        fout[0] = fout[0] + cp * S0;
+    }
 #pragma unroll
     for (int a = 1; a < 19; a += 2) {
         const int b = a + 1;
-        C w = (C)weight(a);
-        C cu = cdot<C>(a, ux, uy, uz);
-        C cF = cdot<C>(a, Fx, Fy, Fz);
-        C wr = w * rho;
-        C feqp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * usq);
-        C feqm = wr * ((C)3 * cu);
-        C fp = (C)0.5 * (fin[a] + fin[b]);
-        C fm = (C)0.5 * (fin[a] - fin[b]);
-        C Sp = w * (((C)9 * cu) * cF - (C)3 * uF);
-        C Sm = w * ((C)3 * cF);
-        C A = omp * (fp - feqp);
-        C B = omm * (fm - feqm);
-        C sp = cp * Sp, sm = cm * Sm;
-        fout[a] = (((fin[a] - A) - B) + sp) + sm;
-        fout[b] = (((fin[b] - A) + B) + sp) - sm;
+        const C w = (C)weight(a);
+        const C cu = cdot<C>(a, ux, uy, uz);
+        const C wr = w * rho;
+        const C feqp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * usq);
+        const C feqm = wr * ((C)3 * cu);
+        const C fp = (C)0.5 * (fin[a] + fin[b]);
+        const C fm = (C)0.5 * (fin[a] - fin[b]);
+        const C A = omp * (fp - feqp);
+        const C B = omm * (fm - feqm);
+        fout[a] = (fin[a] - A) - B;
+        fout[b] = (fin[b] - A) + B;
+        if constexpr (FORCE) {
+            const C cF = cdot<C>(a, Fx, Fy, Fz);
+            const C Sp = w * (((C)9 * cu) * cF - (C)3 * uF);
+            const C Sm = w * ((C)3 * cF);
+            const C sp = cp * Sp, sm = cm * Sm;
+            fout[a] = (fout[a] + sp) + sm;
+            fout[b] = (fout[b] + sp) - sm;
+        }
     }
     return rho;
+}
+
+template <typename C>
+__device__ inline C collide_any(bool force, const C* fin, C* fout, C omp, C omm, C gx, C gy, C gz) {
+    return force ? collide<C, true>(fin, fout, omp, omm, gx, gy, gz) : collide<C, false>(fin, fout, omp, omm, gx, gy, gz);
 }
 
 // --------------------------------------------------------- free surface
@@ -311,9 +357,8 @@ struct Pull {
 __device__ inline Pull make_pull(const Dom& D, long long g) {
     Pull p;
     p.g = g;
-    const int l = (int)(g - D.off);
-    const int x = l % D.nx, r = l / D.nx;
-    const int y = r % D.ny, z = r / D.ny;
+    int x, y, z;
+    local_xyz(D, (int)(g - D.off), x, y, z);
     const int sy = D.nx, sz = D.nx * D.ny;
     p.ox[0] = x == 0 ? D.nx - 1 : -1;
     p.ox[1] = 0;
@@ -363,7 +408,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_stream_liquid(StepArgs A) {
         }
     }
     C fout[19];
-    C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+    C rho = collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
     if (!(rho == rho)) set_status(A.status, ST_NAN);
 #pragma unroll
     for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
@@ -380,16 +425,23 @@ struct Stencil {
     }
 };
 
+__device__ inline int wrap2(int v, int n) {   // v in [-2, n+1]
+    v = v < 0 ? v + n : v;
+    v = v < 0 ? v + n : v;
+    v = v >= n ? v - n : v;
+    v = v >= n ? v - n : v;
+    return v;
+}
+
 __device__ inline Stencil make_stencil(const Dom& D, long long g) {
     Stencil s;
-    const int l = (int)(g - D.off);
-    const int x = l % D.nx, r = l / D.nx;
-    const int y = r % D.ny, z = r / D.ny;
+    int x, y, z;
+    local_xyz(D, (int)(g - D.off), x, y, z);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        s.X[k] = ((x + k - 2) % D.nx + D.nx) % D.nx;
-        s.Y[k] = ((y + k - 2) % D.ny + D.ny) % D.ny;
-        s.Z[k] = ((z + k - 2) % D.nz + D.nz) % D.nz;
+        s.X[k] = wrap2(x + k - 2, D.nx);
+        s.Y[k] = wrap2(y + k - 2, D.ny);
+        s.Z[k] = wrap2(z + k - 2, D.nz);
     }
     s.nx = D.nx;
     s.nxy = (long long)D.nx * D.ny;
@@ -405,81 +457,57 @@ __device__ inline double phi_stencil(const uint8_t* flag, const double* phi, lon
     return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
 }
 
-// The 81 cells of the 5x5x5 neighbourhood that the gradients at the cell and
-// at its six face neighbours read: the 3x3x3 cube (slots 0-26) plus, on each
-// of the six faces, the 3x3 patch two cells away (slots 27-80).
-__host__ __device__ constexpr int stencil_slot(int dx, int dy, int dz) {
-    return (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
-               ? (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
-               : (dx == 2 ? 27 + (dy + 1) + 3 * (dz + 1)
-                  : dx == -2 ? 36 + (dy + 1) + 3 * (dz + 1)
-                  : dy == 2 ? 45 + (dx + 1) + 3 * (dz + 1)
-                  : dy == -2 ? 54 + (dx + 1) + 3 * (dz + 1)
-                  : dz == 2 ? 63 + (dx + 1) + 3 * (dy + 1)
-                            : 72 + (dx + 1) + 3 * (dy + 1));
-}
-
-__host__ __device__ inline void stencil_offset(int k, int& dx, int& dy, int& dz) {
-    if (k < 27) {
-        dx = k % 3 - 1; dy = (k / 3) % 3 - 1; dz = k / 9 - 1;
+// K1N: for every interface cell, the Parker-Youngs gradient of the fill level
+// at the cell (point 0) and the unit normals n_hat = -g/|g| at its six face
+// neighbours (points 1-6: +x, -x, +y, -y, +z, -z); seven threads per cell,
+// each loading the 27 fill levels around its point once.  Results go to
+// nrm[21 * list index + 3 * point + component].
+template <typename C>
+__global__ void __launch_bounds__(128) k_surface_normals(StepArgs A) {
+    const int cnt = *A.icount;
+    if (cnt > A.nrm_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(A.status, ST_TABLE_FULL);
         return;
     }
-    const int f = (k - 27) / 9, r = (k - 27) % 9;
-    const int a = r % 3 - 1, b = r / 3 - 1;
-    switch (f) {
-    case 0: dx = 2; dy = a; dz = b; break;
-    case 1: dx = -2; dy = a; dz = b; break;
-    case 2: dx = a; dy = 2; dz = b; break;
-    case 3: dx = a; dy = -2; dz = b; break;
-    case 4: dx = a; dy = b; dz = 2; break;
-    default: dx = a; dy = b; dz = -2; break;
-    }
-}
-
-// Parker-Youngs gradient at offset (ox, oy, oz) from the preloaded fill levels
-// (same operations, same order as the direct form below).
-template <typename C>
-__device__ inline void py_gradient_from(const C* ph, int ox, int oy, int oz, C& gx, C& gy, C& gz) {
-    gx = (C)0; gy = (C)0; gz = (C)0;
+    C* nrm = (C*)A.nrm;
+    const long long total = 7LL * cnt;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const int i = (int)(t / 7), j = (int)(t - 7LL * (t / 7));
+        const long long g = A.ilist[i];
+        const Dom& D = A.doms[A.blk_dom[g / FSL_BLOCK]];
+        const Stencil st = make_stencil(D, g);
+        const int ox = j == 1 ? 1 : (j == 2 ? -1 : 0);
+        const int oy = j == 3 ? 1 : (j == 4 ? -1 : 0);
+        const int oz = j == 5 ? 1 : (j == 6 ? -1 : 0);
+        C ph[27];
 #pragma unroll
-    for (int b = -1; b <= 1; ++b) {
+        for (int k = 0; k < 27; ++k)
+            ph[k] = (C)phi_stencil(A.flag, A.phi, st.at(ox + k % 3 - 1, oy + (k / 3) % 3 - 1, oz + k / 9 - 1));
+        C gx = (C)0, gy = (C)0, gz = (C)0;
 #pragma unroll
-        for (int a = -1; a <= 1; ++a) {
-            const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
-            gx = gx + W * (ph[stencil_slot(ox + 1, oy + a, oz + b)] - ph[stencil_slot(ox - 1, oy + a, oz + b)]);
-            gy = gy + W * (ph[stencil_slot(ox + a, oy + 1, oz + b)] - ph[stencil_slot(ox + a, oy - 1, oz + b)]);
-            gz = gz + W * (ph[stencil_slot(ox + a, oy + b, oz + 1)] - ph[stencil_slot(ox + a, oy + b, oz - 1)]);
+        for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+            for (int a = -1; a <= 1; ++a) {
+                const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
+                gx = gx + W * (ph[2 + 3 * (a + 1) + 9 * (b + 1)] - ph[0 + 3 * (a + 1) + 9 * (b + 1)]);
+                gy = gy + W * (ph[(a + 1) + 3 * 2 + 9 * (b + 1)] - ph[(a + 1) + 3 * 0 + 9 * (b + 1)]);
+                gz = gz + W * (ph[(a + 1) + 3 * (b + 1) + 9 * 2] - ph[(a + 1) + 3 * (b + 1) + 9 * 0]);
+            }
+        }
+        C* out = nrm + (long long)i * 21 + 3 * j;
+        if (j == 0) {
+            out[0] = gx; out[1] = gy; out[2] = gz;
+        } else {
+            const C q = gx * gx + gy * gy + gz * gz;
+            if (q > (C)0) {
+                const C len = sqrt(q);
+                out[0] = -(gx / len); out[1] = -(gy / len); out[2] = -(gz / len);
+            } else {
+                out[0] = (C)0; out[1] = (C)0; out[2] = (C)0;
+            }
         }
     }
-}
-
-template <typename C>
-__device__ inline void unit_normal_from(const C* ph, int ox, int oy, int oz, C& nx, C& ny, C& nz) {
-    C gx, gy, gz;
-    py_gradient_from<C>(ph, ox, oy, oz, gx, gy, gz);
-    const C q = gx * gx + gy * gy + gz * gz;
-    if (q > (C)0) {
-        const C len = sqrt(q);
-        nx = -(gx / len); ny = -(gy / len); nz = -(gz / len);
-    } else {
-        nx = (C)0; ny = (C)0; nz = (C)0;
-    }
-}
-
-// kappa = 1/2 div(n_hat), central differences (Eq. 15).
-template <typename C>
-__device__ inline C curvature_from(const C* ph) {
-    C px, py, pz, mx, my, mz;
-    unit_normal_from<C>(ph, 1, 0, 0, px, py, pz);
-    unit_normal_from<C>(ph, -1, 0, 0, mx, my, mz);
-    const C dX = px - mx;
-    unit_normal_from<C>(ph, 0, 1, 0, px, py, pz);
-    unit_normal_from<C>(ph, 0, -1, 0, mx, my, mz);
-    const C dY = py - my;
-    unit_normal_from<C>(ph, 0, 0, 1, px, py, pz);
-    unit_normal_from<C>(ph, 0, 0, -1, mx, my, mz);
-    const C dZ = pz - mz;
-    return (C)0.25 * ((dX + dY) + dZ);
 }
 
 // K1I: interface cells, from the list of interface cells built at the end of
@@ -522,17 +550,14 @@ __global__ void __launch_bounds__(128) k_stream_interface(StepArgs A) {
             C rs, jsx, jsy, jsz;
             moments<C>(fs, rs, jsx, jsy, jsz);
             const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
-            // fill levels of the 81 cells the seven gradients need, loaded once
-            C ph[81];
-#pragma unroll
-            for (int k = 0; k < 81; ++k) {
-                int dx, dy, dz;
-                stencil_offset(k, dx, dy, dz);
-                ph[k] = (C)phi_stencil(A.flag, A.phi, st.at(dx, dy, dz));
-            }
-            const C kappa = curvature_from<C>(ph);
-            C gx, gy, gz;
-            py_gradient_from<C>(ph, 0, 0, 0, gx, gy, gz);
+            // gradient at the cell and unit normals at its six face neighbours
+            // (k_surface_normals); kappa = 1/2 div(n_hat) (Eq. 15)
+            const C* nr = (const C*)A.nrm + (long long)i * 21;
+            const C gx = nr[0], gy = nr[1], gz = nr[2];
+            const C dX = nr[3 * 1 + 0] - nr[3 * 2 + 0];
+            const C dY = nr[3 * 3 + 1] - nr[3 * 4 + 1];
+            const C dZ = nr[3 * 5 + 2] - nr[3 * 6 + 2];
+            const C kappa = (C)0.25 * ((dX + dY) + dZ);
             const int b = A.id[g];
             const double pv = b >= 0 ? bubble_pressure(A.vfx[b], A.vxfx[b], A.vsfx[b], A.constp[b]) : 1.0 / 3.0;
             const C pg = (C)pv + (C)D.sigma2 * kappa;
@@ -576,7 +601,7 @@ __global__ void __launch_bounds__(128) k_stream_interface(StepArgs A) {
             }
             const double mnew = A.m[g] + dm;
             C fout[19];
-            const C rho = collide<C>(fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+            const C rho = collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
             if (!(rho == rho)) set_status(A.status, ST_NAN);
 #pragma unroll
             for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
@@ -741,7 +766,8 @@ __global__ void k_export_pdf(const T* f, long long S, long long off, int n, doub
 }
 
 // Launch helpers instantiated once per storage form.
-template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, cudaStream_t s);
+template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, cudaStream_t s,
+                                         cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
 template <typename T> void launch_convert_b(const StepArgs& A, long long nblocks, cudaStream_t s);
 template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
                                              const double* rho, const double* u, cudaStream_t s);
@@ -749,9 +775,16 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
                                              double* rho, double* u, cudaStream_t s);
 
 #define FSL_INSTANTIATE_FORM(T)                                                                              \
-    template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, cudaStream_t s) {            \
+    template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, cudaStream_t s,               \
+                                      cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {                 \
+        /* liquid cells on s, interface cells on s2 at the same time (disjoint outputs) */                  \
+        cudaEventRecord(fork, s);                                                                            \
+        cudaStreamWaitEvent(s2, fork, 0);                                                                    \
+        k_surface_normals<typename Form<T>::C><<<(unsigned)ifb, 128, 0, s2>>>(A);                           \
+        k_stream_interface<T><<<(unsigned)ifb, 128, 0, s2>>>(A);                                            \
         k_stream_liquid<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                           \
-        k_stream_interface<T><<<(unsigned)ifb, 128, 0, s>>>(A);                                             \
+        cudaEventRecord(join, s2);                                                                           \
+        cudaStreamWaitEvent(s, join, 0);                                                                     \
     }                                                                                                        \
     template <> void launch_convert_b<T>(const StepArgs& A, long long nb, cudaStream_t s) {                  \
         k_convert_b<T><<<(unsigned)nb, 128, 0, s>>>(A);                                                     \
