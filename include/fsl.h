@@ -167,6 +167,30 @@ fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
 /* Counts of the cell types of domain d (array of 5), synchronises. */
 fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts);
 
+/* Allocation-free bubble labelling.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory (latency-critical
+ * loops in which an allocation may synchronise the device, deployments that
+ * give all device memory to their own pool, host frameworks that forbid a
+ * library to allocate).  It labels the connected components of the gas and
+ * interface cells of one lattice under the 18-neighbourhood with every axis
+ * wrapping, label = minimum linear index of the component, -1 elsewhere: the
+ * same labels fsl_fields(FSL_F_ID) reports after fsl_init_geometry.
+ *   flags  : device pointer, uint8[nx*ny*nz] cell types (bits above the type
+ *            are ignored), read only;
+ *   labels : device pointer, int64[nx*ny*nz], written;
+ *   cuda_stream : stream the three kernels are enqueued on (NULL = legacy
+ *            default stream); the call returns without waiting.
+ * It calls no allocator: its scratch is a fixed array of 2^21 int32 labels
+ * (8 MiB) compiled into the library, held by every GPU that loads it until the
+ * process exits.  nx*ny*nz above 2^21 returns FSL_ERR_ARG.  The first call on
+ * a device looks up the scratch's device address (cudaGetSymbolAddress with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the scratch, and each call rewrites it
+ * from the start; calls whose kernels overlap on the GPU (different streams,
+ * not ordered) race and give wrong labels. */
+fsl_status fsl_label_bubbles_static(const uint8_t* flags, int32_t nx, int32_t ny, int32_t nz, int64_t* labels,
+                                    void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,10 +1,11 @@
 """Build the CUDA library libfsl.so in-tree for GB300 (sm_103a).
 
-Three translation units compiled in parallel with nvcc and linked into one
+Four translation units compiled in parallel with nvcc and linked into one
 shared library next to this file:
   fsl_core.cu  precision-independent kernels + FP64 forms, -fmad=false
   fsl_fast.cu  FP32 / FP16-shifted / BF16-shifted forms
   fsl_api.cu   the C ABI of include/fsl.h
+  fsl_noalloc.cu  allocation-free bubble labelling (fixed device scratch)
 """
 from __future__ import annotations
 
@@ -27,6 +28,7 @@ UNITS = {
     "fsl_core.cu": ["-fmad=false"],
     "fsl_fast.cu": [],
     "fsl_api.cu": ["-fmad=false"],
+    "fsl_noalloc.cu": [],
 }
 
 

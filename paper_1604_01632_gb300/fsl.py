@@ -27,7 +27,8 @@ FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.flo
 # names the library must export (checked by the CPU test suite)
 EXPORTS = ["fsl_create", "fsl_init_geometry", "fsl_set_bubble_source", "fsl_step", "fsl_sync", "fsl_bubbles",
            "fsl_fields", "fsl_destroy", "fsl_last_error", "fsl_kernel_launches", "fsl_set_timing",
-           "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs"]
+           "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs",
+           "fsl_label_bubbles_static"]
 
 
 class FslError(RuntimeError):
@@ -90,6 +91,8 @@ def load_library():
     L.fsl_set_timing.argtypes = [vp, i32]
     L.fsl_stream_collide_ms.restype = dbl
     L.fsl_stream_collide_ms.argtypes = [vp]
+    L.fsl_label_bubbles_static.restype = i32
+    L.fsl_label_bubbles_static.argtypes = [vp, i32, i32, i32, vp, vp]
     L.fsl_set_graphs.restype = i32
     L.fsl_set_graphs.argtypes = [vp, i32]
     L.fsl_labelling_runs.restype = i64
@@ -128,6 +131,24 @@ def _default_stream() -> int:
     except Exception:
         pass
     return 0
+
+
+STATIC_MAX_CELLS = 1 << 21
+
+
+def label_bubbles_static(flags, nx: int, ny: int, nz: int, labels, stream: Optional[int] = None):
+    """Allocation-free bubble labelling through fsl_label_bubbles_static.
+
+    For callers that cannot allocate device memory.  `flags` (uint8) and
+    `labels` (int64) are caller-owned device tensors of nx*ny*nz elements; the
+    library uses only its fixed 2^21-cell scratch.  Labels are the minimum
+    linear index of each 18-connected gas/interface component, -1 elsewhere.
+    Calls that overlap on the GPU share the scratch and race."""
+    L = load_library()
+    st = L.fsl_label_bubbles_static(_ptr(flags), nx, ny, nz, _ptr(labels),
+                                     ctypes.c_void_p(_default_stream() if stream is None else stream))
+    if st != FSL_OK:
+        raise FslError(st, "fsl_label_bubbles_static failed")
 
 
 class Simulation:
