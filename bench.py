@@ -52,6 +52,9 @@ def workload(name: str):
         return S.gas_thread(), "gas_thread 256x64x64 TRT sigma=5e-3 R=8(1+0.1 sin(2 pi x/64))"
     if name == "static_bubble":
         return S.static_bubble(), "static_bubble 32^3 BGK R=8 sigma=1e-3"
+    if name == "gas_thread_large":
+        return (S.gas_thread(nx=1024, ny=256, nz=256, radius=32.0, wavelength=256.0),
+                "gas_thread 1024x256x256 TRT sigma=5e-3 R=32(1+0.1 sin(2 pi x/256))")
     raise ValueError(name)
 
 
@@ -203,6 +206,15 @@ def run_gpu(args, rank: int, world: int):
     traffic = traffic_per_launch(args.precision, args.workload)
     sim.close()
 
+    # per-phase device times from a separate direct-launch pass (diagnostic)
+    phases = None
+    if not args.no_variants:
+        ph = make(args.precision)
+        ph.set_graphs(False)
+        timed_steps(ph, 20, args.warmup)
+        phases = {k: round(v / 20 * 1e3, 2) for k, v in ph.phase_ms().items()}
+        ph.close()
+
     variants = {}
     if not args.no_variants:
         for prec in ("fp32", "bf16s", "fp64"):
@@ -259,7 +271,7 @@ def run_gpu(args, rank: int, world: int):
                          "kernel": KERNEL, "algorithmic_bytes_per_launch": int(abytes),
                          "avg_launch_ms": round(k1_avg, 5), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "variants": variants,
+            "variants": variants, "phase_us_per_step_direct_launch": phases,
         }
         print(json.dumps(line))
 

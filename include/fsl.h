@@ -164,6 +164,13 @@ double fsl_stream_collide_ms(const fsl_domain* h);
  * Results are identical. */
 fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
 
+/* Device time per phase of the steps timed since fsl_set_timing(h, 1), summed,
+ * in milliseconds, when the handle runs without graphs (fsl_set_graphs(h, 0)):
+ * out[0] stream-collide (liquid and interface kernels), out[1] conversion
+ * phase A, out[2] phase B, out[3] excess mass and triggers, out[4] fill-level
+ * and volume update, out[5] labelling.  Read after fsl_sync. */
+fsl_status fsl_phase_ms(const fsl_domain* h, double* out);
+
 /* Counts of the cell types of domain d (array of 5), synchronises. */
 fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts);
 

@@ -33,9 +33,8 @@ struct fsl_domain {
     cudaStream_t ls2 = nullptr;   // second stream, used only to capture the labelling body
     cudaStream_t ls3 = nullptr;   // interface kernels, concurrent with the liquid kernel
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    void* nrm = nullptr;
-    int nrm_cap = 0;
-    int ifblocks = 1216;          // grid of the interface kernel (8 blocks of 128 per SM)
+
+    int ifblocks = 304;           // grid of the list kernels (2 blocks per SM)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
     std::vector<Dom> hdoms;
@@ -52,7 +51,7 @@ struct fsl_domain {
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *flag = nullptr, *mark = nullptr;
-    double *m = nullptr, *phi = nullptr, *rhoi = nullptr, *exs = nullptr;
+    double *m = nullptr, *phi = nullptr, *phit = nullptr, *rhoi = nullptr, *exs = nullptr;
     int* id = nullptr;
     long long *vfx = nullptr, *vxfx = nullptr, *vsfx = nullptr, *ncells = nullptr;
     int* constp = nullptr;
@@ -62,7 +61,7 @@ struct fsl_domain {
     int* ilist[2] = {nullptr, nullptr};   // interface list read by a step starting from buffer k
     int* icount[2] = {nullptr, nullptr};
     int *mlist = nullptr, *mcount = nullptr, *glist = nullptr, *gcount = nullptr, *llist = nullptr, *lcount = nullptr;
-    int *cstep = nullptr, *stepno = nullptr;
+    int *cstep = nullptr, *recv = nullptr, *stepno = nullptr;
     long long* icnt = nullptr;
     // labelling scratch
     int *lab = nullptr, *aux = nullptr;
@@ -91,6 +90,9 @@ struct fsl_domain {
     std::vector<cudaEvent_t> evpool;
     size_t evused = 0;
     double k1_ms = 0.0;
+    std::vector<cudaEvent_t> phpool;   // direct mode: events between the kernels of a step
+    size_t phused = 0;
+    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
     std::vector<void*> allocs;
     std::string err;
 };
@@ -134,6 +136,7 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.mark = h->mark;
     A.m = h->m;
     A.phi = h->phi;
+    A.phit = h->phit;
     A.rhoi = h->rhoi;
     A.exs = h->exs;
     A.id = h->id;
@@ -158,11 +161,11 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.llist = h->llist;
     A.lcount = h->lcount;
     A.cstep = h->cstep;
+    A.recv = h->recv;
     A.stepno = h->stepno;
     A.icnt = h->icnt;
-    A.nrm = h->nrm;
-    A.nrm_cap = h->nrm_cap;
     A.cond = 0;
+    A.d0 = h->hdoms[0];
     return A;
 }
 
@@ -214,7 +217,17 @@ void launch_cb(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
 // Stream-collide and the four conversion phases of one step (6 kernels).
 // With e0/e1 the stream-collide pair is bracketed by event records (captured
 // as event-record nodes when the stream is capturing; their nodes go to rec).
-int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e1, cudaGraphNode_t* rec) {
+cudaEvent_t next_phase_event(fsl_domain* h) {
+    while (h->phpool.size() < h->phused + 1) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->phpool.push_back(e);
+    }
+    return h->phpool[h->phused++];
+}
+
+int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e1, cudaGraphNode_t* rec,
+                 bool phases = false) {
     auto last_node = [&](int k) {
         if (!rec) return;
         cudaStreamCaptureStatus cs;
@@ -233,9 +246,13 @@ int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e
     launch_k1(h, A, h->ls);
     if (e1) { record(e1); last_node(1); }
     launch_convert_a(A, h->ifblocks, h->ls);
+    if (phases) cudaEventRecord(next_phase_event(h), h->ls);
     launch_cb(h, A, h->ls);
+    if (phases) cudaEventRecord(next_phase_event(h), h->ls);
     launch_convert_c(A, h->ifblocks, h->ls);
+    if (phases) cudaEventRecord(next_phase_event(h), h->ls);
     launch_convert_d(A, h->ifblocks, h->ls);
+    if (phases) cudaEventRecord(next_phase_event(h), h->ls);
     return 6;
 }
 
@@ -428,7 +445,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms > 0) h->ifblocks = 8 * sms;
+        if (sms > 0) h->ifblocks = 2 * sms;
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
@@ -443,6 +460,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->mark, N);
     AL(h->m, 8 * N);
     AL(h->phi, 8 * N);
+    AL(h->phit, 8 * N);
     AL(h->rhoi, 8 * N);
     AL(h->exs, 8 * N);
     AL(h->id, 4 * N);
@@ -466,12 +484,10 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->llist, 4 * N);
     AL(h->lcount, sizeof(int));
     AL(h->cstep, 4 * N);
+    AL(h->recv, 4 * N);
     AL(h->stepno, sizeof(int));
     AL(h->icnt, 8 * n_domains);
-    // interface-list entries whose normals fit in the scratch (one eighth of
-    // the lattice, at least 64 Ki); more interface cells latch TABLE_FULL
-    h->nrm_cap = (int)std::min<long long>(h->stride, std::max<long long>(65536, h->stride / 8));
-    AL(h->nrm, (size_t)h->nrm_cap * 21 * (precision == FSL_P_FP64 ? 8 : 4));
+
     AL(h->lab, 4 * N);
     AL(h->aux, 4 * N);
     AL(h->hkeys, 8 * (size_t)hc);
@@ -503,6 +519,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->id, 0xff, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->m, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->phi, 0, 8 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->phit, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->rhoi, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->exs, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->f[0], 0, 19 * N * h->fbytes);
@@ -518,6 +535,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->lcount, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->stepno, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->cstep, 0xff, 4 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->recv, 0xff, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->icnt, 0, 8 * n_domains);
     if (e == cudaSuccess) e = cudaMemset(h->runs, 0, 8);
     if (e == cudaSuccess) e = cudaMemset(h->vfx, 0, 8 * NS);
@@ -624,8 +642,9 @@ fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
                 e0 = ev.first;
                 e1 = ev.second;
             }
-            h->launches += enqueue_main(h, A, e0, e1, nullptr);
+            h->launches += enqueue_main(h, A, e0, e1, nullptr, h->timing);
             h->launches += launch_ccl(A, ccl_args(h, 0), h->nblocks, h->vsfx, h->constp, h->ls);
+            if (h->timing) cudaEventRecord(next_phase_event(h), h->ls);
             h->cur = 1 - h->cur;
         }
     } else if (h->timing) {
@@ -661,7 +680,24 @@ fsl_status fsl_sync(fsl_domain* h) {
             tot += ms;
         }
         h->k1_ms = tot;
+        // direct mode: phase k of step n runs from event 5n+k-1 (the end of
+        // the stream-collide pair for k = 1) to event 5n+k
+        if (h->phused >= 5 && h->phused == 5 * (h->evused / 2)) {
+            for (int k = 0; k < 6; ++k) h->phase_ms[k] = 0.0;
+            for (size_t n = 0; n < h->evused / 2; ++n) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, h->evpool[2 * n], h->evpool[2 * n + 1]);
+                h->phase_ms[0] += ms;
+                cudaEvent_t prev = h->evpool[2 * n + 1];
+                for (int k = 0; k < 5; ++k) {
+                    cudaEventElapsedTime(&ms, prev, h->phpool[5 * n + k]);
+                    h->phase_ms[1 + k] += ms;
+                    prev = h->phpool[5 * n + k];
+                }
+            }
+        }
         h->evused = 0;
+        h->phused = 0;
     }
     return latch(h);
 }
@@ -671,10 +707,17 @@ fsl_status fsl_set_timing(fsl_domain* h, int32_t on) {
     h->timing = on != 0;
     h->k1_ms = 0.0;
     h->evused = 0;
+    h->phused = 0;
     return FSL_OK;
 }
 
 double fsl_stream_collide_ms(const fsl_domain* h) { return h ? h->k1_ms : 0.0; }
+
+fsl_status fsl_phase_ms(const fsl_domain* h, double* out) {
+    if (!h || !out) return FSL_ERR_ARG;
+    for (int k = 0; k < 6; ++k) out[k] = h->phase_ms[k];
+    return FSL_OK;
+}
 
 fsl_status fsl_set_graphs(fsl_domain* h, int32_t on) {
     if (!h) return FSL_ERR_ARG;
@@ -831,6 +874,7 @@ fsl_status fsl_destroy(fsl_domain* h) {
     for (int k = 0; k < 2; ++k)
         if (h->timed_src[k]) cudaGraphDestroy(h->timed_src[k]);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->phpool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);

@@ -46,28 +46,30 @@ __device__ inline void warp_add(long long* base, int key, long long v) {
 // All four phases work on compact lists (marked cells, new interface cells,
 // interface cells), so their cost follows the interface, not the lattice.
 
-// C1 (phase A), over the marked list: a filled cell turns each gas neighbour
-// into interface (the neighbour's first filled neighbour in direction order
-// claims it, so it is listed once) and cancels the emptied marks next to it.
+// C1 (phase A), one thread per (marked cell, direction): a filled cell turns
+// the gas neighbour in that direction into interface (the neighbour's first
+// filled neighbour in direction order claims it, so it is listed once) and
+// cancels an emptied mark there.
 __global__ void __launch_bounds__(128) k_convert_a(StepArgs A) {
+    pdl_trigger();
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
         if (threadIdx.x == 0) *A.icount_next = 0;
     }
     const int nm = *A.mcount;
+    const int total = 18 * nm;
     const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < nm; base += stride) {
-        const int i = base + threadIdx.x;
-        const bool valid = i < nm;
-        const long long p = valid ? A.mlist[i] : 0;
-        const bool filled = valid && A.mark[p] == MK_FILLED;
-        const int d = valid ? A.blk_dom[p / FSL_BLOCK] : 0;
-        const Dom& D = A.doms[d];
-        const Cell c = make_cell(D, valid ? p : D.off);
-        for (int a = 1; a < 19; ++a) {
-            bool claim = false;
-            long long z = 0;
-            if (filled) {
+    for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
+        const int t = base + threadIdx.x;
+        bool claim = false;
+        long long z = 0;
+        if (t < total) {
+            const long long p = A.mlist[t / 18];
+            const int a = 1 + t % 18;
+            if (A.mark[p] == MK_FILLED) {
+                const int d = block_dom(A, p);
+                const Dom D = get_dom(A, d);
+                const Cell c = make_cell(D, p);
                 z = c.at(cx(a), cy(a), cz(a));
                 const uint8_t tz = ctype(A.flag[z]);
                 if (tz == GAS) {
@@ -80,8 +82,8 @@ __global__ void __launch_bounds__(128) k_convert_a(StepArgs A) {
                     A.mark[z] = MK_NONE;
                 }
             }
-            list_append(A.glist, A.gcount, claim, (int)z);
         }
+        list_append(A.glist, A.gcount, claim, (int)z);
     }
 }
 
@@ -114,14 +116,16 @@ __device__ inline bool removal_is_local(unsigned fg) {
 // removal must pass the local test with the lower-index filled cells already
 // gone and the higher-index ones still present, or the labelling runs.
 __global__ void __launch_bounds__(128) k_convert_c(StepArgs A) {
+    pdl_wait();
+    pdl_trigger();
     const int nm = *A.mcount, nl = *A.lcount;
     const int total = nm + nl;
     const int step = *A.stepno;
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
         const long long g = i < nm ? A.mlist[i] : A.llist[i - nm];
-        const int d = A.blk_dom[g / FSL_BLOCK];
-        const Dom& D = A.doms[d];
+        const int d = block_dom(A, g);
+        const Dom D = get_dom(A, d);
         const Cell c = make_cell(D, g);
         const uint8_t mk = A.mark[g];
         if (i < nm) {
@@ -130,7 +134,10 @@ __global__ void __launch_bounds__(128) k_convert_c(StepArgs A) {
             int k = 0;
             for (int a = 1; a < 19; ++a) {
                 const long long z = c.at(cx(a), cy(a), cz(a));
-                if (new_type(ctype(A.flag[z]), A.mark[z]) == IFC) ++k;
+                if (new_type(ctype(A.flag[z]), A.mark[z]) == IFC) {
+                    ++k;
+                    A.recv[z] = step;   // z pulls a share in the update phase
+                }
             }
             if (k > 0) A.exs[g] = mex / (double)k;
             else atomicAdd((unsigned long long*)&A.pool[d], (unsigned long long)__double2ll_rn(mex * 1099511627776.0));
@@ -173,6 +180,7 @@ __global__ void __launch_bounds__(128) k_convert_c(StepArgs A) {
 // volumes change by exact fixed-point differences; the interface list of the
 // next step; reservoir drain; the graph condition of the labelling.
 __global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
+    pdl_wait();
     const int ni = *A.icount, ng = *A.gcount, nl = *A.lcount;
     const int total = ni + ng + nl;
     const int step = *A.stepno;
@@ -182,48 +190,58 @@ __global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
         const bool valid = i < total;
         long long g = 0;
         if (valid) g = i < ni ? A.ilist[i] : (i < ni + ng ? A.glist[i - ni] : A.llist[i - ni - ng]);
-        const int d = valid ? A.blk_dom[g / FSL_BLOCK] : 0;
+        const int d = valid ? block_dom(A, g) : 0;
         int key = -1;
         long long dv = 0;
         int ckey = -1;
         long long dc = 0;
         bool keep = false;
         if (valid) {
+            // everything the cell needs, loaded together
             const uint8_t f = A.flag[g];
-            const uint8_t t = ctype(f);
             const uint8_t mk = A.mark[g];
             key = A.id[g];
+            const double m0 = A.m[g], rh = A.rhoi[g], ph0 = A.phi[g];
+            const int rs = A.recv[g];
+            const long long nI = A.nif[d];
+            const long long pool = A.pool[d];
+            const uint8_t t = ctype(f);
             if (t == IFC && mk == MK_CFILLED) {
-                dv = -volume_term(IFC, A.phi[g]);
+                dv = -volume_term(IFC, ph0);
                 ckey = key;
                 dc = -1;
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
                 A.phi[g] = 1.0;
+                A.phit[g] = 1.0;
                 A.id[g] = -1;
                 A.mark[g] = MK_NONE;
             } else if (t == IFC && mk == MK_CEMPTIED) {
-                dv = FSL_VOL_ONE - volume_term(IFC, A.phi[g]);
+                dv = FSL_VOL_ONE - volume_term(IFC, ph0);
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
                 A.phi[g] = 0.0;
+                A.phit[g] = 0.0;
                 A.m[g] = 0.0;
                 A.mark[g] = MK_NONE;
             } else {
-                const Dom& D = A.doms[d];
-                const Cell c = make_cell(D, g);
-                double s = A.m[g];
-                for (int a = 1; a < 19; ++a) {
-                    const long long z = c.at(cx(a), cy(a), cz(a));
-                    if (A.cstep[z] == step) s = s + A.exs[z];
+                double s = m0;
+                if (rs == step) {
+                    // a converted neighbour listed this cell among its receivers
+                    const Dom D = get_dom(A, d);
+                    const Cell c = make_cell(D, g);
+                    for (int a = 1; a < 19; ++a) {
+                        const long long z = c.at(cx(a), cy(a), cz(a));
+                        if (A.cstep[z] == step) s = s + A.exs[z];
+                    }
                 }
-                const long long nI = A.nif[d];
                 if (nI > 0) {
-                    const double share = ((double)A.pool[d] * 9.094947017729282379150390625e-13) / (double)nI;
+                    const double share = ((double)pool * 9.094947017729282379150390625e-13) / (double)nI;
                     s = s + share;
                 }
-                const double phn = s / A.rhoi[g];
-                const long long told = volume_term(t, A.phi[g]);
+                const double phn = s / rh;
+                const long long told = volume_term(t, ph0);
                 A.m[g] = s;
                 A.phi[g] = phn;
+                A.phit[g] = phn < 0.0 ? 0.0 : (phn > 1.0 ? 1.0 : phn);
                 if (t != IFC) A.flag[g] = (uint8_t)((f & ~K_TYPE) | IFC);
                 dv = volume_term(IFC, phn) - told;
                 if (t == LIQ) { ckey = key; dc = 1; }
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
         // interface (types read through the marks, which stay consistent
         // while other threads update the flags)
         for (int d = 0; d < A.ndom; ++d) {
-            const Dom& D = A.doms[d];
+            const Dom D = get_dom(A, d);
             if (D.seed < 0) continue;
             const long long gs = D.off + D.seed;
             const uint8_t nt = new_type(ctype(A.flag[gs]), A.mark[gs]);
@@ -256,7 +274,7 @@ __global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
 // Interface list and per-domain interface counts of the initial state.
 __global__ void __launch_bounds__(FSL_BLOCK) k_build_ilist(StepArgs A) {
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const int d = A.blk_dom[blockIdx.x];
+    const int d = block_dom(A, (long long)blockIdx.x * FSL_BLOCK);
     const bool itf = ctype(A.flag[g]) == IFC;
     warp_add(A.icnt, itf ? d : -1, 1);
     list_append(A.ilist, A.icount, itf, (int)g);
@@ -319,7 +337,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_hook(StepArgs A, CclArgs K) {
     if (!K.initial && *A.trig == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     if (!is_fg(A.flag[g])) return;
-    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+    const Dom D = get_dom(A, block_dom(A, (long long)blockIdx.x * FSL_BLOCK));
     const Cell c = make_cell(D, g);
     // the nine directions 1, 3, ..., 17 cover each neighbour pair once
     for (int a = 1; a < 19; a += 2) {
@@ -343,8 +361,8 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_compress(StepArgs A, CclArgs 
     if (!ok) { set_status(A.status, ST_CCL); return; }
     K.lab[g] = r;
     if (r == (int)g) {
-        const int d = A.blk_dom[blockIdx.x];
-        const Dom& D = A.doms[d];
+        const int d = block_dom(A, (long long)blockIdx.x * FSL_BLOCK);
+        const Dom D = get_dom(A, d);
         const int k = atomicAdd(&K.nslot[d], 1);
         if (k >= D.slot_cap) { set_status(A.status, ST_TABLE_FULL); K.aux[g] = -1; return; }
         K.aux[g] = D.slot_off + k;
@@ -388,7 +406,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_pairs(StepArgs A, CclArgs K) 
         hash_add(K, key, term, A.status);
         atomicAdd((unsigned long long*)&K.vtot[b], (unsigned long long)term);
         atomicMin(&K.minc[b], K.lab[g]);
-        const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+        const Dom D = get_dom(A, block_dom(A, (long long)blockIdx.x * FSL_BLOCK));
         if (D.seed >= 0 && g - D.off == D.seed) {
             const long long x = A.vxfx[b];
             hash_add(K, key, x, A.status);
@@ -431,7 +449,7 @@ __global__ void k_ccl_install(StepArgs A, CclArgs K, long long* vsfx, int* const
     const long long nth = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < K.nslots_total; s += nth) {
         const int d = K.slot_dom[s];
-        const Dom& D = A.doms[d];
+        const Dom D = get_dom(A, d);
         const int k = (int)(s - D.slot_off);
         if (k < K.nslot[d]) {
             A.vfx[s] = K.nvfx[s];
@@ -480,8 +498,8 @@ __global__ void k_export_cells(const uint8_t* flag, const double* phi, const dou
 // ------------------------------------------------------------ host launches
 
 void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_a<<<(unsigned)nb, 128, 0, s>>>(A); }
-void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_c<<<(unsigned)nb, 128, 0, s>>>(A); }
-void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_d<<<(unsigned)nb, 128, 0, s>>>(A); }
+void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s) { launch_pdl(k_convert_c, (unsigned)nb, 128u, s, A); }
+void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s) { launch_pdl(k_convert_d, (unsigned)nb, 128u, s, A); }
 void launch_build_ilist(const StepArgs& A, long long nb, cudaStream_t s) { k_build_ilist<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
 
 int launch_ccl(const StepArgs& A, const CclArgs& K, long long nb, long long* vsfx, int* constp, cudaStream_t s) {

@@ -89,6 +89,8 @@ struct StepArgs {
     uint8_t* mark;
     double* m;                  // interface mass
     double* phi;                // fill level
+    double* phit;               // fill level as the normal stencil reads it: walls and
+                                // liquid 1, gas 0, interface clamp(phi, 0, 1)
     double* rhoi;               // density of interface cells at their last collision
     double* exs;                // excess-mass share of converted cells
     int* id;                    // bubble slot of gas/interface cells, -1 elsewhere
@@ -113,12 +115,17 @@ struct StepArgs {
     int* llist;                 // liquid cells that become interface (phase B)
     int* lcount;
     int* cstep;                 // step number at which each cell was last converted
+    int* recv;                  // step number at which each cell last received excess mass
     int* stepno;                // device step counter
     long long* icnt;            // per-domain interface count at the end of the step
-    void* nrm;                  // per interface-list entry: gradient + six normals (21 values)
-    int nrm_cap;                // list entries nrm can hold
     unsigned long long cond;    // graph conditional handle set to the trigger (0: none)
+    Dom d0;                     // domain 0, read from the parameter space when ndom == 1
 };
+
+// Domain descriptor and domain of a cell: a handle with one domain reads
+// them from the kernel parameters, a batch from its device tables.
+__device__ inline Dom get_dom(const StepArgs& A, int d) { return A.ndom == 1 ? A.d0 : A.doms[d]; }
+__device__ inline int block_dom(const StepArgs& A, long long g) { return A.ndom == 1 ? 0 : A.blk_dom[g / FSL_BLOCK]; }
 
 // D3Q19 velocities; constexpr so that unrolled loops fold them into offsets
 __host__ __device__ constexpr int cx(int a) {
@@ -134,12 +141,40 @@ __host__ __device__ constexpr int cz(int a) {
            : ((a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0);
 }
 
+// the same velocities for a run-time direction: two bits (c + 1) per direction
+__device__ inline int rcx(int a) { return (int)((0x1548889549ULL >> (2 * a)) & 3) - 1; }
+__device__ inline int rcy(int a) { return (int)((0x895609495ULL >> (2 * a)) & 3) - 1; }
+__device__ inline int rcz(int a) { return (int)((0x20a0954955ULL >> (2 * a)) & 3) - 1; }
+
 __host__ __device__ inline int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 __host__ __device__ inline double weight(int a) {
     return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
 __device__ inline void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation waits here until its predecessor has finished and its writes
+// are visible; a predecessor lets its dependent start launching early.
+__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch a kernel whose predecessor on the stream is a kernel, overlapping its
+// launch with the predecessor's tail (the kernel must call pdl_wait() first).
+template <typename... Args>
+inline cudaError_t launch_pdl(void (*k)(Args...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // Append v to list for every lane with pred set, one atomic per warp.  Every
 // lane of the warp must call.
@@ -190,22 +225,30 @@ __device__ inline Cell make_cell(const Dom& D, long long g) {
 template <typename T> struct Form;
 template <> struct Form<double> {
     using C = double;
+    static constexpr bool shifted = false;
     __device__ static inline double ld(const double* p, int) { return *p; }
     __device__ static inline void st(double* p, int, double v) { *p = v; }
 };
 template <> struct Form<float> {
     using C = float;
+    static constexpr bool shifted = false;
     __device__ static inline float ld(const float* p, int) { return *p; }
     __device__ static inline void st(float* p, int, float v) { *p = v; }
 };
 // shifted forms store f_a - w_a (rho0 = 1)
 template <> struct Form<__half> {
     using C = float;
+    static constexpr bool shifted = true;
+    __device__ static inline float ld_dev(const __half* p) { return __half2float(*p); }
+    __device__ static inline void st_dev(__half* p, float v) { *p = __float2half_rn(v); }
     __device__ static inline float ld(const __half* p, int a) { return (float)weight(a) + __half2float(*p); }
     __device__ static inline void st(__half* p, int a, float v) { *p = __float2half_rn(v - (float)weight(a)); }
 };
 template <> struct Form<__nv_bfloat16> {
     using C = float;
+    static constexpr bool shifted = true;
+    __device__ static inline float ld_dev(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static inline void st_dev(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static inline float ld(const __nv_bfloat16* p, int a) {
         return (float)weight(a) + __bfloat162float(*p);
     }
@@ -308,6 +351,55 @@ __device__ inline C collide(const C* fin, C* fout, C omp, C omm, C gx, C gy, C g
     return rho;
 }
 
+// The same collision on deviations d_a = f_a - w_a (rho0 = 1), for the
+// shifted 16-bit storage forms: rho = 1 + sum d, j = sum c d, and
+// d_eq = f_eq - w = w [(rho - 1) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u)].
+template <bool FORCE>
+__device__ inline void collide_dev(const float* d, float* dout, float omp, float omm, float gx, float gy, float gz) {
+    float drho = d[0];
+#pragma unroll
+    for (int a = 1; a < 19; ++a) drho += d[a];
+    const float rho = 1.f + drho;
+    float jx = d[1] - d[2] + d[7] - d[8] + d[9] - d[10] + d[11] - d[12] + d[13] - d[14];
+    float jy = d[3] - d[4] + d[7] - d[8] - d[9] + d[10] + d[15] - d[16] + d[17] - d[18];
+    float jz = d[5] - d[6] + d[11] - d[12] - d[13] + d[14] + d[15] - d[16] - d[17] + d[18];
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    if constexpr (FORCE) {
+        Fx = rho * gx; Fy = rho * gy; Fz = rho * gz;
+        jx += 0.5f * Fx; jy += 0.5f * Fy; jz += 0.5f * Fz;
+    }
+    const float ir = 1.f / rho;
+    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float cp = 1.f - 0.5f * omp, cm = 1.f - 0.5f * omm;
+    const float w0 = (float)weight(0);
+    dout[0] = d[0] - omp * (d[0] - w0 * (drho - rho * usq15));
+    float uF = 0.f;
+    if constexpr (FORCE) {
+        uF = ux * Fx + uy * Fy + uz * Fz;
+        dout[0] += cp * (w0 * (-3.f * uF));
+    }
+#pragma unroll
+    for (int a = 1; a < 19; a += 2) {
+        const int b = a + 1;
+        const float w = (float)weight(a);
+        const float cu = cdot<float>(a, ux, uy, uz);
+        const float eqp = w * (drho + rho * (4.5f * cu * cu - usq15));
+        const float eqm = w * rho * 3.f * cu;
+        const float A = omp * (0.5f * (d[a] + d[b]) - eqp);
+        const float B = omm * (0.5f * (d[a] - d[b]) - eqm);
+        dout[a] = d[a] - A - B;
+        dout[b] = d[b] - A + B;
+        if constexpr (FORCE) {
+            const float cF = cdot<float>(a, Fx, Fy, Fz);
+            const float sp = cp * (w * (9.f * cu * cF - 3.f * uF));
+            const float sm = cm * (w * 3.f * cF);
+            dout[a] += sp + sm;
+            dout[b] += sp - sm;
+        }
+    }
+}
+
 template <typename C>
 __device__ inline C collide_any(bool force, const C* fin, C* fout, C omp, C omm, C gx, C gy, C gz) {
     return force ? collide<C, true>(fin, fout, omp, omm, gx, gy, gz) : collide<C, false>(fin, fout, omp, omm, gx, gy, gz);
@@ -381,50 +473,77 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_stream_liquid(StepArgs A) {
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     const uint8_t f = A.flag[g];
     if (ctype(f) != LIQ) return;
-    const Dom& D = A.doms[A.blk_dom[blockIdx.x]];
+    const Dom D = get_dom(A, block_dom(A, g));
     const Pull P = make_pull(D, g);
+    const unsigned gi = (unsigned)g;
     const long long S = A.stride;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
-    C fin[19];
-    fin[0] = Form<T>::ld(src + g, 0);
-    if (!(f & K_WALL)) {
+    if constexpr (Form<T>::shifted) {
+        // deviations from w_a all the way through
+        float d[19];
+        d[0] = Form<T>::ld_dev(src + gi);
+        if (!(f & K_WALL)) {
 #pragma unroll
-        for (int a = 1; a < 19; ++a) fin[a] = Form<T>::ld(src + (long long)a * S + P.at(-cx(a), -cy(a), -cz(a)), a);
-    } else {
+            for (int a = 1; a < 19; ++a)
+                d[a] = Form<T>::ld_dev(src + a * S + (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]));
+        } else {
 #pragma unroll
-        for (int a = 1; a < 19; ++a) {
-            const int ab = opp(a);
-            const long long y = P.at(-cx(a), -cy(a), -cz(a));
-            const uint8_t ty = ctype(A.flag[y]);
-            if (ty == OBS) {
-                fin[a] = Form<T>::ld(src + (long long)ab * S + g, ab);
-            } else if (ty == LID) {
-                C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
-                fin[a] = Form<T>::ld(src + (long long)ab * S + g, ab) + ((C)6 * (C)weight(a)) * cuw;
-            } else {
-                fin[a] = Form<T>::ld(src + (long long)a * S + y, a);
+            for (int a = 1; a < 19; ++a) {
+                const int ab = opp(a);
+                const unsigned y = (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]);
+                const uint8_t ty = ctype(A.flag[y]);
+                if (ty == OBS) {
+                    d[a] = Form<T>::ld_dev(src + ab * S + gi);   // w_a = w_abar
+                } else if (ty == LID) {
+                    const float cuw = cdot<float>(a, (float)D.lid[0], (float)D.lid[1], (float)D.lid[2]);
+                    d[a] = Form<T>::ld_dev(src + ab * S + gi) + (6.f * (float)weight(a)) * cuw;
+                } else {
+                    d[a] = Form<T>::ld_dev(src + a * S + y);
+                }
             }
         }
-    }
-    C fout[19];
-    C rho = collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
-    if (!(rho == rho)) set_status(A.status, ST_NAN);
+        float dout[19];
+        if (D.has_force)
+            collide_dev<true>(d, dout, (float)D.omp, (float)D.omm, (float)D.g[0], (float)D.g[1], (float)D.g[2]);
+        else
+            collide_dev<false>(d, dout, (float)D.omp, (float)D.omm, 0.f, 0.f, 0.f);
+        if (!(dout[0] == dout[0])) set_status(A.status, ST_NAN);
 #pragma unroll
-    for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
+        for (int a = 0; a < 19; ++a) Form<T>::st_dev(dst + a * S + gi, dout[a]);
+    } else {
+        C fin[19];
+        fin[0] = Form<T>::ld(src + gi, 0);
+        if (!(f & K_WALL)) {
+#pragma unroll
+            for (int a = 1; a < 19; ++a)
+                fin[a] = Form<T>::ld(src + a * S + (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]), a);
+        } else {
+#pragma unroll
+            for (int a = 1; a < 19; ++a) {
+                const int ab = opp(a);
+                const unsigned y = (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]);
+                const uint8_t ty = ctype(A.flag[y]);
+                if (ty == OBS) {
+                    fin[a] = Form<T>::ld(src + ab * S + gi, ab);
+                } else if (ty == LID) {
+                    C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
+                    fin[a] = Form<T>::ld(src + ab * S + gi, ab) + ((C)6 * (C)weight(a)) * cuw;
+                } else {
+                    fin[a] = Form<T>::ld(src + a * S + y, a);
+                }
+            }
+        }
+        C fout[19];
+        C rho = collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+        if (!(rho == rho)) set_status(A.status, ST_NAN);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Form<T>::st(dst + a * S + gi, a, fout[a]);
+    }
 }
 
-// Wrapped coordinates x-2..x+2 (and y, z) of one interface cell, for the
-// 5x5x5 fill-level stencil of the curvature.
-struct Stencil {
-    int X[5], Y[5], Z[5];
-    int nx;
-    long long nxy, off;
-    __device__ inline long long at(int dx, int dy, int dz) const {
-        return off + X[dx + 2] + (long long)nx * Y[dy + 2] + nxy * Z[dz + 2];
-    }
-};
-
+// Coordinates of one interface cell, for the 5x5x5 fill-level stencil of the
+// curvature and its +-1 neighbours; offsets up to 2 wrap around the domain.
 __device__ inline int wrap2(int v, int n) {   // v in [-2, n+1]
     v = v < 0 ? v + n : v;
     v = v < 0 ? v + n : v;
@@ -433,91 +552,56 @@ __device__ inline int wrap2(int v, int n) {   // v in [-2, n+1]
     return v;
 }
 
+struct Stencil {
+    int x, y, z, nx, ny, nz;
+    long long off, g;
+    bool inner;   // two cells from every face: no wrap needed
+    __device__ inline long long at(int dx, int dy, int dz) const {
+        if (inner) return g + dx + (long long)nx * (dy + (long long)ny * dz);
+        return off + wrap2(x + dx, nx) + (long long)nx * (wrap2(y + dy, ny) + (long long)ny * wrap2(z + dz, nz));
+    }
+};
+
 __device__ inline Stencil make_stencil(const Dom& D, long long g) {
     Stencil s;
-    int x, y, z;
-    local_xyz(D, (int)(g - D.off), x, y, z);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        s.X[k] = wrap2(x + k - 2, D.nx);
-        s.Y[k] = wrap2(y + k - 2, D.ny);
-        s.Z[k] = wrap2(z + k - 2, D.nz);
-    }
-    s.nx = D.nx;
-    s.nxy = (long long)D.nx * D.ny;
+    local_xyz(D, (int)(g - D.off), s.x, s.y, s.z);
+    s.nx = D.nx; s.ny = D.ny; s.nz = D.nz;
     s.off = D.off;
+    s.g = g;
+    s.inner = s.x >= 2 && s.x < D.nx - 2 && s.y >= 2 && s.y < D.ny - 2 && s.z >= 2 && s.z < D.nz - 2;
     return s;
 }
 
-__device__ inline double phi_stencil(const uint8_t* flag, const double* phi, long long j) {
-    const uint8_t t = ctype(flag[j]);
-    if (t == LIQ || t == OBS || t == LID) return 1.0;
-    if (t == GAS) return 0.0;
-    const double v = phi[j];
-    return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
-}
-
-// K1N: for every interface cell, the Parker-Youngs gradient of the fill level
-// at the cell (point 0) and the unit normals n_hat = -g/|g| at its six face
-// neighbours (points 1-6: +x, -x, +y, -y, +z, -z); seven threads per cell,
-// each loading the 27 fill levels around its point once.  Results go to
-// nrm[21 * list index + 3 * point + component].
-template <typename C>
-__global__ void __launch_bounds__(128) k_surface_normals(StepArgs A) {
-    const int cnt = *A.icount;
-    if (cnt > A.nrm_cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(A.status, ST_TABLE_FULL);
-        return;
-    }
-    C* nrm = (C*)A.nrm;
-    const long long total = 7LL * cnt;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
-        const int i = (int)(t / 7), j = (int)(t - 7LL * (t / 7));
-        const long long g = A.ilist[i];
-        const Dom& D = A.doms[A.blk_dom[g / FSL_BLOCK]];
-        const Stencil st = make_stencil(D, g);
-        const int ox = j == 1 ? 1 : (j == 2 ? -1 : 0);
-        const int oy = j == 3 ? 1 : (j == 4 ? -1 : 0);
-        const int oz = j == 5 ? 1 : (j == 6 ? -1 : 0);
-        C ph[27];
-#pragma unroll
-        for (int k = 0; k < 27; ++k)
-            ph[k] = (C)phi_stencil(A.flag, A.phi, st.at(ox + k % 3 - 1, oy + (k / 3) % 3 - 1, oz + k / 9 - 1));
-        C gx = (C)0, gy = (C)0, gz = (C)0;
-#pragma unroll
-        for (int b = -1; b <= 1; ++b) {
-#pragma unroll
-            for (int a = -1; a <= 1; ++a) {
-                const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
-                gx = gx + W * (ph[2 + 3 * (a + 1) + 9 * (b + 1)] - ph[0 + 3 * (a + 1) + 9 * (b + 1)]);
-                gy = gy + W * (ph[(a + 1) + 3 * 2 + 9 * (b + 1)] - ph[(a + 1) + 3 * 0 + 9 * (b + 1)]);
-                gz = gz + W * (ph[(a + 1) + 3 * (b + 1) + 9 * 2] - ph[(a + 1) + 3 * (b + 1) + 9 * 0]);
-            }
-        }
-        C* out = nrm + (long long)i * 21 + 3 * j;
-        if (j == 0) {
-            out[0] = gx; out[1] = gy; out[2] = gz;
-        } else {
-            const C q = gx * gx + gy * gy + gz * gz;
-            if (q > (C)0) {
-                const C len = sqrt(q);
-                out[0] = -(gx / len); out[1] = -(gy / len); out[2] = -(gz / len);
-            } else {
-                out[0] = (C)0; out[1] = (C)0; out[2] = (C)0;
-            }
-        }
-    }
-}
 
 // K1I: interface cells, from the list of interface cells built at the end of
-// the previous step: stream with bounce-back, mass exchange over the 18 links
-// (Eq. 10), reconstruction of the PDFs coming from the gas side with the gas
-// density 3 (p_V + 2 sigma kappa) of the cell's bubble (Eqs. 8, 11-15),
-// collide, then the filled / emptied marks.
+// the previous step.  A block takes 32 cells per pass.  Load phase, eight
+// threads per cell into shared memory: thread j (0-6) reads the 27 stencil fill
+// levels around point j (the cell, then its +x, -x, +y, -y, +z, -z
+// neighbours) and forms the Parker-Youngs gradient there (a unit normal for
+// j > 0); thread 7 reads the cell's mass and bubble pressure; all eight read
+// the PDFs, neighbour types and mass-exchange terms of directions j, j+8,
+// j+16.  Compute phase, one thread per cell (the first warp), in the oracle's
+// order: stream with bounce-back, mass exchange over the 18 links (Eq. 10),
+// reconstruction of the PDFs coming from the gas side with the gas density
+// 3 (p_V + 2 sigma kappa) of the cell's bubble (Eqs. 8, 11-15, kappa = 1/2 div
+// n_hat), collision, then the filled / emptied marks.
 template <typename T>
-__global__ void __launch_bounds__(128) k_stream_interface(StepArgs A) {
+struct IfStage {
     using C = typename Form<T>::C;
+    C fs[32][19];      // own post-collision PDFs
+    C fy[32][19];      // PDF streaming in from the source cell
+    double ex[32][19]; // mass-exchange term of each link (Eq. 10)
+    C nrm[32][7][3];   // gradient at the cell, unit normals at the face neighbours
+    double m[32];      // mass
+    double pv[32];     // bubble pressure (Eq. 13)
+    uint8_t ty[32][19];
+    uint8_t tz[32][19];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
+    using C = typename Form<T>::C;
+    __shared__ IfStage<T> sh;
     if (blockIdx.x == 0) {
         // per-step counters; the previous step's kernels are done with them
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
@@ -535,84 +619,135 @@ __global__ void __launch_bounds__(128) k_stream_interface(StepArgs A) {
     const long long S = A.stride;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < cnt; base += stride) {
-        const int i = base + threadIdx.x;
-        const bool valid = i < cnt;
-        const long long g = valid ? A.ilist[i] : 0;
-        uint8_t mk = MK_NONE;
-        if (valid) {
-            const Dom& D = A.doms[A.blk_dom[g / FSL_BLOCK]];
+    const int c = threadIdx.x >> 3;      // cell of this thread in the load phase
+    const int j = threadIdx.x & 7;
+    for (int i0 = blockIdx.x * 32; i0 < cnt; i0 += gridDim.x * 32) {
+        // ---------------- load phase
+        if (i0 + c < cnt) {
+            const long long g = A.ilist[i0 + c];
+            const Dom D = get_dom(A, block_dom(A, g));
             const Stencil st = make_stencil(D, g);
-            C fs[19];
+            if (j < 7) {
+                const int ox = j == 1 ? 1 : (j == 2 ? -1 : 0);
+                const int oy = j == 3 ? 1 : (j == 4 ? -1 : 0);
+                const int oz = j == 5 ? 1 : (j == 6 ? -1 : 0);
+                C ph[27];
 #pragma unroll
-            for (int a = 0; a < 19; ++a) fs[a] = Form<T>::ld(src + (long long)a * S + g, a);
-            C rs, jsx, jsy, jsz;
-            moments<C>(fs, rs, jsx, jsy, jsz);
-            const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
-            // gradient at the cell and unit normals at its six face neighbours
-            // (k_surface_normals); kappa = 1/2 div(n_hat) (Eq. 15)
-            const C* nr = (const C*)A.nrm + (long long)i * 21;
-            const C gx = nr[0], gy = nr[1], gz = nr[2];
-            const C dX = nr[3 * 1 + 0] - nr[3 * 2 + 0];
-            const C dY = nr[3 * 3 + 1] - nr[3 * 4 + 1];
-            const C dZ = nr[3 * 5 + 2] - nr[3 * 6 + 2];
-            const C kappa = (C)0.25 * ((dX + dY) + dZ);
-            const int b = A.id[g];
-            const double pv = b >= 0 ? bubble_pressure(A.vfx[b], A.vxfx[b], A.vsfx[b], A.constp[b]) : 1.0 / 3.0;
-            const C pg = (C)pv + (C)D.sigma2 * kappa;
-            const C rg = (C)3 * pg;
-            C fg[19];
-            feq_all<C>(rg, ugx, ugy, ugz, fg);
-
-            C fin[19];
-            fin[0] = fs[0];
+                for (int k = 0; k < 27; ++k) ph[k] = (C)A.phit[st.at(ox + k % 3 - 1, oy + (k / 3) % 3 - 1, oz + k / 9 - 1)];
+                C gx = (C)0, gy = (C)0, gz = (C)0;
 #pragma unroll
-            for (int a = 1; a < 19; ++a) {
-                const int ab = opp(a);
-                const long long y = st.at(-cx(a), -cy(a), -cz(a));
-                const uint8_t ty = ctype(A.flag[y]);
-                if (ty == OBS) {
-                    fin[a] = fs[ab];
-                } else if (ty == LID) {
-                    const C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
-                    fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
-                } else if (ty == GAS) {
-                    fin[a] = (fg[a] + fg[ab]) - fs[ab];
-                } else {
-                    fin[a] = Form<T>::ld(src + (long long)a * S + y, a);
-                    if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
+                for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a) {
+                        const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
+                        gx = gx + W * (ph[2 + 3 * (a + 1) + 9 * (b + 1)] - ph[0 + 3 * (a + 1) + 9 * (b + 1)]);
+                        gy = gy + W * (ph[(a + 1) + 3 * 2 + 9 * (b + 1)] - ph[(a + 1) + 3 * 0 + 9 * (b + 1)]);
+                        gz = gz + W * (ph[(a + 1) + 3 * (b + 1) + 9 * 2] - ph[(a + 1) + 3 * (b + 1) + 9 * 0]);
+                    }
                 }
+                if (j > 0) {
+                    const C q = gx * gx + gy * gy + gz * gz;
+                    if (q > (C)0) {
+                        const C len = sqrt(q);
+                        gx = -(gx / len); gy = -(gy / len); gz = -(gz / len);
+                    } else {
+                        gx = (C)0; gy = (C)0; gz = (C)0;
+                    }
+                }
+                sh.nrm[c][j][0] = gx;
+                sh.nrm[c][j][1] = gy;
+                sh.nrm[c][j][2] = gz;
+            } else {
+                sh.m[c] = A.m[g];
+                const int bub = A.id[g];
+                sh.pv[c] = bub >= 0 ? bubble_pressure(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : 1.0 / 3.0;
             }
-            // mass exchange over the 18 links, in direction order (Eq. 10)
             const double phx = A.phi[g];
-            double dm = 0.0;
-#pragma unroll
-            for (int a = 1; a < 19; ++a) {
+            for (int a = j; a < 19; a += 8) {
+                const C fsa = Form<T>::ld(src + (long long)a * S + g, a);
+                sh.fs[c][a] = fsa;
+                if (a == 0) continue;
                 const int ab = opp(a);
-                const long long z = st.at(cx(a), cy(a), cz(a));
+                const int ax = rcx(a), ay = rcy(a), az = rcz(a);
+                const long long y = st.at(-ax, -ay, -az);
+                sh.ty[c][a] = ctype(A.flag[y]);
+                sh.fy[c][a] = Form<T>::ld(src + (long long)a * S + y, a);
+                const long long z = st.at(ax, ay, az);
                 const uint8_t tz = ctype(A.flag[z]);
+                sh.tz[c][a] = tz;
                 if (tz == LIQ || tz == IFC) {
                     const double fz = (double)Form<T>::ld(src + (long long)ab * S + z, ab);
-                    const double ex = fz - (double)fs[a];
-                    if (tz == LIQ) dm = dm + ex;
-                    else dm = dm + (0.5 * (phx + A.phi[z])) * ex;
+                    const double e = fz - (double)fsa;
+                    sh.ex[c][a] = tz == IFC ? (0.5 * (phx + A.phi[z])) * e : e;
                 }
             }
-            const double mnew = A.m[g] + dm;
-            C fout[19];
-            const C rho = collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
-            if (!(rho == rho)) set_status(A.status, ST_NAN);
-#pragma unroll
-            for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
-            const double r = (double)rho;
-            A.m[g] = mnew;
-            A.rhoi[g] = r;
-            if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
-            else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
-            A.mark[g] = mk;
         }
-        list_append(A.mlist, A.mcount, mk != MK_NONE, (int)g);
+        __syncthreads();
+        // ---------------- compute phase (first warp, one thread per cell)
+        if (threadIdx.x < 32) {
+            const int cc = threadIdx.x;
+            uint8_t mk = MK_NONE;
+            long long g = 0;
+            if (i0 + cc < cnt) {
+                g = A.ilist[i0 + cc];
+                const Dom D = get_dom(A, block_dom(A, g));
+                C fs[19];
+#pragma unroll
+                for (int a = 0; a < 19; ++a) fs[a] = sh.fs[cc][a];
+                C rs, jsx, jsy, jsz;
+                moments<C>(fs, rs, jsx, jsy, jsz);
+                const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
+                const C dX = sh.nrm[cc][1][0] - sh.nrm[cc][2][0];
+                const C dY = sh.nrm[cc][3][1] - sh.nrm[cc][4][1];
+                const C dZ = sh.nrm[cc][5][2] - sh.nrm[cc][6][2];
+                const C kappa = (C)0.25 * ((dX + dY) + dZ);
+                const C gx = sh.nrm[cc][0][0], gy = sh.nrm[cc][0][1], gz = sh.nrm[cc][0][2];
+                const C pg = (C)sh.pv[cc] + (C)D.sigma2 * kappa;
+                const C rg = (C)3 * pg;
+                C fg[19];
+                feq_all<C>(rg, ugx, ugy, ugz, fg);
+                C fin[19];
+                fin[0] = fs[0];
+#pragma unroll
+                for (int a = 1; a < 19; ++a) {
+                    const int ab = opp(a);
+                    const uint8_t ty = sh.ty[cc][a];
+                    if (ty == OBS) {
+                        fin[a] = fs[ab];
+                    } else if (ty == LID) {
+                        const C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
+                        fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
+                    } else if (ty == GAS) {
+                        fin[a] = (fg[a] + fg[ab]) - fs[ab];
+                    } else {
+                        fin[a] = sh.fy[cc][a];
+                        if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
+                    }
+                }
+                // mass exchange, summed in direction order (Eq. 10)
+                double dm = 0.0;
+#pragma unroll
+                for (int a = 1; a < 19; ++a) {
+                    const uint8_t tz = sh.tz[cc][a];
+                    if (tz == LIQ || tz == IFC) dm = dm + sh.ex[cc][a];
+                }
+                const double mnew = sh.m[cc] + dm;
+                C fout[19];
+                const C rho =
+                    collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+                if (!(rho == rho)) set_status(A.status, ST_NAN);
+#pragma unroll
+                for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
+                const double r = (double)rho;
+                A.m[g] = mnew;
+                A.rhoi[g] = r;
+                if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
+                else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
+                A.mark[g] = mk;
+            }
+            list_append(A.mlist, A.mcount, mk != MK_NONE, (int)g);
+        }
+        __syncthreads();
     }
 }
 
@@ -627,76 +762,107 @@ __device__ inline long long first_marked(const StepArgs& A, const Dom& D, long l
     return -1;
 }
 
-// C2 (conversion phase B), over the marked list and the new-from-gas list.
-// An emptied cell that kept its mark turns each liquid neighbour into
-// interface when it is that neighbour's first emptied neighbour in direction
-// order (so each new cell is claimed once, by the bubble of its first emptied
-// neighbour; m = rho of its own PDFs).  A new interface cell from gas gets
-// f = f_eq of the mean density and velocity of its liquid and non-emptied
-// interface neighbours, m = 0.
+// C2 (conversion phase B).  First part, one thread per (marked cell,
+// direction): an emptied cell that kept its mark turns the liquid neighbour in
+// that direction into interface when it is that neighbour's first emptied
+// neighbour in direction order (so each new cell is claimed once, by the
+// bubble of its first emptied neighbour; m = rho of its own PDFs).  Second
+// part, one warp per new interface cell from gas: lanes 1-18 take the density
+// and velocity of the liquid or non-emptied interface neighbour in their
+// direction, lane 0 sums them in direction order and sets f = f_eq of the
+// means, m = 0.
 template <typename T>
 __global__ void __launch_bounds__(128) k_convert_b(StepArgs A) {
     using C = typename Form<T>::C;
+    pdl_wait();
+    pdl_trigger();
+    const unsigned full = 0xffffffffu;
     const int nm = *A.mcount, ng = *A.gcount;
-    const int total = nm + ng;
+    const int p1 = (18 * nm + 31) & ~31;          // first part, padded to whole warps
+    const int total = p1 + 32 * ng;
     const long long S = A.stride;
     T* f = (T*)A.fdst;
     const int stride = gridDim.x * blockDim.x;
     for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
-        const int i = base + threadIdx.x;
-        const bool valid = i < total;
-        long long p = 0;
-        if (valid) p = i < nm ? A.mlist[i] : A.glist[i - nm];
-        const int d = valid ? A.blk_dom[p / FSL_BLOCK] : 0;
-        const Dom& D = A.doms[d];
-        const bool emptied = valid && i < nm && A.mark[p] == MK_EMPTIED;
-        const Cell c = make_cell(D, valid ? p : D.off);
-        for (int a = 1; a < 19; ++a) {
+        const int t = base + threadIdx.x;
+        if (base + (int)(threadIdx.x & ~31) < p1) {
+            // claims of liquid neighbours by emptied cells
+            const bool valid = t < 18 * nm;
             bool claim = false;
             long long z = 0;
-            if (emptied) {
-                z = c.at(cx(a), cy(a), cz(a));
-                if (ctype(A.flag[z]) == LIQ && first_marked(A, D, z, MK_EMPTIED) == p) {
-                    claim = true;
-                    double r = (double)Form<T>::ld(f + z, 0);
-                    for (int q = 1; q < 19; ++q) r = r + (double)Form<T>::ld(f + (long long)q * S + z, q);
-                    A.mark[z] = MK_NEWL;
-                    A.id[z] = A.id[p];
-                    A.m[z] = r;
-                    A.rhoi[z] = r;
-                    atomicAdd((unsigned long long*)&A.nif[d], 1ull);
+            if (valid) {
+                const long long p = A.mlist[t / 18];
+                const int a = 1 + t % 18;
+                if (A.mark[p] == MK_EMPTIED) {
+                    const int d = block_dom(A, p);
+                    const Dom D = get_dom(A, d);
+                    const Cell c = make_cell(D, p);
+                    z = c.at(cx(a), cy(a), cz(a));
+                    if (ctype(A.flag[z]) == LIQ && first_marked(A, D, z, MK_EMPTIED) == p) {
+                        claim = true;
+                        double r = (double)Form<T>::ld(f + z, 0);
+                        for (int q = 1; q < 19; ++q) r = r + (double)Form<T>::ld(f + (long long)q * S + z, q);
+                        A.mark[z] = MK_NEWL;
+                        A.id[z] = A.id[p];
+                        A.m[z] = r;
+                        A.rhoi[z] = r;
+                        atomicAdd((unsigned long long*)&A.nif[d], 1ull);
+                    }
                 }
             }
             list_append(A.llist, A.lcount, claim, (int)z);
+            continue;
         }
-        if (!valid || i < nm) continue;
-        // new interface cell from gas
-        C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
-        int cnt = 0;
-        for (int a = 1; a < 19; ++a) {
+        // new interface cell from gas, one warp per cell
+        const int w = (t - p1) >> 5;
+        const int lane = threadIdx.x & 31;
+        if (w >= ng) continue;
+        const long long p = A.glist[w];
+        const Dom D = get_dom(A, block_dom(A, p));
+        C r = (C)1, ux = (C)0, uy = (C)0, uz = (C)0;
+        int use = 0;
+        if (lane >= 1 && lane <= 18) {
+            const Cell c = make_cell(D, p);
+            const int a = lane;
             const long long z = c.at(cx(a), cy(a), cz(a));
             const uint8_t tz = ctype(A.flag[z]);
             if (tz == LIQ || (tz == IFC && A.mark[z] != MK_EMPTIED)) {
                 C fo[19];
 #pragma unroll
                 for (int q = 0; q < 19; ++q) fo[q] = Form<T>::ld(f + (long long)q * S + z, q);
-                C r, jx, jy, jz;
+                C jx, jy, jz;
                 moments<C>(fo, r, jx, jy, jz);
-                sr = sr + r;
-                sux = sux + jx / r;
-                suy = suy + jy / r;
-                suz = suz + jz / r;
+                ux = jx / r; uy = jy / r; uz = jz / r;
+                use = 1;
+            }
+        }
+        C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
+        int cnt = 0;
+#pragma unroll
+        for (int a = 1; a < 19; ++a) {
+            const int ua = __shfl_sync(full, use, a);
+            const C ra = __shfl_sync(full, r, a);
+            const C xa = __shfl_sync(full, ux, a);
+            const C ya = __shfl_sync(full, uy, a);
+            const C za = __shfl_sync(full, uz, a);
+            if (ua) {
+                sr = sr + ra;
+                sux = sux + xa;
+                suy = suy + ya;
+                suz = suz + za;
                 ++cnt;
             }
         }
-        const C rbar = sr / (C)cnt;
-        const C ux = sux / (C)cnt, uy = suy / (C)cnt, uz = suz / (C)cnt;
-        C fe[19];
-        feq_all<C>(rbar, ux, uy, uz, fe);
+        if (lane == 0) {
+            const C rbar = sr / (C)cnt;
+            const C vx = sux / (C)cnt, vy = suy / (C)cnt, vz = suz / (C)cnt;
+            C fe[19];
+            feq_all<C>(rbar, vx, vy, vz, fe);
 #pragma unroll
-        for (int q = 0; q < 19; ++q) Form<T>::st(f + (long long)q * S + p, q, fe[q]);
-        A.m[p] = 0.0;
-        A.rhoi[p] = (double)rbar;
+            for (int q = 0; q < 19; ++q) Form<T>::st(f + (long long)q * S + p, q, fe[q]);
+            A.m[p] = 0.0;
+            A.rhoi[p] = (double)rbar;
+        }
     }
 }
 
@@ -706,7 +872,7 @@ template <typename T>
 __global__ void __launch_bounds__(FSL_BLOCK) k_init_state(StepArgs A, int d, const uint8_t* flags_in,
                                                          const double* fill, const double* rho, const double* u) {
     using C = typename Form<T>::C;
-    const Dom& D = A.doms[d];
+    const Dom D = get_dom(A, d);
     const long long l = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     if (l >= D.n) return;
     const long long g = D.off + l;
@@ -728,6 +894,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_init_state(StepArgs A, int d, con
     A.exs[g] = 0.0;
     double ph = (t == LIQ) ? 1.0 : (t == IFC ? fill[l] : 0.0);
     A.phi[g] = ph;
+    A.phit[g] = (t == LIQ || t == OBS || t == LID) ? 1.0 : (t == GAS ? 0.0 : (ph < 0.0 ? 0.0 : (ph > 1.0 ? 1.0 : ph)));
     T* f = (T*)A.fdst;
     if (t == LIQ || t == IFC) {
         C fe[19];
@@ -780,14 +947,13 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         /* liquid cells on s, interface cells on s2 at the same time (disjoint outputs) */                  \
         cudaEventRecord(fork, s);                                                                            \
         cudaStreamWaitEvent(s2, fork, 0);                                                                    \
-        k_surface_normals<typename Form<T>::C><<<(unsigned)ifb, 128, 0, s2>>>(A);                           \
-        k_stream_interface<T><<<(unsigned)ifb, 128, 0, s2>>>(A);                                            \
+        k_stream_interface<T><<<(unsigned)ifb, 256, 0, s2>>>(A);                                            \
         k_stream_liquid<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                           \
         cudaEventRecord(join, s2);                                                                           \
         cudaStreamWaitEvent(s, join, 0);                                                                     \
     }                                                                                                        \
     template <> void launch_convert_b<T>(const StepArgs& A, long long nb, cudaStream_t s) {                  \
-        k_convert_b<T><<<(unsigned)nb, 128, 0, s>>>(A);                                                     \
+        launch_pdl(k_convert_b<T>, (unsigned)nb, 128u, s, A);                                                \
     }                                                                                                        \
     template <> void launch_init_state<T>(const StepArgs& A, int d, int n, const uint8_t* fl,                \
                                           const double* fill, const double* rho, const double* u,            \

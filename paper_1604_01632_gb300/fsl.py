@@ -28,7 +28,7 @@ FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.flo
 EXPORTS = ["fsl_create", "fsl_init_geometry", "fsl_set_bubble_source", "fsl_step", "fsl_sync", "fsl_bubbles",
            "fsl_fields", "fsl_destroy", "fsl_last_error", "fsl_kernel_launches", "fsl_set_timing",
            "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs",
-           "fsl_label_bubbles_static"]
+           "fsl_label_bubbles_static", "fsl_phase_ms"]
 
 
 class FslError(RuntimeError):
@@ -93,6 +93,8 @@ def load_library():
     L.fsl_stream_collide_ms.argtypes = [vp]
     L.fsl_label_bubbles_static.restype = i32
     L.fsl_label_bubbles_static.argtypes = [vp, i32, i32, i32, vp, vp]
+    L.fsl_phase_ms.restype = i32
+    L.fsl_phase_ms.argtypes = [vp, vp]
     L.fsl_set_graphs.restype = i32
     L.fsl_set_graphs.argtypes = [vp, i32]
     L.fsl_labelling_runs.restype = i64
@@ -267,6 +269,11 @@ class Simulation:
 
     def set_graphs(self, on: bool):
         self._check(self.L.fsl_set_graphs(self._h, 1 if on else 0))
+
+    def phase_ms(self) -> Dict[str, float]:
+        out = (ctypes.c_double * 6)()
+        self._check(self.L.fsl_phase_ms(self._h, out))
+        return dict(zip(("stream_collide", "phase_a", "phase_b", "excess", "update", "labelling"), list(out)))
 
     def stream_collide_ms(self) -> float:
         return float(self.L.fsl_stream_collide_ms(self._h))
