@@ -438,7 +438,14 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e != cudaSuccess) { fsl_status st = cuda_fail(h, e, "tables"); delete h; return st; }
     e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ls2, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ls3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // the interface kernel is a short latency-bound chain: give its stream
+        // the highest priority so that its blocks are placed before the
+        // liquid kernel's
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        e = cudaStreamCreateWithPriority(&h->ls3, cudaStreamNonBlocking, hi);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) {

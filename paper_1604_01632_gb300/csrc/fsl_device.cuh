@@ -468,7 +468,7 @@ __device__ inline Pull make_pull(const Dom& D, long long g) {
 // liquid cells.  Only cells flagged as touching a wall read the types of
 // their neighbours; a liquid cell never touches gas (closed interface layer).
 template <typename T>
-__global__ void __launch_bounds__(FSL_BLOCK) k_stream_liquid(StepArgs A) {
+__global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
     using C = typename Form<T>::C;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     const uint8_t f = A.flag[g];
@@ -947,7 +947,7 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         /* liquid cells on s, interface cells on s2 at the same time (disjoint outputs) */                  \
         cudaEventRecord(fork, s);                                                                            \
         cudaStreamWaitEvent(s2, fork, 0);                                                                    \
-        k_stream_interface<T><<<(unsigned)ifb, 256, 0, s2>>>(A);                                            \
+        k_stream_interface<T><<<(unsigned)(2 * ifb), 256, 0, s2>>>(A);                                      \
         k_stream_liquid<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                           \
         cudaEventRecord(join, s2);                                                                           \
         cudaStreamWaitEvent(s, join, 0);                                                                     \
