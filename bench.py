@@ -229,6 +229,12 @@ def run_gpu(args, rank: int, world: int):
                               "stream_collide_frac": round(vb / (vk1 / kk * 1e-3) / 1e9 / peak, 3)}
             v.close()
 
+    # batched bubble populations: 64 independent domains in one handle (one
+    # graph per step) against the same domains stepped as 64 separate handles
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = run_batched(args, fsl, torch, stream, flush)
+
     # end to end through the C ABI from host buffers: upload the initial state,
     # K steps, read back the fields and the bubble table
     e2e = None
@@ -271,9 +277,59 @@ def run_gpu(args, rank: int, world: int):
                          "kernel": KERNEL, "algorithmic_bytes_per_launch": int(abytes),
                          "avg_launch_ms": round(k1_avg, 5), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "variants": variants, "phase_us_per_step_direct_launch": phases,
+            "variants": variants, "phase_us_per_step_direct_launch": phases, "batched": batched,
         }
         print(json.dumps(line))
+
+
+def run_batched(args, fsl, torch, stream, flush, steps: int = 20):
+    """64 domains of 32-96 cells per axis with 20-200 bubbles each, FP16-shifted
+    storage: one handle advancing all domains per launch, against a loop over 64
+    single-domain handles."""
+    from paper_1604_01632_gb300 import scenarios as S
+    doms = S.bubble_population(n_domains=64, seed=0)
+    cells = sum(d.n for d in doms)
+    out = {"domains": len(doms), "cells": cells, "steps": steps, "storage": args.precision}
+
+    def timed(step_fn, sync_fn):
+        for _ in range(3):
+            flush.zero_()
+            step_fn()
+        sync_fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record()
+            step_fn()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        sync_fn()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    sim = fsl.Simulation.from_scenarios(doms, precision=args.precision, stream=int(stream.cuda_stream))
+    r0 = sim.labelling_runs
+    ms = timed(lambda: sim.step(1), sim.sync)
+    out["batched_mlups"] = round(cells * steps / (ms * 1e-3) / 1e6, 1)
+    out["batched_ms_per_step"] = round(ms / steps, 4)
+    out["labelling_runs_per_step"] = round((sim.labelling_runs - r0) / (steps + 3), 3)
+    sim.close()
+    sims = [fsl.Simulation.from_scenarios([d], precision=args.precision, stream=int(stream.cuda_stream)) for d in doms]
+
+    def step_all():
+        for x in sims:
+            x.step(1)
+
+    def sync_all():
+        for x in sims:
+            x.sync()
+
+    ms = timed(step_all, sync_all)
+    out["looped_mlups"] = round(cells * steps / (ms * 1e-3) / 1e6, 1)
+    out["looped_ms_per_step"] = round(ms / steps, 4)
+    for x in sims:
+        x.close()
+    return out
 
 
 def cpu_baseline(sc, steps: int):
@@ -324,6 +380,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="direct kernel launches (for ncu)")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

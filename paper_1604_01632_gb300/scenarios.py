@@ -243,30 +243,62 @@ def orifice(nx: int = 128, ny: int = 128, nz: int = 256, plate_z: int = 8, hole_
 
 
 def _rsa(rng, dims, radii, gap, max_attempts, periodic=True):
-    """Random sequential addition of non-overlapping spheres with a liquid gap."""
-    placed_c, placed_r = [], []
+    """Random sequential addition of non-overlapping spheres with a liquid gap:
+    each sphere in turn draws random centres until one keeps the gap to every
+    sphere placed so far; all draws together are capped at max_attempts."""
     dims = np.asarray(dims, dtype=np.float64)
+    pc = np.zeros((len(radii), 3))
+    pr = np.zeros(len(radii))
+    n = 0
     attempts = 0
     for r in radii:
-        ok = False
-        while attempts < max_attempts and not ok:
-            attempts += 1
-            c = rng.uniform(0.0, 1.0, 3) * dims
-            good = True
-            for pc, pr in zip(placed_c, placed_r):
-                d = c - pc
+        placed = False
+        while attempts < max_attempts and not placed:
+            # a batch of candidate centres tested against all placed spheres
+            batch = int(min(256, max_attempts - attempts))
+            cand = rng.uniform(0.0, 1.0, (batch, 3)) * dims
+            if n == 0:
+                ok = np.ones(batch, dtype=bool)
+            else:
+                d = cand[:, None, :] - pc[None, :n, :]
                 if periodic:
                     d -= dims * np.round(d / dims)
-                if np.sqrt((d * d).sum()) < r + pr + gap:
-                    good = False
-                    break
-            if good:
-                placed_c.append(c)
-                placed_r.append(r)
-                ok = True
+                dist = np.sqrt((d * d).sum(-1))
+                ok = (dist >= (r + pr[:n] + gap)[None, :]).all(1)
+            hit = np.nonzero(ok)[0]
+            if hit.size:
+                attempts += int(hit[0]) + 1
+                pc[n] = cand[hit[0]]
+                pr[n] = r
+                n += 1
+                placed = True
+            else:
+                attempts += batch
         if attempts >= max_attempts:
             break
-    return np.array(placed_c).reshape(-1, 3), np.array(placed_r)
+    return pc[:n].copy(), pr[:n].copy()
+
+
+def _stamp_spheres(shape, centres, radii, sub: int = 4) -> np.ndarray:
+    """Liquid fraction of a periodic box holding non-overlapping gas spheres:
+    each sphere is sub-sampled only inside its own bounding box."""
+    nz, ny, nx = shape
+    fill = np.ones(shape)
+    offs = (np.arange(sub, dtype=np.float64) + 0.5) / sub - 0.5
+    for c, r in zip(centres, radii):
+        lo = np.floor(np.asarray(c) - r - 1).astype(int)
+        hi = np.ceil(np.asarray(c) + r + 1).astype(int)
+        zi = np.arange(lo[2], hi[2]); yi = np.arange(lo[1], hi[1]); xi = np.arange(lo[0], hi[0])
+        zz, yy, xx = np.meshgrid(zi, yi, xi, indexing="ij")
+        cnt = np.zeros(zz.shape)
+        for oz in offs:
+            for oy in offs:
+                for ox in offs:
+                    d2 = (xx + 0.5 + ox - c[0]) ** 2 + (yy + 0.5 + oy - c[1]) ** 2 + (zz + 0.5 + oz - c[2]) ** 2
+                    cnt += d2 < r * r
+        sl = (np.mod(zz, nz), np.mod(yy, ny), np.mod(xx, nx))
+        fill[sl] = np.minimum(fill[sl], 1.0 - cnt / float(sub ** 3))
+    return fill
 
 
 def _periodic_spheres_sdf(centres, radii, dims):
@@ -293,8 +325,7 @@ def random_bubbles(nx: int, ny: int, nz: int, n_bubbles: int, r_min: float, r_ma
     radii = rng.uniform(r_min, r_max, n_bubbles)
     centres, radii = _rsa(rng, (nx, ny, nz), radii, gap, max_attempts)
     shape = (nz, ny, nx)
-    sdf = _periodic_spheres_sdf(centres, radii, (nx, ny, nz))
-    fill = liquid_fraction(shape, sdf)
+    fill = _stamp_spheres(shape, centres, radii)
     flags = classify(fill)
     x, y, z = _centres(shape)
     u = np.zeros((3,) + shape)
