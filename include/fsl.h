@@ -67,6 +67,9 @@ typedef struct {
     double lid_velocity[3];   /* velocity of FSL_LID cells */
     int32_t normal_rule;      /* 1: also rebuild PDFs whose direction has n.c < 0 (paper Eq. 11 text) */
     int32_t bubble_capacity;  /* bubble-table slots for this domain; 0 = default */
+    int32_t lonely_rule;      /* 1: an interface cell with no gas neighbour fills, one with no liquid
+                                 neighbour empties (it no longer separates liquid from gas) */
+    int32_t reserved;         /* set to 0 */
 } fsl_params;
 
 /* One bubble (paper Sec. 2.3): id = minimum linear index of its gas and

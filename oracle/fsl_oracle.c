@@ -39,7 +39,10 @@
  *   - kappa = 1/2 div(n_hat) by central differences of n_hat at the six face
  *     neighbours; kappa < 0 on a bubble, so the liquid next to a bubble of
  *     radius R sees p_V - 2 sigma / R.
- *   - Conversion: filled if m > (1+eps) rho, emptied if m < -eps rho; phase A
+ *   - Conversion: filled if m > (1+eps) rho, emptied if m < -eps rho; an
+ *     interface cell with no gas neighbour also counts as filled, one with no
+ *     liquid neighbour as emptied (it no longer separates liquid from gas, and
+ *     left alone it would form bubbles of zero volume); phase A
  *     (filled cells turn gas neighbours into interface, cancel emptied marks
  *     next to them), phase B (emptied cells turn liquid neighbours into
  *     interface).  New interface cells from gas get f = f_eq of the mean
@@ -601,6 +604,19 @@ static void step_once(ora_sim* s) {
             s->rhoi[i] = rho;
             if (mnew > (1.0 + eps) * rho) s->mark[i] = MK_FILLED;
             else if (mnew < (-eps) * rho) s->mark[i] = MK_EMPTIED;
+            else if (P->lonely_rule) {
+                /* an interface cell that no longer separates liquid from gas:
+                 * without a gas neighbour it becomes liquid, without a liquid
+                 * neighbour it becomes gas (types at the start of the step) */
+                int has_gas = 0, has_liq = 0;
+                for (int a = 1; a < 19; ++a) {
+                    uint8_t tz = s->flag[nbr(s, i, CX[a], CY[a], CZ[a])];
+                    if (tz == GAS) has_gas = 1;
+                    if (tz == LIQ) has_liq = 1;
+                }
+                if (!has_gas) s->mark[i] = MK_FILLED;
+                else if (!has_liq) s->mark[i] = MK_EMPTIED;
+            }
         }
     }
     for (int64_t i = 0; i < n; ++i) {

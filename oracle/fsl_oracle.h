@@ -32,6 +32,7 @@ typedef struct {
     double eps;             /* conversion threshold */
     double lid[3];          /* moving-wall velocity (cell type 4) */
     int32_t normal_rule;    /* 1: also rebuild PDFs with n.c < 0; 0: gas links only */
+    int32_t lonely_rule;    /* 1: interface cells without gas (liquid) neighbours fill (empty) */
 } ora_params;
 
 typedef struct {

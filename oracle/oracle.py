@@ -32,7 +32,7 @@ class Params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("collision", ctypes.c_int32), ("tau", ctypes.c_double), ("magic", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("g", ctypes.c_double * 3), ("eps", ctypes.c_double),
-                ("lid", ctypes.c_double * 3), ("normal_rule", ctypes.c_int32)]
+                ("lid", ctypes.c_double * 3), ("normal_rule", ctypes.c_int32), ("lonely_rule", ctypes.c_int32)]
 
 
 class Bubble(ctypes.Structure):
@@ -87,7 +87,7 @@ def _ptr(a: np.ndarray):
 
 
 def make_params(nx, ny, nz, collision=0, tau=0.8, magic=3.0 / 16.0, sigma=0.0, gravity=(0.0, 0.0, 0.0),
-                eps=1e-3, lid=(0.0, 0.0, 0.0), normal_rule=1) -> Params:
+                eps=1e-3, lid=(0.0, 0.0, 0.0), normal_rule=1, lonely_rule=1) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = nx, ny, nz
     p.collision, p.tau, p.magic, p.sigma = collision, tau, magic, sigma
@@ -96,6 +96,7 @@ def make_params(nx, ny, nz, collision=0, tau=0.8, magic=3.0 / 16.0, sigma=0.0, g
         p.lid[k] = lid[k]
     p.eps = eps
     p.normal_rule = normal_rule
+    p.lonely_rule = lonely_rule
     return p
 
 

@@ -418,6 +418,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         div_magic(p.nx, D.mgx, D.shx);
         div_magic(p.ny, D.mgy, D.shy);
         D.has_force = (p.gravity[0] != 0.0 || p.gravity[1] != 0.0 || p.gravity[2] != 0.0) ? 1 : 0;
+        D.lonely_rule = p.lonely_rule;
         h->hdoms.push_back(D);
         long long padded = (n + FSL_BLOCK - 1) / FSL_BLOCK * FSL_BLOCK;
         for (long long b = 0; b < padded / FSL_BLOCK; ++b) h->blk_dom.push_back(d);
@@ -478,7 +479,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->constp, 4 * NS);
     AL(h->pool, 8 * n_domains);
     AL(h->nif, 8 * n_domains);
-    AL(h->trig, sizeof(int));
+    AL(h->trig, sizeof(int) * (n_domains + 1));
     AL(h->status, sizeof(int));
     AL(h->ilist[0], 4 * N);
     AL(h->ilist[1], 4 * N);
@@ -533,7 +534,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->f[1], 0, 19 * N * h->fbytes);
     if (e == cudaSuccess) e = cudaMemset(h->pool, 0, 8 * n_domains);
     if (e == cudaSuccess) e = cudaMemset(h->nif, 0, 8 * n_domains);
-    if (e == cudaSuccess) e = cudaMemset(h->trig, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->trig, 0, sizeof(int) * (n_domains + 1));
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->icount[0], 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->icount[1], 0, sizeof(int));

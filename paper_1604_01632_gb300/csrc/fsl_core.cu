@@ -154,7 +154,10 @@ __global__ void __launch_bounds__(128) k_convert_c(StepArgs A) {
                             if (ntz == GAS || ntz == IFC || later_filled)
                                 fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
                         }
-                if (!removal_is_local(fgm)) atomicExch(A.trig, 1);
+                if (!removal_is_local(fgm)) {
+                    atomicExch(&A.trig[1 + d], 1);
+                    atomicExch(A.trig, 1);
+                }
             }
             A.cstep[g] = step;
             A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(128) k_convert_c(StepArgs A) {
             const long long z = c.at(cx(a), cy(a), cz(a));
             const uint8_t ntz = new_type(ctype(A.flag[z]), A.mark[z]);
             if ((ntz == GAS || ntz == IFC) && A.id[z] != b) {
+                atomicExch(&A.trig[1 + d], 1);
                 atomicExch(A.trig, 1);
                 break;
             }
@@ -315,10 +319,16 @@ __device__ inline bool unite(int* L, int a, int b, int cap) {
     return false;
 }
 
+// Domain of a block taking part in this labelling pass (every domain after
+// initialisation, else the domains whose step set the trigger).
+__device__ inline bool ccl_active(const StepArgs& A, const CclArgs& K, int d) {
+    return K.initial || A.trig[1 + d] != 0;
+}
+
 __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_init(StepArgs A, CclArgs K) {
     if (!K.initial && *A.trig == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    K.lab[g] = is_fg(A.flag[g]) ? (int)g : -1;
+    if (ccl_active(A, K, block_dom(A, g))) K.lab[g] = is_fg(A.flag[g]) ? (int)g : -1;
     const long long nth = (long long)gridDim.x * FSL_BLOCK;
     for (long long h = g; h < K.hcap; h += nth) {
         K.hkeys[h] = ~0ull;
@@ -330,13 +340,14 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_init(StepArgs A, CclArgs K) {
         K.vtot[s] = 0;
         K.minc[s] = INT_MAX;
     }
-    for (long long dd = g; dd < A.ndom; dd += nth) K.nslot[dd] = 0;
+    for (long long dd = g; dd < A.ndom; dd += nth)
+        if (ccl_active(A, K, (int)dd)) K.nslot[dd] = 0;
 }
 
 __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_hook(StepArgs A, CclArgs K) {
     if (!K.initial && *A.trig == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    if (!is_fg(A.flag[g])) return;
+    if (!ccl_active(A, K, block_dom(A, g)) || !is_fg(A.flag[g])) return;
     const Dom D = get_dom(A, block_dom(A, (long long)blockIdx.x * FSL_BLOCK));
     const Cell c = make_cell(D, g);
     // the nine directions 1, 3, ..., 17 cover each neighbour pair once
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_hook(StepArgs A, CclArgs K) {
 __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_compress(StepArgs A, CclArgs K) {
     if (!K.initial && *A.trig == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    if (!is_fg(A.flag[g])) return;
+    if (!ccl_active(A, K, block_dom(A, g)) || !is_fg(A.flag[g])) return;
     bool ok = true;
     const int r = find_root(K.lab, (int)g, K.max_iter, ok);
     if (!ok) { set_status(A.status, ST_CCL); return; }
@@ -389,6 +400,7 @@ __device__ inline void hash_add(const CclArgs& K, unsigned long long key, long l
 __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_pairs(StepArgs A, CclArgs K) {
     if (!K.initial && *A.trig == 0) return;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    if (!ccl_active(A, K, block_dom(A, g))) return;   // whole block: one domain
     const uint8_t t = ctype(A.flag[g]);
     int c = -1;
     long long term = 0;
@@ -449,6 +461,7 @@ __global__ void k_ccl_install(StepArgs A, CclArgs K, long long* vsfx, int* const
     const long long nth = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < K.nslots_total; s += nth) {
         const int d = K.slot_dom[s];
+        if (!ccl_active(A, K, d)) continue;   // untouched domains keep their table
         const Dom D = get_dom(A, d);
         const int k = (int)(s - D.slot_off);
         if (k < K.nslot[d]) {

@@ -56,6 +56,7 @@ struct Dom {
     unsigned mgx, mgy;          // x = l - nx*(l/nx) etc. by multiply-high: l/nx = umulhi(l, mgx) >> shx
     int shx, shy;               // (shift -1: the divisor is 1)
     int has_force;              // gravity is not zero
+    int lonely_rule;            // interface cells without gas / liquid neighbours fill / empty
 };
 
 // Invariant-divisor division for 0 <= n < 2^31: with s = ceil(log2 d) and
@@ -101,7 +102,7 @@ struct StepArgs {
     const int* constp;          // bubble constant-pressure flag (slot)
     long long* pool;            // per-domain pooled excess mass, fixed point 2^-40
     long long* nif;             // per-domain interface count after conversion
-    int* trig;                  // merge/split trigger (any domain)
+    int* trig;                  // merge/split trigger: [0] any domain, [1 + d] domain d
     int* status;
     int ndom;
     int* ilist;                 // interface cells at the start of this step
@@ -607,6 +608,7 @@ __global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
             if (A.nif[d] > 0) A.pool[d] = 0;   // the pool was shared out last step
             A.nif[d] = A.icnt[d];
+            A.trig[1 + d] = 0;
         }
         if (threadIdx.x == 0) {
             *A.stepno += 1;
@@ -743,6 +745,17 @@ __global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
                 A.rhoi[g] = r;
                 if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
                 else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
+                else if (D.lonely_rule) {
+                    // a cell that no longer separates liquid from gas
+                    bool has_gas = false, has_liq = false;
+#pragma unroll
+                    for (int a = 1; a < 19; ++a) {
+                        has_gas |= sh.tz[cc][a] == GAS;
+                        has_liq |= sh.tz[cc][a] == LIQ;
+                    }
+                    if (!has_gas) mk = MK_FILLED;
+                    else if (!has_liq) mk = MK_EMPTIED;
+                }
                 A.mark[g] = mk;
             }
             list_append(A.mlist, A.mcount, mk != MK_NONE, (int)g);

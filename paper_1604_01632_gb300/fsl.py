@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("collision", ctypes.c_int32), ("tau", ctypes.c_double), ("magic", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("eps", ctypes.c_double),
                 ("lid_velocity", ctypes.c_double * 3), ("normal_rule", ctypes.c_int32),
-                ("bubble_capacity", ctypes.c_int32)]
+                ("bubble_capacity", ctypes.c_int32), ("lonely_rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BubbleRec(ctypes.Structure):
@@ -106,7 +106,7 @@ def load_library():
 
 
 def make_params(nx, ny, nz, collision=0, tau=0.8, magic=3.0 / 16.0, sigma=0.0, gravity=(0.0, 0.0, 0.0),
-                eps=1e-3, lid=(0.0, 0.0, 0.0), normal_rule=1, bubble_capacity=0) -> Params:
+                eps=1e-3, lid=(0.0, 0.0, 0.0), normal_rule=1, lonely_rule=1, bubble_capacity=0) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = nx, ny, nz
     p.collision, p.tau, p.magic, p.sigma = collision, tau, magic, sigma
@@ -115,7 +115,9 @@ def make_params(nx, ny, nz, collision=0, tau=0.8, magic=3.0 / 16.0, sigma=0.0, g
         p.lid_velocity[k] = lid[k]
     p.eps = eps
     p.normal_rule = normal_rule
+    p.lonely_rule = lonely_rule
     p.bubble_capacity = bubble_capacity
+    p.reserved = 0
     return p
 
 

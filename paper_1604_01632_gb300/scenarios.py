@@ -57,6 +57,7 @@ class Scenario:
     eps: float = 1e-3
     lid: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     normal_rule: int = 1
+    lonely_rule: int = 1
     # (seed cell, extra volume, volume drain per step, constant pressure)
     sources: List[Tuple[int, float, float, int]] = dataclasses.field(default_factory=list)
     steps: int = 0
@@ -68,7 +69,7 @@ class Scenario:
     def params(self) -> dict:
         return dict(nx=self.nx, ny=self.ny, nz=self.nz, collision=self.collision, tau=self.tau,
                     magic=self.magic, sigma=self.sigma, gravity=tuple(self.gravity), eps=self.eps,
-                    lid=tuple(self.lid), normal_rule=self.normal_rule)
+                    lid=tuple(self.lid), normal_rule=self.normal_rule, lonely_rule=self.lonely_rule)
 
     def linear(self, x: int, y: int, z: int) -> int:
         return int(x + self.nx * (y + self.ny * z))
