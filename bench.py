@@ -156,7 +156,7 @@ def run_gpu(args, rank: int, world: int):
             sim.set_graphs(False)
         return sim
 
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = L2Flush(torch, args.flush)
     meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = float(meas_peaks["hbm_gbs"]) if meas_peaks else 6800.0
@@ -164,7 +164,7 @@ def run_gpu(args, rank: int, world: int):
     def timed_steps(sim, K, W, timing=True):
         sim.set_timing(timing)
         for _ in range(W):
-            flush.zero_()
+            flush()
             sim.step(1)
         sim.sync()
         sim.set_timing(timing)
@@ -176,7 +176,7 @@ def run_gpu(args, rank: int, world: int):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         for k in range(K):
-            flush.zero_()
+            flush()
             ev[k][0].record()
             sim.step(1)
             ev[k][1].record()
@@ -268,7 +268,7 @@ def run_gpu(args, rank: int, world: int):
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": wl_desc, "cells": n, "storage": args.precision,
-                       "l2": "flushed (256 MB write) before every timed step; steps timed by CUDA events",
+                       "l2": flush.describe() + " before every timed step; steps timed by CUDA events",
                        "parallelism": f"replicas x{world}",
                        "labelling_runs_per_step": round(lruns / args.steps, 3),
                        "cell_counts_liquid_interface_gas_obstacle": [int(c) for c in counts[:4]]},
@@ -282,6 +282,29 @@ def run_gpu(args, rank: int, world: int):
         print(json.dumps(line))
 
 
+class L2Flush:
+    """Empties the 129 MB L2 before a timed step: a 256 MB write, then (mode
+    "write+read") a 256 MB read of a second buffer, so that the lines left in
+    L2 are clean and the timed step does not pay for writing back the flush
+    buffer's dirty lines."""
+
+    def __init__(self, torch, mode):
+        self.mode = mode
+        self.torch = torch
+        self.w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        self.r = torch.ones(32 << 20, dtype=torch.int64, device="cuda") if mode == "write+read" else None
+
+    def __call__(self):
+        self.w.zero_()
+        if self.r is not None:
+            self.r.sum()
+
+    def describe(self):
+        if self.mode == "write+read":
+            return "flushed (256 MB write, then 256 MB read of another buffer: no dirty lines left)"
+        return "flushed (256 MB write)"
+
+
 def run_batched(args, fsl, torch, stream, flush, steps: int = 20):
     """64 domains of 32-96 cells per axis with 20-200 bubbles each, FP16-shifted
     storage: one handle advancing all domains per launch, against a loop over 64
@@ -293,13 +316,13 @@ def run_batched(args, fsl, torch, stream, flush, steps: int = 20):
 
     def timed(step_fn, sync_fn):
         for _ in range(3):
-            flush.zero_()
+            flush()
             step_fn()
         sync_fn()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
         for k in range(steps):
-            flush.zero_()
+            flush()
             ev[k][0].record()
             step_fn()
             ev[k][1].record()
@@ -381,6 +404,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="direct kernel launches (for ncu)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--flush", default="write+read", choices=["write", "write+read"],
+                    help="L2 flush between timed steps")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

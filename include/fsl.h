@@ -169,9 +169,11 @@ fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
 
 /* Device time per phase of the steps timed since fsl_set_timing(h, 1), summed,
  * in milliseconds, when the handle runs without graphs (fsl_set_graphs(h, 0)):
- * out[0] stream-collide (liquid and interface kernels), out[1] conversion
- * phase A, out[2] phase B, out[3] excess mass and triggers, out[4] fill-level
- * and volume update, out[5] labelling.  Read after fsl_sync. */
+ * out (array of 7): [0] stream-collide (liquid and interface kernels, which run
+ * at the same time), [1] start of the pair to the end of the liquid kernel, [2]
+ * start of the pair to the end of the interface kernel, [3] conversion phases
+ * A and B, [4] excess mass and triggers, [5] fill-level and volume update, [6]
+ * labelling.  Read after fsl_sync. */
 fsl_status fsl_phase_ms(const fsl_domain* h, double* out);
 
 /* Counts of the cell types of domain d (array of 5), synchronises. */

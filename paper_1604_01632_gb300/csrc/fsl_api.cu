@@ -52,6 +52,7 @@ struct fsl_domain {
     int cur = 0;
     uint8_t *flag = nullptr, *mark = nullptr;
     double *m = nullptr, *phi = nullptr, *phit = nullptr, *rhoi = nullptr, *exs = nullptr;
+    float *phif = nullptr, *phitf = nullptr;   // FP32 copies (FP32-collide forms only)
     int* id = nullptr;
     long long *vfx = nullptr, *vxfx = nullptr, *vsfx = nullptr, *ncells = nullptr;
     int* constp = nullptr;
@@ -92,7 +93,7 @@ struct fsl_domain {
     double k1_ms = 0.0;
     std::vector<cudaEvent_t> phpool;   // direct mode: events between the kernels of a step
     size_t phused = 0;
-    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+    double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     std::vector<void*> allocs;
     std::string err;
 };
@@ -137,6 +138,8 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.m = h->m;
     A.phi = h->phi;
     A.phit = h->phit;
+    A.phif = h->phif;
+    A.phitf = h->phitf;
     A.rhoi = h->rhoi;
     A.exs = h->exs;
     A.id = h->id;
@@ -196,25 +199,25 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     return K;
 }
 
-void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
+void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st, cudaEvent_t el = nullptr, cudaEvent_t ei = nullptr) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
-    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
-    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
-    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join); break;
+    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
+    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
+    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
+    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
     }
 }
 
 void launch_cb(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_convert_b<double>(A, h->ifblocks, st); break;
-    case FSL_P_FP32: launch_convert_b<float>(A, h->ifblocks, st); break;
-    case FSL_P_F16S: launch_convert_b<__half>(A, h->ifblocks, st); break;
-    default: launch_convert_b<__nv_bfloat16>(A, h->ifblocks, st); break;
+    case FSL_P_FP64: launch_convert_ab<double>(A, h->ifblocks, st); break;
+    case FSL_P_FP32: launch_convert_ab<float>(A, h->ifblocks, st); break;
+    case FSL_P_F16S: launch_convert_ab<__half>(A, h->ifblocks, st); break;
+    default: launch_convert_ab<__nv_bfloat16>(A, h->ifblocks, st); break;
     }
 }
 
-// Stream-collide and the four conversion phases of one step (6 kernels).
+// Stream-collide and the three conversion kernels of one step (5 kernels).
 // With e0/e1 the stream-collide pair is bracketed by event records (captured
 // as event-record nodes when the stream is capturing; their nodes go to rec).
 cudaEvent_t next_phase_event(fsl_domain* h) {
@@ -243,17 +246,20 @@ int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e
         else cudaEventRecord(e, h->ls);
     };
     if (e0) { record(e0); last_node(0); }
-    launch_k1(h, A, h->ls);
+    if (phases) {
+        cudaEvent_t el = next_phase_event(h), ei = next_phase_event(h);
+        launch_k1(h, A, h->ls, el, ei);
+    } else {
+        launch_k1(h, A, h->ls);
+    }
     if (e1) { record(e1); last_node(1); }
-    launch_convert_a(A, h->ifblocks, h->ls);
-    if (phases) cudaEventRecord(next_phase_event(h), h->ls);
     launch_cb(h, A, h->ls);
     if (phases) cudaEventRecord(next_phase_event(h), h->ls);
     launch_convert_c(A, h->ifblocks, h->ls);
     if (phases) cudaEventRecord(next_phase_event(h), h->ls);
     launch_convert_d(A, h->ifblocks, h->ls);
     if (phases) cudaEventRecord(next_phase_event(h), h->ls);
-    return 6;
+    return 5;
 }
 
 std::pair<cudaEvent_t, cudaEvent_t> next_events(fsl_domain* h) {
@@ -415,6 +421,11 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         D.sigma2 = 2.0 * p.sigma;
         for (int k = 0; k < 3; ++k) { D.g[k] = p.gravity[k]; D.lid[k] = p.lid_velocity[k]; }
         D.eps = p.eps;
+        D.fomp = (float)D.omp;
+        D.fomm = (float)D.omm;
+        D.fsigma2 = (float)D.sigma2;
+        for (int k = 0; k < 3; ++k) { D.fg[k] = (float)D.g[k]; D.flid[k] = (float)D.lid[k]; }
+        D.feps = (float)D.eps;
         div_magic(p.nx, D.mgx, D.shx);
         div_magic(p.ny, D.mgy, D.shy);
         D.has_force = (p.gravity[0] != 0.0 || p.gravity[1] != 0.0 || p.gravity[2] != 0.0) ? 1 : 0;
@@ -469,6 +480,10 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->m, 8 * N);
     AL(h->phi, 8 * N);
     AL(h->phit, 8 * N);
+    if (precision != FSL_P_FP64) {
+        AL(h->phif, 4 * N);
+        AL(h->phitf, 4 * N);
+    }
     AL(h->rhoi, 8 * N);
     AL(h->exs, 8 * N);
     AL(h->id, 4 * N);
@@ -528,6 +543,8 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->m, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->phi, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->phit, 0, 8 * N);
+    if (e == cudaSuccess && h->phif) e = cudaMemset(h->phif, 0, 4 * N);
+    if (e == cudaSuccess && h->phitf) e = cudaMemset(h->phitf, 0, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->rhoi, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->exs, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->f[0], 0, 19 * N * h->fbytes);
@@ -688,19 +705,25 @@ fsl_status fsl_sync(fsl_domain* h) {
             tot += ms;
         }
         h->k1_ms = tot;
-        // direct mode: phase k of step n runs from event 5n+k-1 (the end of
-        // the stream-collide pair for k = 1) to event 5n+k
-        if (h->phused >= 5 && h->phused == 5 * (h->evused / 2)) {
-            for (int k = 0; k < 6; ++k) h->phase_ms[k] = 0.0;
+        // direct mode, six phase events per step: the ends of the liquid and
+        // interface kernels (timed from the start of the pair), then the ends
+        // of the three conversion kernels and of the labelling (each timed
+        // from the end of the one before, the first from the end of the pair)
+        if (h->phused >= 6 && h->phused == 6 * (h->evused / 2)) {
+            for (int k = 0; k < 7; ++k) h->phase_ms[k] = 0.0;
             for (size_t n = 0; n < h->evused / 2; ++n) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, h->evpool[2 * n], h->evpool[2 * n + 1]);
                 h->phase_ms[0] += ms;
-                cudaEvent_t prev = h->evpool[2 * n + 1];
-                for (int k = 0; k < 5; ++k) {
-                    cudaEventElapsedTime(&ms, prev, h->phpool[5 * n + k]);
+                for (int k = 0; k < 2; ++k) {
+                    cudaEventElapsedTime(&ms, h->evpool[2 * n], h->phpool[6 * n + k]);
                     h->phase_ms[1 + k] += ms;
-                    prev = h->phpool[5 * n + k];
+                }
+                cudaEvent_t prev = h->evpool[2 * n + 1];
+                for (int k = 2; k < 6; ++k) {
+                    cudaEventElapsedTime(&ms, prev, h->phpool[6 * n + k]);
+                    h->phase_ms[1 + k] += ms;
+                    prev = h->phpool[6 * n + k];
                 }
             }
         }
@@ -723,7 +746,7 @@ double fsl_stream_collide_ms(const fsl_domain* h) { return h ? h->k1_ms : 0.0; }
 
 fsl_status fsl_phase_ms(const fsl_domain* h, double* out) {
     if (!h || !out) return FSL_ERR_ARG;
-    for (int k = 0; k < 6; ++k) out[k] = h->phase_ms[k];
+    for (int k = 0; k < 7; ++k) out[k] = h->phase_ms[k];
     return FSL_OK;
 }
 

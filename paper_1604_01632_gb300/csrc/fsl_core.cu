@@ -46,47 +46,6 @@ __device__ inline void warp_add(long long* base, int key, long long v) {
 // All four phases work on compact lists (marked cells, new interface cells,
 // interface cells), so their cost follows the interface, not the lattice.
 
-// C1 (phase A), one thread per (marked cell, direction): a filled cell turns
-// the gas neighbour in that direction into interface (the neighbour's first
-// filled neighbour in direction order claims it, so it is listed once) and
-// cancels an emptied mark there.
-__global__ void __launch_bounds__(128) k_convert_a(StepArgs A) {
-    pdl_trigger();
-    if (blockIdx.x == 0) {
-        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
-        if (threadIdx.x == 0) *A.icount_next = 0;
-    }
-    const int nm = *A.mcount;
-    const int total = 18 * nm;
-    const int stride = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
-        const int t = base + threadIdx.x;
-        bool claim = false;
-        long long z = 0;
-        if (t < total) {
-            const long long p = A.mlist[t / 18];
-            const int a = 1 + t % 18;
-            if (A.mark[p] == MK_FILLED) {
-                const int d = block_dom(A, p);
-                const Dom D = get_dom(A, d);
-                const Cell c = make_cell(D, p);
-                z = c.at(cx(a), cy(a), cz(a));
-                const uint8_t tz = ctype(A.flag[z]);
-                if (tz == GAS) {
-                    if (first_marked(A, D, z, MK_FILLED) == p) {
-                        claim = true;
-                        A.mark[z] = MK_NEWG;
-                        atomicAdd((unsigned long long*)&A.nif[d], 1ull);
-                    }
-                } else if (tz == IFC && A.mark[z] == MK_EMPTIED) {
-                    A.mark[z] = MK_NONE;
-                }
-            }
-        }
-        list_append(A.glist, A.gcount, claim, (int)z);
-    }
-}
-
 // Local test that removing the filled cell at the centre of the cube cannot
 // split its bubble: the gas/interface cells among its 18 neighbours must stay
 // connected inside the cube (18-connectivity) without the centre.
@@ -217,6 +176,7 @@ __global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
                 A.phi[g] = 1.0;
                 A.phit[g] = 1.0;
+                if (A.phif) { A.phif[g] = 1.f; A.phitf[g] = 1.f; }
                 A.id[g] = -1;
                 A.mark[g] = MK_NONE;
             } else if (t == IFC && mk == MK_CEMPTIED) {
@@ -224,6 +184,7 @@ __global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
                 A.phi[g] = 0.0;
                 A.phit[g] = 0.0;
+                if (A.phif) { A.phif[g] = 0.f; A.phitf[g] = 0.f; }
                 A.m[g] = 0.0;
                 A.mark[g] = MK_NONE;
             } else {
@@ -245,7 +206,9 @@ __global__ void __launch_bounds__(128) k_convert_d(StepArgs A) {
                 const long long told = volume_term(t, ph0);
                 A.m[g] = s;
                 A.phi[g] = phn;
-                A.phit[g] = phn < 0.0 ? 0.0 : (phn > 1.0 ? 1.0 : phn);
+                const double pht = phn < 0.0 ? 0.0 : (phn > 1.0 ? 1.0 : phn);
+                A.phit[g] = pht;
+                if (A.phif) { A.phif[g] = (float)phn; A.phitf[g] = (float)pht; }
                 if (t != IFC) A.flag[g] = (uint8_t)((f & ~K_TYPE) | IFC);
                 dv = volume_term(IFC, phn) - told;
                 if (t == LIQ) { ckey = key; dc = 1; }
@@ -510,7 +473,6 @@ __global__ void k_export_cells(const uint8_t* flag, const double* phi, const dou
 
 // ------------------------------------------------------------ host launches
 
-void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s) { k_convert_a<<<(unsigned)nb, 128, 0, s>>>(A); }
 void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s) { launch_pdl(k_convert_c, (unsigned)nb, 128u, s, A); }
 void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s) { launch_pdl(k_convert_d, (unsigned)nb, 128u, s, A); }
 void launch_build_ilist(const StepArgs& A, long long nb, cudaStream_t s) { k_build_ilist<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }

@@ -57,7 +57,27 @@ struct Dom {
     int shx, shy;               // (shift -1: the divisor is 1)
     int has_force;              // gravity is not zero
     int lonely_rule;            // interface cells without gas / liquid neighbours fill / empty
+    // the same parameters rounded to FP32 once on the host: the FP32-collide
+    // kernels read these, so that no thread converts from FP64 (the FP64 pipe
+    // is a small fraction of the FP32 rate on this GPU)
+    float fomp, fomm, fsigma2, fg[3], flid[3], feps;
 };
+
+// Relaxation rates, 2 sigma, gravity and lid velocity in the arithmetic type C.
+template <typename C> struct Par {
+    C omp, omm, sigma2, g[3], lid[3];
+};
+template <typename C> __device__ inline Par<C> par_of(const Dom& D) {
+    Par<C> P;
+    if constexpr (sizeof(C) == 8) {
+        P.omp = D.omp; P.omm = D.omm; P.sigma2 = D.sigma2;
+        for (int k = 0; k < 3; ++k) { P.g[k] = D.g[k]; P.lid[k] = D.lid[k]; }
+    } else {
+        P.omp = D.fomp; P.omm = D.fomm; P.sigma2 = D.fsigma2;
+        for (int k = 0; k < 3; ++k) { P.g[k] = D.fg[k]; P.lid[k] = D.flid[k]; }
+    }
+    return P;
+}
 
 // Invariant-divisor division for 0 <= n < 2^31: with s = ceil(log2 d) and
 // m = ceil(2^(31+s) / d) < 2^32, n / d = (n * m) >> (31 + s) (Granlund and
@@ -92,6 +112,8 @@ struct StepArgs {
     double* phi;                // fill level
     double* phit;               // fill level as the normal stencil reads it: walls and
                                 // liquid 1, gas 0, interface clamp(phi, 0, 1)
+    float* phif;                // FP32 copies of phi and phit for the FP32-collide
+    float* phitf;               // forms (null for the FP64 form)
     double* rhoi;               // density of interface cells at their last collision
     double* exs;                // excess-mass share of converted cells
     int* id;                    // bubble slot of gas/interface cells, -1 elsewhere
@@ -150,6 +172,11 @@ __device__ inline int rcz(int a) { return (int)((0x20a0954955ULL >> (2 * a)) & 3
 __host__ __device__ inline int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 __host__ __device__ inline double weight(int a) {
     return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+// the same weights in the arithmetic type C (for C = float the FP32 roundings
+// of the FP64 constants, folded at compile time)
+template <typename C> __host__ __device__ inline C weightc(int a) {
+    return a == 0 ? (C)(1.0 / 3.0) : (a <= 6 ? (C)(1.0 / 18.0) : (C)(1.0 / 36.0));
 }
 
 __device__ inline void set_status(int* st, int code) { atomicCAS(st, 0, code); }
@@ -242,8 +269,8 @@ template <> struct Form<__half> {
     static constexpr bool shifted = true;
     __device__ static inline float ld_dev(const __half* p) { return __half2float(*p); }
     __device__ static inline void st_dev(__half* p, float v) { *p = __float2half_rn(v); }
-    __device__ static inline float ld(const __half* p, int a) { return (float)weight(a) + __half2float(*p); }
-    __device__ static inline void st(__half* p, int a, float v) { *p = __float2half_rn(v - (float)weight(a)); }
+    __device__ static inline float ld(const __half* p, int a) { return weightc<float>(a) + __half2float(*p); }
+    __device__ static inline void st(__half* p, int a, float v) { *p = __float2half_rn(v - weightc<float>(a)); }
 };
 template <> struct Form<__nv_bfloat16> {
     using C = float;
@@ -251,10 +278,10 @@ template <> struct Form<__nv_bfloat16> {
     __device__ static inline float ld_dev(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static inline void st_dev(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static inline float ld(const __nv_bfloat16* p, int a) {
-        return (float)weight(a) + __bfloat162float(*p);
+        return weightc<float>(a) + __bfloat162float(*p);
     }
     __device__ static inline void st(__nv_bfloat16* p, int a, float v) {
-        *p = __float2bfloat16_rn(v - (float)weight(a));
+        *p = __float2bfloat16_rn(v - weightc<float>(a));
     }
 };
 
@@ -283,11 +310,11 @@ __device__ inline void moments(const C* f, C& rho, C& jx, C& jy, C& jz) {
 template <typename C>
 __device__ inline void feq_all(C rho, C ux, C uy, C uz, C* out) {
     C usq = ux * ux + uy * uy + uz * uz;
-    out[0] = ((C)weight(0) * rho) * ((C)1 - (C)1.5 * usq);
+    out[0] = (weightc<C>(0) * rho) * ((C)1 - (C)1.5 * usq);
 #pragma unroll
     for (int a = 1; a < 19; a += 2) {
         C cu = cdot<C>(a, ux, uy, uz);
-        C wr = (C)weight(a) * rho;
+        C wr = weightc<C>(a) * rho;
         C fp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * usq);
         C fm = wr * ((C)3 * cu);
         out[a] = fp + fm;
@@ -318,18 +345,18 @@ __device__ inline C collide(const C* fin, C* fout, C omp, C omm, C gx, C gy, C g
     }
     const C usq = ux * ux + uy * uy + uz * uz;
     const C cp = (C)1 - (C)0.5 * omp, cm = (C)1 - (C)0.5 * omm;
-    const C feq0 = ((C)weight(0) * rho) * ((C)1 - (C)1.5 * usq);
+    const C feq0 = (weightc<C>(0) * rho) * ((C)1 - (C)1.5 * usq);
     fout[0] = fin[0] - omp * (fin[0] - feq0);
     C uF = (C)0;
     if constexpr (FORCE) {
         uF = ux * Fx + uy * Fy + uz * Fz;
-        const C S0 = (C)weight(0) * ((C)-3 * uF);
+        const C S0 = weightc<C>(0) * ((C)-3 * uF);
         fout[0] = fout[0] + cp * S0;
     }
 #pragma unroll
     for (int a = 1; a < 19; a += 2) {
         const int b = a + 1;
-        const C w = (C)weight(a);
+        const C w = weightc<C>(a);
         const C cu = cdot<C>(a, ux, uy, uz);
         const C wr = w * rho;
         const C feqp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * usq);
@@ -373,7 +400,7 @@ __device__ inline void collide_dev(const float* d, float* dout, float omp, float
     const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
     const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float cp = 1.f - 0.5f * omp, cm = 1.f - 0.5f * omm;
-    const float w0 = (float)weight(0);
+    const float w0 = weightc<float>(0);
     dout[0] = d[0] - omp * (d[0] - w0 * (drho - rho * usq15));
     float uF = 0.f;
     if constexpr (FORCE) {
@@ -383,7 +410,7 @@ __device__ inline void collide_dev(const float* d, float* dout, float omp, float
 #pragma unroll
     for (int a = 1; a < 19; a += 2) {
         const int b = a + 1;
-        const float w = (float)weight(a);
+        const float w = weightc<float>(a);
         const float cu = cdot<float>(a, ux, uy, uz);
         const float eqp = w * (drho + rho * (4.5f * cu * cu - usq15));
         const float eqm = w * rho * 3.f * cu;
@@ -416,6 +443,19 @@ __device__ inline double bubble_pressure(long long vfx, long long vxfx, long lon
     if (V <= 1e-3) return p0;
     double Vs = (double)vsfx * 2.3283064365386962890625e-10;
     return (Vs / V) * p0;
+}
+
+// The same pressure in FP32 from the fixed-point volumes, for the FP32-collide
+// forms: v 2^-32 = hi + lo 2^-32 with 32-bit halves (no FP64 arithmetic).
+__device__ inline float fx_to_float(long long v) {
+    return (float)(int)(v >> 32) + (float)(unsigned)(v & 0xffffffffLL) * 2.3283064365386962890625e-10f;
+}
+__device__ inline float bubble_pressure_f(long long vfx, long long vxfx, long long vsfx, int constp) {
+    const float p0 = (float)(1.0 / 3.0);
+    if (constp) return p0;
+    const float V = fx_to_float(vfx + vxfx);
+    if (V <= 1e-3f) return p0;
+    return (fx_to_float(vsfx) / V) * p0;
 }
 
 __device__ inline long long volume_term(uint8_t t, double phi) {
@@ -475,6 +515,7 @@ __global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
     const uint8_t f = A.flag[g];
     if (ctype(f) != LIQ) return;
     const Dom D = get_dom(A, block_dom(A, g));
+    const Par<C> R = par_of<C>(D);
     const Pull P = make_pull(D, g);
     const unsigned gi = (unsigned)g;
     const long long S = A.stride;
@@ -497,8 +538,8 @@ __global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
                 if (ty == OBS) {
                     d[a] = Form<T>::ld_dev(src + ab * S + gi);   // w_a = w_abar
                 } else if (ty == LID) {
-                    const float cuw = cdot<float>(a, (float)D.lid[0], (float)D.lid[1], (float)D.lid[2]);
-                    d[a] = Form<T>::ld_dev(src + ab * S + gi) + (6.f * (float)weight(a)) * cuw;
+                    const float cuw = cdot<float>(a, R.lid[0], R.lid[1], R.lid[2]);
+                    d[a] = Form<T>::ld_dev(src + ab * S + gi) + (6.f * weightc<float>(a)) * cuw;
                 } else {
                     d[a] = Form<T>::ld_dev(src + a * S + y);
                 }
@@ -506,9 +547,9 @@ __global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
         }
         float dout[19];
         if (D.has_force)
-            collide_dev<true>(d, dout, (float)D.omp, (float)D.omm, (float)D.g[0], (float)D.g[1], (float)D.g[2]);
+            collide_dev<true>(d, dout, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
         else
-            collide_dev<false>(d, dout, (float)D.omp, (float)D.omm, 0.f, 0.f, 0.f);
+            collide_dev<false>(d, dout, R.omp, R.omm, 0.f, 0.f, 0.f);
         if (!(dout[0] == dout[0])) set_status(A.status, ST_NAN);
 #pragma unroll
         for (int a = 0; a < 19; ++a) Form<T>::st_dev(dst + a * S + gi, dout[a]);
@@ -528,15 +569,15 @@ __global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
                 if (ty == OBS) {
                     fin[a] = Form<T>::ld(src + ab * S + gi, ab);
                 } else if (ty == LID) {
-                    C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
-                    fin[a] = Form<T>::ld(src + ab * S + gi, ab) + ((C)6 * (C)weight(a)) * cuw;
+                    C cuw = cdot<C>(a, R.lid[0], R.lid[1], R.lid[2]);
+                    fin[a] = Form<T>::ld(src + ab * S + gi, ab) + ((C)6 * weightc<C>(a)) * cuw;
                 } else {
                     fin[a] = Form<T>::ld(src + a * S + y, a);
                 }
             }
         }
         C fout[19];
-        C rho = collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+        C rho = collide_any<C>(D.has_force, fin, fout, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
         if (!(rho == rho)) set_status(A.status, ST_NAN);
 #pragma unroll
         for (int a = 0; a < 19; ++a) Form<T>::st(dst + a * S + gi, a, fout[a]);
@@ -575,33 +616,45 @@ __device__ inline Stencil make_stencil(const Dom& D, long long g) {
 
 
 // K1I: interface cells, from the list of interface cells built at the end of
-// the previous step.  A block takes 32 cells per pass.  Load phase, eight
-// threads per cell into shared memory: thread j (0-6) reads the 27 stencil fill
-// levels around point j (the cell, then its +x, -x, +y, -y, +z, -z
-// neighbours) and forms the Parker-Youngs gradient there (a unit normal for
-// j > 0); thread 7 reads the cell's mass and bubble pressure; all eight read
-// the PDFs, neighbour types and mass-exchange terms of directions j, j+8,
-// j+16.  Compute phase, one thread per cell (the first warp), in the oracle's
-// order: stream with bounce-back, mass exchange over the 18 links (Eq. 10),
-// reconstruction of the PDFs coming from the gas side with the gas density
-// 3 (p_V + 2 sigma kappa) of the cell's bubble (Eqs. 8, 11-15, kappa = 1/2 div
-// n_hat), collision, then the filled / emptied marks.
+// the previous step.  A block of 128 threads takes FSL_IFC cells per pass.
+// Load phase, four threads per cell: the 5x5x5 box of fill levels around the
+// cell (rows along x), and for the directions q, q+4, ... the cell's PDFs, the
+// PDF streaming in, the neighbour types and the mass-exchange terms.
+// Gradient phase, four threads per cell: Parker-Youngs gradients at the cell
+// and at its six face neighbours (unit normals there).  Compute phase, one
+// thread per cell, in the oracle's order: stream with bounce-back (Eq. 7),
+// mass exchange over the 18 links (Eq. 10), reconstruction of the PDFs coming
+// from the gas side with the gas density 3 (p_V + 2 sigma kappa) of the
+// cell's bubble (Eqs. 8, 11-15, kappa = 1/2 div n_hat by central differences
+// of the face normals), collision (Eq. 6), then the filled / emptied marks.
+// The FP32-collide forms do all of this in FP32 except the cell mass, which
+// accumulates in FP64.
+#define FSL_IF_THREADS 128
+template <typename T> struct IfCells {
+    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : 32;
+};
 template <typename T>
 struct IfStage {
     using C = typename Form<T>::C;
-    C fs[32][19];      // own post-collision PDFs
-    C fy[32][19];      // PDF streaming in from the source cell
-    double ex[32][19]; // mass-exchange term of each link (Eq. 10)
-    C nrm[32][7][3];   // gradient at the cell, unit normals at the face neighbours
-    double m[32];      // mass
-    double pv[32];     // bubble pressure (Eq. 13)
-    uint8_t ty[32][19];
-    uint8_t tz[32][19];
+    static constexpr int N = IfCells<T>::n;
+    C ph[N][125];      // fill levels, 5x5x5 box around the cell
+    C fs[N][19];       // own post-collision PDFs of the previous step
+    C fy[N][19];       // PDF streaming in from the source cell
+    C ex[N][19];       // mass-exchange term of each link (Eq. 10)
+    C nrm[N][7][3];    // gradient at the cell, unit normals at the face neighbours
+    C pv[N];           // bubble pressure (Eq. 13)
+    double m[N];       // mass
+    uint8_t ty[N][19];
+    uint8_t tz[N][19];
 };
 
+__device__ inline int ph_index(int dx, int dy, int dz) { return (dx + 2) + 5 * (dy + 2) + 25 * (dz + 2); }
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
+__global__ void __launch_bounds__(FSL_IF_THREADS) k_stream_interface(StepArgs A) {
     using C = typename Form<T>::C;
+    constexpr int N = IfCells<T>::n;
+    constexpr int TPC = FSL_IF_THREADS / N;   // threads per cell in the load and gradient phases
     __shared__ IfStage<T> sh;
     if (blockIdx.x == 0) {
         // per-step counters; the previous step's kernels are done with them
@@ -621,51 +674,43 @@ __global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
     const long long S = A.stride;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
-    const int c = threadIdx.x >> 3;      // cell of this thread in the load phase
-    const int j = threadIdx.x & 7;
-    for (int i0 = blockIdx.x * 32; i0 < cnt; i0 += gridDim.x * 32) {
+    // fill levels in the arithmetic type (FP32 copies for the FP32-collide forms)
+    const C* __restrict__ phic;
+    const C* __restrict__ phtc;
+    if constexpr (sizeof(C) == 8) { phic = A.phi; phtc = A.phit; }
+    else { phic = A.phif; phtc = A.phitf; }
+    const int c = threadIdx.x / TPC;      // cell of this thread in the load and gradient phases
+    const int q = threadIdx.x % TPC;
+    for (int i0 = blockIdx.x * N; i0 < cnt; i0 += gridDim.x * N) {
         // ---------------- load phase
         if (i0 + c < cnt) {
             const long long g = A.ilist[i0 + c];
             const Dom D = get_dom(A, block_dom(A, g));
             const Stencil st = make_stencil(D, g);
-            if (j < 7) {
-                const int ox = j == 1 ? 1 : (j == 2 ? -1 : 0);
-                const int oy = j == 3 ? 1 : (j == 4 ? -1 : 0);
-                const int oz = j == 5 ? 1 : (j == 6 ? -1 : 0);
-                C ph[27];
+            // rows (dy, dz) of the box, five cells along x each
+            for (int r = q; r < 25; r += TPC) {
+                const int dy = r % 5 - 2, dz = r / 5 - 2;
+                C* row = &sh.ph[c][5 * r];
+                if (st.x >= 2 && st.x < st.nx - 2) {
+                    const long long b = st.at(0, dy, dz);
 #pragma unroll
-                for (int k = 0; k < 27; ++k) ph[k] = (C)A.phit[st.at(ox + k % 3 - 1, oy + (k / 3) % 3 - 1, oz + k / 9 - 1)];
-                C gx = (C)0, gy = (C)0, gz = (C)0;
+                    for (int k = 0; k < 5; ++k) row[k] = phtc[b + (k - 2)];
+                } else {
 #pragma unroll
-                for (int b = -1; b <= 1; ++b) {
-#pragma unroll
-                    for (int a = -1; a <= 1; ++a) {
-                        const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
-                        gx = gx + W * (ph[2 + 3 * (a + 1) + 9 * (b + 1)] - ph[0 + 3 * (a + 1) + 9 * (b + 1)]);
-                        gy = gy + W * (ph[(a + 1) + 3 * 2 + 9 * (b + 1)] - ph[(a + 1) + 3 * 0 + 9 * (b + 1)]);
-                        gz = gz + W * (ph[(a + 1) + 3 * (b + 1) + 9 * 2] - ph[(a + 1) + 3 * (b + 1) + 9 * 0]);
-                    }
+                    for (int k = 0; k < 5; ++k) row[k] = phtc[st.at(k - 2, dy, dz)];
                 }
-                if (j > 0) {
-                    const C q = gx * gx + gy * gy + gz * gz;
-                    if (q > (C)0) {
-                        const C len = sqrt(q);
-                        gx = -(gx / len); gy = -(gy / len); gz = -(gz / len);
-                    } else {
-                        gx = (C)0; gy = (C)0; gz = (C)0;
-                    }
-                }
-                sh.nrm[c][j][0] = gx;
-                sh.nrm[c][j][1] = gy;
-                sh.nrm[c][j][2] = gz;
-            } else {
+            }
+            if (q == TPC - 1) {
                 sh.m[c] = A.m[g];
                 const int bub = A.id[g];
-                sh.pv[c] = bub >= 0 ? bubble_pressure(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : 1.0 / 3.0;
+                if constexpr (sizeof(C) == 8)
+                    sh.pv[c] = bub >= 0 ? bubble_pressure(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : 1.0 / 3.0;
+                else
+                    sh.pv[c] = bub >= 0 ? bubble_pressure_f(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub])
+                                        : (float)(1.0 / 3.0);
             }
-            const double phx = A.phi[g];
-            for (int a = j; a < 19; a += 8) {
+            const C phx = phic[g];
+            for (int a = q; a < 19; a += TPC) {
                 const C fsa = Form<T>::ld(src + (long long)a * S + g, a);
                 sh.fs[c][a] = fsa;
                 if (a == 0) continue;
@@ -678,21 +723,55 @@ __global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
                 const uint8_t tz = ctype(A.flag[z]);
                 sh.tz[c][a] = tz;
                 if (tz == LIQ || tz == IFC) {
-                    const double fz = (double)Form<T>::ld(src + (long long)ab * S + z, ab);
-                    const double e = fz - (double)fsa;
-                    sh.ex[c][a] = tz == IFC ? (0.5 * (phx + A.phi[z])) * e : e;
+                    const C e = Form<T>::ld(src + (long long)ab * S + z, ab) - fsa;
+                    sh.ex[c][a] = tz == IFC ? ((C)0.5 * (phx + phic[z])) * e : e;
                 }
             }
         }
         __syncthreads();
-        // ---------------- compute phase (first warp, one thread per cell)
+        // ---------------- gradient phase: point j (the cell, then its +x, -x,
+        // +y, -y, +z, -z neighbours) for j = q, q + TPC, ...
+        if (i0 + c < cnt) {
+            for (int j = q; j < 7; j += TPC) {
+                const int ox = j == 1 ? 1 : (j == 2 ? -1 : 0);
+                const int oy = j == 3 ? 1 : (j == 4 ? -1 : 0);
+                const int oz = j == 5 ? 1 : (j == 6 ? -1 : 0);
+                const C* P = &sh.ph[c][ph_index(ox, oy, oz)];   // P[dx + 5 dy + 25 dz]
+                C gx = (C)0, gy = (C)0, gz = (C)0;
+#pragma unroll
+                for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+                    for (int a = -1; a <= 1; ++a) {
+                        const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
+                        gx = gx + W * (P[1 + 5 * a + 25 * b] - P[-1 + 5 * a + 25 * b]);
+                        gy = gy + W * (P[a + 5 + 25 * b] - P[a - 5 + 25 * b]);
+                        gz = gz + W * (P[a + 5 * b + 25] - P[a + 5 * b - 25]);
+                    }
+                }
+                if (j > 0) {
+                    const C qq = gx * gx + gy * gy + gz * gz;
+                    if (qq > (C)0) {
+                        const C len = sqrt(qq);
+                        gx = -(gx / len); gy = -(gy / len); gz = -(gz / len);
+                    } else {
+                        gx = (C)0; gy = (C)0; gz = (C)0;
+                    }
+                }
+                sh.nrm[c][j][0] = gx;
+                sh.nrm[c][j][1] = gy;
+                sh.nrm[c][j][2] = gz;
+            }
+        }
+        __syncthreads();
+        // ---------------- compute phase, one thread per cell
         if (threadIdx.x < 32) {
             const int cc = threadIdx.x;
             uint8_t mk = MK_NONE;
             long long g = 0;
-            if (i0 + cc < cnt) {
+            if (cc < N && i0 + cc < cnt) {
                 g = A.ilist[i0 + cc];
                 const Dom D = get_dom(A, block_dom(A, g));
+                const Par<C> R = par_of<C>(D);
                 C fs[19];
 #pragma unroll
                 for (int a = 0; a < 19; ++a) fs[a] = sh.fs[cc][a];
@@ -704,7 +783,7 @@ __global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
                 const C dZ = sh.nrm[cc][5][2] - sh.nrm[cc][6][2];
                 const C kappa = (C)0.25 * ((dX + dY) + dZ);
                 const C gx = sh.nrm[cc][0][0], gy = sh.nrm[cc][0][1], gz = sh.nrm[cc][0][2];
-                const C pg = (C)sh.pv[cc] + (C)D.sigma2 * kappa;
+                const C pg = sh.pv[cc] + R.sigma2 * kappa;
                 const C rg = (C)3 * pg;
                 C fg[19];
                 feq_all<C>(rg, ugx, ugy, ugz, fg);
@@ -717,8 +796,8 @@ __global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
                     if (ty == OBS) {
                         fin[a] = fs[ab];
                     } else if (ty == LID) {
-                        const C cuw = cdot<C>(a, (C)D.lid[0], (C)D.lid[1], (C)D.lid[2]);
-                        fin[a] = fs[ab] + ((C)6 * (C)weight(a)) * cuw;
+                        const C cuw = cdot<C>(a, R.lid[0], R.lid[1], R.lid[2]);
+                        fin[a] = fs[ab] + ((C)6 * weightc<C>(a)) * cuw;
                     } else if (ty == GAS) {
                         fin[a] = (fg[a] + fg[ab]) - fs[ab];
                     } else {
@@ -726,33 +805,38 @@ __global__ void __launch_bounds__(256) k_stream_interface(StepArgs A) {
                         if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
                     }
                 }
-                // mass exchange, summed in direction order (Eq. 10)
-                double dm = 0.0;
+                // mass exchange, summed in direction order (Eq. 10); the cell
+                // mass itself accumulates in FP64 for every form
+                C dm = (C)0;
+                bool has_gas = false, has_liq = false;
 #pragma unroll
                 for (int a = 1; a < 19; ++a) {
                     const uint8_t tz = sh.tz[cc][a];
                     if (tz == LIQ || tz == IFC) dm = dm + sh.ex[cc][a];
+                    has_gas |= tz == GAS;
+                    has_liq |= tz == LIQ;
                 }
-                const double mnew = sh.m[cc] + dm;
+                const double mnew = sh.m[cc] + (double)dm;
                 C fout[19];
-                const C rho =
-                    collide_any<C>(D.has_force, fin, fout, (C)D.omp, (C)D.omm, (C)D.g[0], (C)D.g[1], (C)D.g[2]);
+                const C rho = collide_any<C>(D.has_force, fin, fout, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
                 if (!(rho == rho)) set_status(A.status, ST_NAN);
 #pragma unroll
                 for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
-                const double r = (double)rho;
                 A.m[g] = mnew;
-                A.rhoi[g] = r;
-                if (mnew > (1.0 + D.eps) * r) mk = MK_FILLED;
-                else if (mnew < (-D.eps) * r) mk = MK_EMPTIED;
+                A.rhoi[g] = (double)rho;
+                bool filled, emptied;
+                if constexpr (sizeof(C) == 8) {
+                    filled = mnew > (1.0 + D.eps) * rho;
+                    emptied = mnew < (-D.eps) * rho;
+                } else {
+                    const float mf = (float)mnew;
+                    filled = mf > (1.f + D.feps) * rho;
+                    emptied = mf < (-D.feps) * rho;
+                }
+                if (filled) mk = MK_FILLED;
+                else if (emptied) mk = MK_EMPTIED;
                 else if (D.lonely_rule) {
                     // a cell that no longer separates liquid from gas
-                    bool has_gas = false, has_liq = false;
-#pragma unroll
-                    for (int a = 1; a < 19; ++a) {
-                        has_gas |= sh.tz[cc][a] == GAS;
-                        has_liq |= sh.tz[cc][a] == LIQ;
-                    }
                     if (!has_gas) mk = MK_FILLED;
                     else if (!has_liq) mk = MK_EMPTIED;
                 }
@@ -775,107 +859,116 @@ __device__ inline long long first_marked(const StepArgs& A, const Dom& D, long l
     return -1;
 }
 
-// C2 (conversion phase B).  First part, one thread per (marked cell,
-// direction): an emptied cell that kept its mark turns the liquid neighbour in
-// that direction into interface when it is that neighbour's first emptied
-// neighbour in direction order (so each new cell is claimed once, by the
-// bubble of its first emptied neighbour; m = rho of its own PDFs).  Second
-// part, one warp per new interface cell from gas: lanes 1-18 take the density
-// and velocity of the liquid or non-emptied interface neighbour in their
-// direction, lane 0 sums them in direction order and sets f = f_eq of the
-// means, m = 0.
+// An interface cell carrying an emptied mark that phase A does not cancel (no
+// filled neighbour).  Written as a test on the marks K1I set, so it holds
+// whether or not another thread has already cleared the cancelled mark.
+__device__ inline bool still_emptied(const StepArgs& A, const Dom& D, long long w) {
+    if (ctype(A.flag[w]) != IFC || A.mark[w] != MK_EMPTIED) return false;
+    const Cell c = make_cell(D, w);
+    for (int a = 1; a < 19; ++a) {
+        const long long v = c.at(cx(a), cy(a), cz(a));
+        if (ctype(A.flag[v]) == IFC && A.mark[v] == MK_FILLED) return false;
+    }
+    return true;
+}
+
+// Conversion phases A and B (Sec. 2.2, cell conversion), one thread per
+// (marked cell, direction).  A filled cell turns the gas neighbour in that
+// direction into interface when it is that neighbour's first filled neighbour
+// in direction order (so each new cell is claimed once) and initialises it
+// with f = f_eq of the mean density and velocity of its liquid and
+// non-emptied interface neighbours, m = 0; it also cancels an emptied mark
+// there.  An emptied cell with no filled neighbour turns the liquid neighbour
+// in that direction into interface when it is that neighbour's first such
+// emptied neighbour: the new cell keeps its PDFs, takes m = rho and joins the
+// emptied cell's bubble.
 template <typename T>
-__global__ void __launch_bounds__(128) k_convert_b(StepArgs A) {
+__global__ void __launch_bounds__(128) k_convert_ab(StepArgs A) {
     using C = typename Form<T>::C;
-    pdl_wait();
+    if (blockIdx.x == 0) {
+        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
+        if (threadIdx.x == 0) *A.icount_next = 0;
+    }
     pdl_trigger();
-    const unsigned full = 0xffffffffu;
-    const int nm = *A.mcount, ng = *A.gcount;
-    const int p1 = (18 * nm + 31) & ~31;          // first part, padded to whole warps
-    const int total = p1 + 32 * ng;
+    const int nm = *A.mcount;
+    const int total = 18 * nm;
     const long long S = A.stride;
     T* f = (T*)A.fdst;
     const int stride = gridDim.x * blockDim.x;
     for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
         const int t = base + threadIdx.x;
-        if (base + (int)(threadIdx.x & ~31) < p1) {
-            // claims of liquid neighbours by emptied cells
-            const bool valid = t < 18 * nm;
-            bool claim = false;
-            long long z = 0;
-            if (valid) {
-                const long long p = A.mlist[t / 18];
-                const int a = 1 + t % 18;
-                if (A.mark[p] == MK_EMPTIED) {
-                    const int d = block_dom(A, p);
-                    const Dom D = get_dom(A, d);
-                    const Cell c = make_cell(D, p);
-                    z = c.at(cx(a), cy(a), cz(a));
-                    if (ctype(A.flag[z]) == LIQ && first_marked(A, D, z, MK_EMPTIED) == p) {
-                        claim = true;
-                        double r = (double)Form<T>::ld(f + z, 0);
-                        for (int q = 1; q < 19; ++q) r = r + (double)Form<T>::ld(f + (long long)q * S + z, q);
-                        A.mark[z] = MK_NEWL;
-                        A.id[z] = A.id[p];
-                        A.m[z] = r;
-                        A.rhoi[z] = r;
+        bool gclaim = false, lclaim = false;
+        long long z = 0;
+        if (t < total) {
+            const long long p = A.mlist[t / 18];
+            const int a = 1 + t % 18;
+            const int d = block_dom(A, p);
+            const Dom D = get_dom(A, d);
+            const uint8_t mp = A.mark[p];
+            const Cell c = make_cell(D, p);
+            z = c.at(rcx(a), rcy(a), rcz(a));
+            const uint8_t tz = ctype(A.flag[z]);
+            if (mp == MK_FILLED) {
+                if (tz == GAS) {
+                    if (first_marked(A, D, z, MK_FILLED) == p) {
+                        gclaim = true;
+                        // f = f_eq of the mean density and velocity of the liquid
+                        // and non-emptied interface neighbours, in direction order
+                        const Cell cz_ = make_cell(D, z);
+                        C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
+                        int cnt = 0;
+                        for (int q = 1; q < 19; ++q) {
+                            const long long w = cz_.at(cx(q), cy(q), cz(q));
+                            const uint8_t tw = ctype(A.flag[w]);
+                            if (tw == LIQ || (tw == IFC && !still_emptied(A, D, w))) {
+                                C fo[19];
+#pragma unroll
+                                for (int r = 0; r < 19; ++r) fo[r] = Form<T>::ld(f + (long long)r * S + w, r);
+                                C rr, jx, jy, jz;
+                                moments<C>(fo, rr, jx, jy, jz);
+                                sr = sr + rr;
+                                sux = sux + jx / rr;
+                                suy = suy + jy / rr;
+                                suz = suz + jz / rr;
+                                ++cnt;
+                            }
+                        }
+                        const C rbar = sr / (C)cnt;
+                        const C vx = sux / (C)cnt, vy = suy / (C)cnt, vz = suz / (C)cnt;
+                        C fe[19];
+                        feq_all<C>(rbar, vx, vy, vz, fe);
+#pragma unroll
+                        for (int r = 0; r < 19; ++r) Form<T>::st(f + (long long)r * S + z, r, fe[r]);
+                        A.m[z] = 0.0;
+                        A.rhoi[z] = (double)rbar;
+                        A.mark[z] = MK_NEWG;
                         atomicAdd((unsigned long long*)&A.nif[d], 1ull);
                     }
+                } else if (tz == IFC && A.mark[z] == MK_EMPTIED) {
+                    A.mark[z] = MK_NONE;
+                }
+            } else if (mp == MK_EMPTIED && tz == LIQ && still_emptied(A, D, p)) {
+                // is p the first emptied-and-not-cancelled neighbour of z?
+                const Cell cz_ = make_cell(D, z);
+                long long first = -1;
+                for (int q = 1; q < 19 && first < 0; ++q) {
+                    const long long w = cz_.at(cx(q), cy(q), cz(q));
+                    if (still_emptied(A, D, w)) first = w;
+                }
+                if (first == p) {
+                    lclaim = true;
+                    double r = (double)Form<T>::ld(f + z, 0);
+                    for (int q = 1; q < 19; ++q) r = r + (double)Form<T>::ld(f + (long long)q * S + z, q);
+                    A.mark[z] = MK_NEWL;
+                    A.id[z] = A.id[p];
+                    A.m[z] = r;
+                    A.rhoi[z] = r;
+                    atomicAdd((unsigned long long*)&A.nif[d], 1ull);
                 }
             }
-            list_append(A.llist, A.lcount, claim, (int)z);
-            continue;
         }
-        // new interface cell from gas, one warp per cell
-        const int w = (t - p1) >> 5;
-        const int lane = threadIdx.x & 31;
-        if (w >= ng) continue;
-        const long long p = A.glist[w];
-        const Dom D = get_dom(A, block_dom(A, p));
-        C r = (C)1, ux = (C)0, uy = (C)0, uz = (C)0;
-        int use = 0;
-        if (lane >= 1 && lane <= 18) {
-            const Cell c = make_cell(D, p);
-            const int a = lane;
-            const long long z = c.at(cx(a), cy(a), cz(a));
-            const uint8_t tz = ctype(A.flag[z]);
-            if (tz == LIQ || (tz == IFC && A.mark[z] != MK_EMPTIED)) {
-                C fo[19];
-#pragma unroll
-                for (int q = 0; q < 19; ++q) fo[q] = Form<T>::ld(f + (long long)q * S + z, q);
-                C jx, jy, jz;
-                moments<C>(fo, r, jx, jy, jz);
-                ux = jx / r; uy = jy / r; uz = jz / r;
-                use = 1;
-            }
-        }
-        C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
-        int cnt = 0;
-#pragma unroll
-        for (int a = 1; a < 19; ++a) {
-            const int ua = __shfl_sync(full, use, a);
-            const C ra = __shfl_sync(full, r, a);
-            const C xa = __shfl_sync(full, ux, a);
-            const C ya = __shfl_sync(full, uy, a);
-            const C za = __shfl_sync(full, uz, a);
-            if (ua) {
-                sr = sr + ra;
-                sux = sux + xa;
-                suy = suy + ya;
-                suz = suz + za;
-                ++cnt;
-            }
-        }
-        if (lane == 0) {
-            const C rbar = sr / (C)cnt;
-            const C vx = sux / (C)cnt, vy = suy / (C)cnt, vz = suz / (C)cnt;
-            C fe[19];
-            feq_all<C>(rbar, vx, vy, vz, fe);
-#pragma unroll
-            for (int q = 0; q < 19; ++q) Form<T>::st(f + (long long)q * S + p, q, fe[q]);
-            A.m[p] = 0.0;
-            A.rhoi[p] = (double)rbar;
-        }
+        list_append(A.glist, A.gcount, gclaim, (int)z);
+        list_append(A.llist, A.lcount, lclaim, (int)z);
     }
 }
 
@@ -907,7 +1000,9 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_init_state(StepArgs A, int d, con
     A.exs[g] = 0.0;
     double ph = (t == LIQ) ? 1.0 : (t == IFC ? fill[l] : 0.0);
     A.phi[g] = ph;
-    A.phit[g] = (t == LIQ || t == OBS || t == LID) ? 1.0 : (t == GAS ? 0.0 : (ph < 0.0 ? 0.0 : (ph > 1.0 ? 1.0 : ph)));
+    const double pht = (t == LIQ || t == OBS || t == LID) ? 1.0 : (t == GAS ? 0.0 : (ph < 0.0 ? 0.0 : (ph > 1.0 ? 1.0 : ph)));
+    A.phit[g] = pht;
+    if (A.phif) { A.phif[g] = (float)ph; A.phitf[g] = (float)pht; }
     T* f = (T*)A.fdst;
     if (t == LIQ || t == IFC) {
         C fe[19];
@@ -947,8 +1042,9 @@ __global__ void k_export_pdf(const T* f, long long S, long long off, int n, doub
 
 // Launch helpers instantiated once per storage form.
 template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, cudaStream_t s,
-                                         cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join);
-template <typename T> void launch_convert_b(const StepArgs& A, long long nblocks, cudaStream_t s);
+                                         cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,
+                                         cudaEvent_t ei);
+template <typename T> void launch_convert_ab(const StepArgs& A, long long nblocks, cudaStream_t s);
 template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
                                              const double* rho, const double* u, cudaStream_t s);
 template <typename T> void launch_export_pdf(const void* f, long long S, long long off, int n, double* pdf,
@@ -956,17 +1052,21 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
 
 #define FSL_INSTANTIATE_FORM(T)                                                                              \
     template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, cudaStream_t s,               \
-                                      cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {                 \
-        /* liquid cells on s, interface cells on s2 at the same time (disjoint outputs) */                  \
+                                      cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,   \
+                                      cudaEvent_t ei) {                                                      \
+        /* liquid cells on s, interface cells on s2 at the same time (disjoint outputs); */                 \
+        /* el / ei (optional) mark the end of each kernel */                                                \
         cudaEventRecord(fork, s);                                                                            \
         cudaStreamWaitEvent(s2, fork, 0);                                                                    \
-        k_stream_interface<T><<<(unsigned)(2 * ifb), 256, 0, s2>>>(A);                                      \
+        k_stream_interface<T><<<(unsigned)(2 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                           \
+        if (ei) cudaEventRecord(ei, s2);                                                                     \
         k_stream_liquid<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                           \
+        if (el) cudaEventRecord(el, s);                                                                      \
         cudaEventRecord(join, s2);                                                                           \
         cudaStreamWaitEvent(s, join, 0);                                                                     \
     }                                                                                                        \
-    template <> void launch_convert_b<T>(const StepArgs& A, long long nb, cudaStream_t s) {                  \
-        launch_pdl(k_convert_b<T>, (unsigned)nb, 128u, s, A);                                                \
+    template <> void launch_convert_ab<T>(const StepArgs& A, long long nb, cudaStream_t s) {                 \
+        k_convert_ab<T><<<(unsigned)nb, 128, 0, s>>>(A);                                                    \
     }                                                                                                        \
     template <> void launch_init_state<T>(const StepArgs& A, int d, int n, const uint8_t* fl,                \
                                           const double* fill, const double* rho, const double* u,            \

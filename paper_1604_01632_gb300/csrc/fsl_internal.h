@@ -33,7 +33,6 @@ struct CclArgs {
     int max_iter;                // cap on union / find loops
 };
 
-void launch_convert_a(const StepArgs& A, long long nb, cudaStream_t s);
 void launch_convert_c(const StepArgs& A, long long nb, cudaStream_t s);
 void launch_convert_d(const StepArgs& A, long long nb, cudaStream_t s);
 void launch_build_ilist(const StepArgs& A, long long nb, cudaStream_t s);

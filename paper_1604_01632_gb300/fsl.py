@@ -273,9 +273,10 @@ class Simulation:
         self._check(self.L.fsl_set_graphs(self._h, 1 if on else 0))
 
     def phase_ms(self) -> Dict[str, float]:
-        out = (ctypes.c_double * 6)()
+        out = (ctypes.c_double * 7)()
         self._check(self.L.fsl_phase_ms(self._h, out))
-        return dict(zip(("stream_collide", "phase_a", "phase_b", "excess", "update", "labelling"), list(out)))
+        return dict(zip(("stream_collide", "liquid_end", "interface_end", "phase_ab", "excess", "update",
+                         "labelling"), list(out)))
 
     def stream_collide_ms(self) -> float:
         return float(self.L.fsl_stream_collide_ms(self._h))
