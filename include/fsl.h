@@ -44,7 +44,8 @@ typedef enum {
     FSL_ERR_NAN = -4,                 /* a cell density became NaN */
     FSL_ERR_CCL_NOT_CONVERGED = -5,   /* union-find pass hit its iteration cap */
     FSL_ERR_TABLE_FULL = -6,          /* more bubbles than bubble_capacity */
-    FSL_ERR_CUDA = -7                 /* a CUDA runtime call failed */
+    FSL_ERR_CUDA = -7,                /* a CUDA runtime call failed */
+    FSL_ERR_SYNC = -8                 /* a grid barrier of the conversion kernel timed out */
 } fsl_status;
 
 enum { FSL_LIQUID = 0, FSL_INTERFACE = 1, FSL_GAS = 2, FSL_OBSTACLE = 3, FSL_LID = 4 };
@@ -169,11 +170,11 @@ fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
 
 /* Device time per phase of the steps timed since fsl_set_timing(h, 1), summed,
  * in milliseconds, when the handle runs without graphs (fsl_set_graphs(h, 0)):
- * out (array of 7): [0] stream-collide (liquid and interface kernels, which run
+ * out (array of 4): [0] stream-collide (liquid and interface kernels, which run
  * at the same time), [1] start of the pair to the end of the liquid kernel, [2]
- * start of the pair to the end of the interface kernel, [3] conversion phases
- * A and B, [4] excess mass and triggers, [5] fill-level and volume update, [6]
- * labelling.  Read after fsl_sync. */
+ * start of the pair to the end of the interface kernel, [3] cell conversion
+ * and, on steps that set a merge / split trigger, the labelling (one
+ * cooperative kernel).  Read after fsl_sync. */
 fsl_status fsl_phase_ms(const fsl_domain* h, double* out);
 
 /* Counts of the cell types of domain d (array of 5), synchronises. */

@@ -30,11 +30,11 @@ struct fsl_domain {
     size_t fbytes = 8;            // bytes per stored PDF
     cudaStream_t user = nullptr;  // caller's stream (may be the legacy default)
     cudaStream_t ls = nullptr;    // library stream (capturable)
-    cudaStream_t ls2 = nullptr;   // second stream, used only to capture the labelling body
     cudaStream_t ls3 = nullptr;   // interface kernels, concurrent with the liquid kernel
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     int ifblocks = 304;           // grid of the list kernels (2 blocks per SM)
+    int convblocks = 152;         // grid of the cooperative conversion kernel
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
     std::vector<Dom> hdoms;
@@ -59,6 +59,7 @@ struct fsl_domain {
     long long *pool = nullptr, *nif = nullptr;
     int* trig = nullptr;
     int* status = nullptr;
+    unsigned* bar = nullptr;      // grid barrier of the conversion kernel
     int* ilist[2] = {nullptr, nullptr};   // interface list read by a step starting from buffer k
     int* icount[2] = {nullptr, nullptr};
     int *mlist = nullptr, *mcount = nullptr, *glist = nullptr, *gcount = nullptr, *llist = nullptr, *lcount = nullptr;
@@ -93,7 +94,7 @@ struct fsl_domain {
     double k1_ms = 0.0;
     std::vector<cudaEvent_t> phpool;   // direct mode: events between the kernels of a step
     size_t phused = 0;
-    double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    double phase_ms[4] = {0, 0, 0, 0};
     std::vector<void*> allocs;
     std::string err;
 };
@@ -152,6 +153,7 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.nif = h->nif;
     A.trig = h->trig;
     A.status = h->status;
+    A.bar = h->bar;
     A.ndom = h->ndom;
     A.ilist = h->ilist[src];
     A.icount = h->icount[src];
@@ -167,7 +169,6 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.recv = h->recv;
     A.stepno = h->stepno;
     A.icnt = h->icnt;
-    A.cond = 0;
     A.d0 = h->hdoms[0];
     return A;
 }
@@ -191,6 +192,8 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     K.slot_dom = h->d_slot_dom;
     K.nslots_total = h->nslots;
     K.runs = h->runs;
+    K.vsfx = h->vsfx;
+    K.constp = h->constp;
     K.initial = initial;
     // find() walks strictly decreasing indices and every retry of unite()
     // follows a link made by another thread, so both loops end; the caps only
@@ -208,16 +211,26 @@ void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st, cudaEvent_t el
     }
 }
 
-void launch_cb(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
+cudaError_t launch_conv(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
+    const CclArgs K = ccl_args(h, 0);
     switch (h->precision) {
-    case FSL_P_FP64: launch_convert_ab<double>(A, h->ifblocks, st); break;
-    case FSL_P_FP32: launch_convert_ab<float>(A, h->ifblocks, st); break;
-    case FSL_P_F16S: launch_convert_ab<__half>(A, h->ifblocks, st); break;
-    default: launch_convert_ab<__nv_bfloat16>(A, h->ifblocks, st); break;
+    case FSL_P_FP64: return launch_convert<double>(A, K, h->convblocks, st);
+    case FSL_P_FP32: return launch_convert<float>(A, K, h->convblocks, st);
+    case FSL_P_F16S: return launch_convert<__half>(A, K, h->convblocks, st);
+    default: return launch_convert<__nv_bfloat16>(A, K, h->convblocks, st);
     }
 }
 
-// Stream-collide and the three conversion kernels of one step (5 kernels).
+int conv_blocks_per_sm(int precision) {
+    switch (precision) {
+    case FSL_P_FP64: return convert_blocks_per_sm<double>();
+    case FSL_P_FP32: return convert_blocks_per_sm<float>();
+    case FSL_P_F16S: return convert_blocks_per_sm<__half>();
+    default: return convert_blocks_per_sm<__nv_bfloat16>();
+    }
+}
+
+// Stream-collide pair and the conversion kernel of one step (3 kernels).
 // With e0/e1 the stream-collide pair is bracketed by event records (captured
 // as event-record nodes when the stream is capturing; their nodes go to rec).
 cudaEvent_t next_phase_event(fsl_domain* h) {
@@ -253,13 +266,9 @@ int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e
         launch_k1(h, A, h->ls);
     }
     if (e1) { record(e1); last_node(1); }
-    launch_cb(h, A, h->ls);
+    launch_conv(h, A, h->ls);
     if (phases) cudaEventRecord(next_phase_event(h), h->ls);
-    launch_convert_c(A, h->ifblocks, h->ls);
-    if (phases) cudaEventRecord(next_phase_event(h), h->ls);
-    launch_convert_d(A, h->ifblocks, h->ls);
-    if (phases) cudaEventRecord(next_phase_event(h), h->ls);
-    return 5;
+    return 3;
 }
 
 std::pair<cudaEvent_t, cudaEvent_t> next_events(fsl_domain* h) {
@@ -292,7 +301,8 @@ fsl_status latch(fsl_domain* h) {
                            : st == FSL_ERR_NAN ? "a density became NaN"
                            : st == FSL_ERR_CCL_NOT_CONVERGED ? "bubble labelling hit its iteration cap"
                            : st == FSL_ERR_TABLE_FULL ? "bubble table full"
-                                                      : "device error";
+                           : st == FSL_ERR_SYNC ? "a grid barrier of the conversion kernel timed out"
+                                                : "device error";
         return fail(h, (fsl_status)st, what);
     }
     return FSL_OK;
@@ -303,7 +313,7 @@ fsl_status ensure_initial(fsl_domain* h) {
     for (int d = 0; d < h->ndom; ++d)
         if (!h->inited[d]) return fail(h, FSL_ERR_ARG, "every domain must be initialised first");
     StepArgs A = step_args(h, h->cur);
-    h->launches += launch_ccl(A, ccl_args(h, 1), h->nblocks, h->vsfx, h->constp, h->ls);
+    h->launches += launch_ccl(A, ccl_args(h, 1), h->nblocks, h->ls);
     CK(h, cudaMemsetAsync(h->icount[h->cur], 0, sizeof(int), h->ls));
     CK(h, cudaMemsetAsync(h->icnt, 0, 8 * (size_t)h->ndom, h->ls));
     launch_build_ilist(A, h->nblocks, h->ls);
@@ -322,9 +332,6 @@ fsl_status build_graph(fsl_domain* h, int start, int kind) {
     const int nsteps = kind == 0 ? 2 : 1;
     cudaGraph_t G = nullptr;
     CK(h, cudaGraphCreate(&G, 0));
-    cudaGraphConditionalHandle hc[2];
-    for (int j = 0; j < nsteps; ++j)
-        CK(h, cudaGraphConditionalHandleCreate(&hc[j], G, 0, cudaGraphCondAssignDefault));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (kind == 2) {
         auto ev = next_events(h);
@@ -335,24 +342,7 @@ fsl_status build_graph(fsl_domain* h, int start, int kind) {
     int kk = 0;
     for (int j = 0; j < nsteps; ++j) {
         StepArgs A = step_args(h, j == 0 ? start : 1 - start);
-        A.cond = hc[j];
         kk += enqueue_main(h, A, e0, e1, kind == 2 ? h->rec[start] : nullptr);
-        cudaStreamCaptureStatus cs;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t nd = 0;
-        CK(h, cudaStreamGetCaptureInfo(h->ls, &cs, nullptr, nullptr, &deps, nullptr, &nd));
-        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
-        np.conditional.handle = hc[j];
-        np.conditional.type = cudaGraphCondTypeIf;
-        np.conditional.size = 1;
-        cudaGraphNode_t cn;
-        CK(h, cudaGraphAddNode(&cn, G, deps, nullptr, nd, &np));
-        cudaGraph_t body = np.conditional.phGraph_out[0];
-        CK(h, cudaStreamBeginCaptureToGraph(h->ls2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-        launch_ccl(A, ccl_args(h, 0), h->nblocks, h->vsfx, h->constp, h->ls2);
-        cudaGraph_t tmp = nullptr;
-        CK(h, cudaStreamEndCapture(h->ls2, &tmp));
-        CK(h, cudaStreamUpdateCaptureDependencies(h->ls, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
     }
     cudaGraph_t out = nullptr;
     CK(h, cudaStreamEndCapture(h->ls, &out));
@@ -363,7 +353,7 @@ fsl_status build_graph(fsl_domain* h, int start, int kind) {
     CK(h, cudaGraphInstantiate(&h->graph[start][kind], G, 0));
     if (kind == 2) h->timed_src[start] = G;
     else cudaGraphDestroy(G);
-    h->graph_kernels[kind] = kk;   // the labelling kernels run only on trigger steps
+    h->graph_kernels[kind] = kk;
     if (kind == 2) h->evused -= 2;  // the capture events are placeholders
     return FSL_OK;
 }
@@ -446,10 +436,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     while (hc < 4 * soff) hc <<= 1;
     h->hcap = hc;
 
-    cudaError_t e = upload_tables();
-    if (e != cudaSuccess) { fsl_status st = cuda_fail(h, e, "tables"); delete h; return st; }
-    e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ls2, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         // the interface kernel is a short latency-bound chain: give its stream
         // the highest priority so that its blocks are placed before the
@@ -465,6 +452,12 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms > 0) h->ifblocks = 2 * sms;
+        // the cooperative conversion kernel: every block resident, at most
+        // two per SM (its phases are short lists; fewer blocks make cheaper
+        // barriers)
+        const int per_sm = conv_blocks_per_sm(precision);
+        if (per_sm < 1) e = cudaErrorInvalidConfiguration;
+        h->convblocks = std::max(1, sms) * std::min(2, std::max(1, per_sm));
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
@@ -496,6 +489,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->nif, 8 * n_domains);
     AL(h->trig, sizeof(int) * (n_domains + 1));
     AL(h->status, sizeof(int));
+    AL(h->bar, 2 * sizeof(unsigned));
     AL(h->ilist[0], 4 * N);
     AL(h->ilist[1], 4 * N);
     AL(h->icount[0], sizeof(int));
@@ -553,6 +547,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->nif, 0, 8 * n_domains);
     if (e == cudaSuccess) e = cudaMemset(h->trig, 0, sizeof(int) * (n_domains + 1));
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->bar, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(h->icount[0], 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->icount[1], 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->mcount, 0, sizeof(int));
@@ -657,8 +652,7 @@ fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
     join_in(h);
     int64_t k = 0;
     if (!h->graphs) {
-        // direct launches; the labelling kernels return at once unless the
-        // step set the trigger
+        // direct launches
         for (; k < nsteps; ++k) {
             StepArgs A = step_args(h, h->cur);
             cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -668,8 +662,6 @@ fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
                 e1 = ev.second;
             }
             h->launches += enqueue_main(h, A, e0, e1, nullptr, h->timing);
-            h->launches += launch_ccl(A, ccl_args(h, 0), h->nblocks, h->vsfx, h->constp, h->ls);
-            if (h->timing) cudaEventRecord(next_phase_event(h), h->ls);
             h->cur = 1 - h->cur;
         }
     } else if (h->timing) {
@@ -705,26 +697,21 @@ fsl_status fsl_sync(fsl_domain* h) {
             tot += ms;
         }
         h->k1_ms = tot;
-        // direct mode, six phase events per step: the ends of the liquid and
-        // interface kernels (timed from the start of the pair), then the ends
-        // of the three conversion kernels and of the labelling (each timed
-        // from the end of the one before, the first from the end of the pair)
-        if (h->phused >= 6 && h->phused == 6 * (h->evused / 2)) {
-            for (int k = 0; k < 7; ++k) h->phase_ms[k] = 0.0;
+        // direct mode, three phase events per step: the ends of the liquid
+        // and interface kernels (timed from the start of the pair), then the
+        // end of the conversion kernel (timed from the end of the pair)
+        if (h->phused >= 3 && h->phused == 3 * (h->evused / 2)) {
+            for (int k = 0; k < 4; ++k) h->phase_ms[k] = 0.0;
             for (size_t n = 0; n < h->evused / 2; ++n) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, h->evpool[2 * n], h->evpool[2 * n + 1]);
                 h->phase_ms[0] += ms;
                 for (int k = 0; k < 2; ++k) {
-                    cudaEventElapsedTime(&ms, h->evpool[2 * n], h->phpool[6 * n + k]);
+                    cudaEventElapsedTime(&ms, h->evpool[2 * n], h->phpool[3 * n + k]);
                     h->phase_ms[1 + k] += ms;
                 }
-                cudaEvent_t prev = h->evpool[2 * n + 1];
-                for (int k = 2; k < 6; ++k) {
-                    cudaEventElapsedTime(&ms, prev, h->phpool[6 * n + k]);
-                    h->phase_ms[1 + k] += ms;
-                    prev = h->phpool[6 * n + k];
-                }
+                cudaEventElapsedTime(&ms, h->evpool[2 * n + 1], h->phpool[3 * n + 2]);
+                h->phase_ms[3] += ms;
             }
         }
         h->evused = 0;
@@ -746,7 +733,7 @@ double fsl_stream_collide_ms(const fsl_domain* h) { return h ? h->k1_ms : 0.0; }
 
 fsl_status fsl_phase_ms(const fsl_domain* h, double* out) {
     if (!h || !out) return FSL_ERR_ARG;
-    for (int k = 0; k < 7; ++k) out[k] = h->phase_ms[k];
+    for (int k = 0; k < 4; ++k) out[k] = h->phase_ms[k];
     return FSL_OK;
 }
 
@@ -910,7 +897,6 @@ fsl_status fsl_destroy(fsl_domain* h) {
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ls) cudaStreamDestroy(h->ls);
-    if (h->ls2) cudaStreamDestroy(h->ls2);
     if (h->ls3) cudaStreamDestroy(h->ls3);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);

@@ -17,9 +17,11 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <limits.h>
 #include <stdint.h>
 
 #define FSL_BLOCK 256
+#define FSL_CONV_THREADS 256   // block of the cooperative conversion kernel
 
 namespace fsl {
 
@@ -36,7 +38,7 @@ enum : uint8_t { MK_NONE = 0, MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 3, MK_NEW
                  MK_CFILLED = 5, MK_CEMPTIED = 6 };
 
 // status codes latched by kernels (same values as fsl_status)
-enum { ST_GEOMETRY = -2, ST_NAN = -4, ST_CCL = -5, ST_TABLE_FULL = -6 };
+enum { ST_GEOMETRY = -2, ST_NAN = -4, ST_CCL = -5, ST_TABLE_FULL = -6, ST_SYNC = -8 };
 
 // Fixed-point scales: bubble volumes 2^-32 cells^3, pooled mass 2^-40.
 #define FSL_VOL_ONE 4294967296LL
@@ -141,7 +143,7 @@ struct StepArgs {
     int* recv;                  // step number at which each cell last received excess mass
     int* stepno;                // device step counter
     long long* icnt;            // per-domain interface count at the end of the step
-    unsigned long long cond;    // graph conditional handle set to the trigger (0: none)
+    unsigned* bar;              // grid barrier of the conversion kernel: count, generation
     Dom d0;                     // domain 0, read from the parameter space when ndom == 1
 };
 
@@ -615,23 +617,100 @@ __device__ inline Stencil make_stencil(const Dom& D, long long g) {
 }
 
 
+// Equilibrium (Eq. 3) of the pair that holds direction a (1-18): the
+// symmetric part fp and antisymmetric part fm of the pair's first (odd)
+// direction, as feq_all forms them; f_eq,a = fp + fm for odd a, fp - fm for
+// even a.
+template <typename C>
+__device__ inline void feq_pair(int a, C rho, C ux, C uy, C uz, C usq, C& fp, C& fm) {
+    const int p = (a & 1) ? a : a - 1;
+    const C cu = ((C)rcx(p) * ux + (C)rcy(p) * uy) + (C)rcz(p) * uz;
+    const C wr = weightc<C>(p) * rho;
+    fp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * usq);
+    fm = wr * ((C)3 * cu);
+}
+
+// The collision of `collide` (Eq. 6, TRT with Guo forcing) split so that
+// several threads can share the outputs of one cell: CollidePrep forms the
+// cell's moments and velocity once, collide_out gives output a, each with
+// every operation in the same order as `collide`.
+template <typename C>
+struct CollidePrep {
+    C rho, ux, uy, uz, usq, Fx, Fy, Fz, uF;
+};
+template <typename C, bool FORCE>
+__device__ inline CollidePrep<C> collide_prep(const C* fin, C gx, C gy, C gz) {
+    CollidePrep<C> P;
+    C jx, jy, jz;
+    moments<C>(fin, P.rho, jx, jy, jz);
+    P.Fx = (C)0; P.Fy = (C)0; P.Fz = (C)0;
+    if constexpr (FORCE) {
+        P.Fx = P.rho * gx; P.Fy = P.rho * gy; P.Fz = P.rho * gz;
+        jx = jx + (C)0.5 * P.Fx;
+        jy = jy + (C)0.5 * P.Fy;
+        jz = jz + (C)0.5 * P.Fz;
+    }
+    if constexpr (sizeof(C) == 4) {
+        const C ir = (C)1 / P.rho;
+        P.ux = jx * ir; P.uy = jy * ir; P.uz = jz * ir;
+    } else {
+        P.ux = jx / P.rho; P.uy = jy / P.rho; P.uz = jz / P.rho;
+    }
+    P.usq = P.ux * P.ux + P.uy * P.uy + P.uz * P.uz;
+    P.uF = (C)0;
+    if constexpr (FORCE) P.uF = P.ux * P.Fx + P.uy * P.Fy + P.uz * P.Fz;
+    return P;
+}
+template <typename C, bool FORCE>
+__device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C omp, C omm) {
+    const C cp = (C)1 - (C)0.5 * omp, cm = (C)1 - (C)0.5 * omm;
+    if (a == 0) {
+        const C feq0 = (weightc<C>(0) * P.rho) * ((C)1 - (C)1.5 * P.usq);
+        C out = fin[0] - omp * (fin[0] - feq0);
+        if constexpr (FORCE) {
+            const C S0 = weightc<C>(0) * ((C)-3 * P.uF);
+            out = out + cp * S0;
+        }
+        return out;
+    }
+    const int p = (a & 1) ? a : a - 1;
+    const C w = weightc<C>(p);
+    const C cu = ((C)rcx(p) * P.ux + (C)rcy(p) * P.uy) + (C)rcz(p) * P.uz;
+    const C wr = w * P.rho;
+    const C feqp = wr * (((C)1 + (C)4.5 * (cu * cu)) - (C)1.5 * P.usq);
+    const C feqm = wr * ((C)3 * cu);
+    const C fp = (C)0.5 * (fin[p] + fin[p + 1]);
+    const C fm = (C)0.5 * (fin[p] - fin[p + 1]);
+    const C A = omp * (fp - feqp);
+    const C B = omm * (fm - feqm);
+    C out = (a == p) ? (fin[p] - A) - B : (fin[p + 1] - A) + B;
+    if constexpr (FORCE) {
+        const C cF = ((C)rcx(p) * P.Fx + (C)rcy(p) * P.Fy) + (C)rcz(p) * P.Fz;
+        const C Sp = w * (((C)9 * cu) * cF - (C)3 * P.uF);
+        const C Sm = w * ((C)3 * cF);
+        const C sp = cp * Sp, sm = cm * Sm;
+        out = (a == p) ? (out + sp) + sm : (out + sp) - sm;
+    }
+    return out;
+}
+
 // K1I: interface cells, from the list of interface cells built at the end of
-// the previous step.  A block of 128 threads takes FSL_IFC cells per pass.
-// Load phase, four threads per cell: the 5x5x5 box of fill levels around the
-// cell (rows along x), and for the directions q, q+4, ... the cell's PDFs, the
-// PDF streaming in, the neighbour types and the mass-exchange terms.
-// Gradient phase, four threads per cell: Parker-Youngs gradients at the cell
-// and at its six face neighbours (unit normals there).  Compute phase, one
-// thread per cell, in the oracle's order: stream with bounce-back (Eq. 7),
-// mass exchange over the 18 links (Eq. 10), reconstruction of the PDFs coming
-// from the gas side with the gas density 3 (p_V + 2 sigma kappa) of the
-// cell's bubble (Eqs. 8, 11-15, kappa = 1/2 div n_hat by central differences
-// of the face normals), collision (Eq. 6), then the filled / emptied marks.
-// The FP32-collide forms do all of this in FP32 except the cell mass, which
-// accumulates in FP64.
-#define FSL_IF_THREADS 128
+// the previous step.  A block of 128 threads takes 16 cells per pass, eight
+// threads per cell.  Load phase: the 5x5x5 box of fill levels around the cell
+// (rows along x), and for the directions q, q+8, q+16 the cell's PDFs, the PDF
+// streaming in, the neighbour types and the mass-exchange terms.  Gradient
+// phase: Parker-Youngs gradients at the cell and at its six face neighbours
+// (unit normals there).  Compute phase, the cell's threads sharing its
+// directions, each output formed with the oracle's operations in the oracle's
+// order: stream with bounce-back (Eq. 7), mass exchange over the 18 links
+// (Eq. 10), reconstruction of the PDFs coming from the gas side with the gas
+// density 3 (p_V + 2 sigma kappa) of the cell's bubble (Eqs. 8, 11-15, kappa =
+// 1/2 div n_hat by central differences of the face normals), collision
+// (Eq. 6), then the filled / emptied marks.  The FP32-collide forms do all of
+// this in FP32 except the cell mass, which accumulates in FP64.
+#define FSL_IF_THREADS 128   // 16 cells per pass, eight threads per cell
 template <typename T> struct IfCells {
-    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : 32;
+    static constexpr int n = 16;
 };
 template <typename T>
 struct IfStage {
@@ -640,10 +719,12 @@ struct IfStage {
     C ph[N][125];      // fill levels, 5x5x5 box around the cell
     C fs[N][19];       // own post-collision PDFs of the previous step
     C fy[N][19];       // PDF streaming in from the source cell
+    C fin[N][19];      // PDFs after streaming and reconstruction
     C ex[N][19];       // mass-exchange term of each link (Eq. 10)
     C nrm[N][7][3];    // gradient at the cell, unit normals at the face neighbours
     C pv[N];           // bubble pressure (Eq. 13)
     double m[N];       // mass
+    int g[N];          // cell
     uint8_t ty[N][19];
     uint8_t tz[N][19];
 };
@@ -651,10 +732,10 @@ struct IfStage {
 __device__ inline int ph_index(int dx, int dy, int dz) { return (dx + 2) + 5 * (dy + 2) + 25 * (dz + 2); }
 
 template <typename T>
-__global__ void __launch_bounds__(FSL_IF_THREADS) k_stream_interface(StepArgs A) {
+__global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : 6) k_stream_interface(StepArgs A) {
     using C = typename Form<T>::C;
     constexpr int N = IfCells<T>::n;
-    constexpr int TPC = FSL_IF_THREADS / N;   // threads per cell in the load and gradient phases
+    constexpr int TPC = FSL_IF_THREADS / N;   // threads per cell
     __shared__ IfStage<T> sh;
     if (blockIdx.x == 0) {
         // per-step counters; the previous step's kernels are done with them
@@ -682,26 +763,56 @@ __global__ void __launch_bounds__(FSL_IF_THREADS) k_stream_interface(StepArgs A)
     const int c = threadIdx.x / TPC;      // cell of this thread in the load and gradient phases
     const int q = threadIdx.x % TPC;
     for (int i0 = blockIdx.x * N; i0 < cnt; i0 += gridDim.x * N) {
-        // ---------------- load phase
+        // ---------------- load phase: every global load of the thread is
+        // issued before the first shared-memory store, so that the phase costs
+        // about two memory latencies (the list entry, then everything else)
         if (i0 + c < cnt) {
             const long long g = A.ilist[i0 + c];
             const Dom D = get_dom(A, block_dom(A, g));
             const Stencil st = make_stencil(D, g);
-            // rows (dy, dz) of the box, five cells along x each
-            for (int r = q; r < 25; r += TPC) {
-                const int dy = r % 5 - 2, dz = r / 5 - 2;
-                C* row = &sh.ph[c][5 * r];
-                if (st.x >= 2 && st.x < st.nx - 2) {
-                    const long long b = st.at(0, dy, dz);
+            constexpr int NR = (25 + TPC - 1) / TPC;   // box rows of this thread
+            constexpr int ND = (19 + TPC - 1) / TPC;   // directions of this thread
+            C rowv[NR][5];
+            const bool xin = st.x >= 2 && st.x < st.nx - 2;
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) row[k] = phtc[b + (k - 2)];
-                } else {
+            for (int k = 0; k < NR; ++k) {
+                const int r = q + TPC * k;
+                if (r < 25) {
+                    const int dy = r % 5 - 2, dz = r / 5 - 2;
+                    if (xin) {
+                        const long long b = st.at(0, dy, dz);
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) row[k] = phtc[st.at(k - 2, dy, dz)];
+                        for (int e = 0; e < 5; ++e) rowv[k][e] = phtc[b + (e - 2)];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 5; ++e) rowv[k][e] = phtc[st.at(e - 2, dy, dz)];
+                    }
                 }
             }
+            C fsv[ND], fyv[ND], fzv[ND], phz[ND];
+            uint8_t tyv[ND], tzv[ND];
+#pragma unroll
+            for (int k = 0; k < ND; ++k) {
+                const int a = q + TPC * k;
+                if (a < 19) {
+                    fsv[k] = Form<T>::ld(src + (long long)a * S + g, a);
+                    if (a > 0) {
+                        const int ab = opp(a);
+                        const int ax = rcx(a), ay = rcy(a), az = rcz(a);
+                        const long long y = st.at(-ax, -ay, -az);
+                        const long long z = st.at(ax, ay, az);
+                        tyv[k] = ctype(A.flag[y]);
+                        fyv[k] = Form<T>::ld(src + (long long)a * S + y, a);
+                        tzv[k] = ctype(A.flag[z]);
+                        fzv[k] = Form<T>::ld(src + (long long)ab * S + z, ab);
+                        phz[k] = phic[z];
+                    }
+                }
+            }
+            const C phx = phic[g];
             if (q == TPC - 1) {
                 sh.m[c] = A.m[g];
+                sh.g[c] = (int)g;
                 const int bub = A.id[g];
                 if constexpr (sizeof(C) == 8)
                     sh.pv[c] = bub >= 0 ? bubble_pressure(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : 1.0 / 3.0;
@@ -709,22 +820,28 @@ __global__ void __launch_bounds__(FSL_IF_THREADS) k_stream_interface(StepArgs A)
                     sh.pv[c] = bub >= 0 ? bubble_pressure_f(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub])
                                         : (float)(1.0 / 3.0);
             }
-            const C phx = phic[g];
-            for (int a = q; a < 19; a += TPC) {
-                const C fsa = Form<T>::ld(src + (long long)a * S + g, a);
-                sh.fs[c][a] = fsa;
-                if (a == 0) continue;
-                const int ab = opp(a);
-                const int ax = rcx(a), ay = rcy(a), az = rcz(a);
-                const long long y = st.at(-ax, -ay, -az);
-                sh.ty[c][a] = ctype(A.flag[y]);
-                sh.fy[c][a] = Form<T>::ld(src + (long long)a * S + y, a);
-                const long long z = st.at(ax, ay, az);
-                const uint8_t tz = ctype(A.flag[z]);
-                sh.tz[c][a] = tz;
-                if (tz == LIQ || tz == IFC) {
-                    const C e = Form<T>::ld(src + (long long)ab * S + z, ab) - fsa;
-                    sh.ex[c][a] = tz == IFC ? ((C)0.5 * (phx + phic[z])) * e : e;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                const int r = q + TPC * k;
+                if (r < 25) {
+#pragma unroll
+                    for (int e = 0; e < 5; ++e) sh.ph[c][5 * r + e] = rowv[k][e];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < ND; ++k) {
+                const int a = q + TPC * k;
+                if (a < 19) {
+                    sh.fs[c][a] = fsv[k];
+                    if (a > 0) {
+                        sh.ty[c][a] = tyv[k];
+                        sh.fy[c][a] = fyv[k];
+                        sh.tz[c][a] = tzv[k];
+                        if (tzv[k] == LIQ || tzv[k] == IFC) {
+                            const C e = fzv[k] - fsv[k];
+                            sh.ex[c][a] = tzv[k] == IFC ? ((C)0.5 * (phx + phz[k])) * e : e;
+                        }
+                    }
                 }
             }
         }
@@ -763,84 +880,107 @@ __global__ void __launch_bounds__(FSL_IF_THREADS) k_stream_interface(StepArgs A)
             }
         }
         __syncthreads();
-        // ---------------- compute phase, one thread per cell
-        if (threadIdx.x < 32) {
-            const int cc = threadIdx.x;
-            uint8_t mk = MK_NONE;
+        // ---------------- compute phase, the cell's TPC threads share its
+        // directions (a = q, q + TPC, ...); the cell's moments are formed by
+        // each of them in the same order
+        {
+            const bool act = i0 + c < cnt;
             long long g = 0;
-            if (cc < N && i0 + cc < cnt) {
-                g = A.ilist[i0 + cc];
+            uint8_t mk = MK_NONE;
+            if (act) {
+                g = sh.g[c];
                 const Dom D = get_dom(A, block_dom(A, g));
                 const Par<C> R = par_of<C>(D);
-                C fs[19];
-#pragma unroll
-                for (int a = 0; a < 19; ++a) fs[a] = sh.fs[cc][a];
                 C rs, jsx, jsy, jsz;
-                moments<C>(fs, rs, jsx, jsy, jsz);
+                moments<C>(sh.fs[c], rs, jsx, jsy, jsz);
                 const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
-                const C dX = sh.nrm[cc][1][0] - sh.nrm[cc][2][0];
-                const C dY = sh.nrm[cc][3][1] - sh.nrm[cc][4][1];
-                const C dZ = sh.nrm[cc][5][2] - sh.nrm[cc][6][2];
+                const C usg = ugx * ugx + ugy * ugy + ugz * ugz;
+                const C dX = sh.nrm[c][1][0] - sh.nrm[c][2][0];
+                const C dY = sh.nrm[c][3][1] - sh.nrm[c][4][1];
+                const C dZ = sh.nrm[c][5][2] - sh.nrm[c][6][2];
                 const C kappa = (C)0.25 * ((dX + dY) + dZ);
-                const C gx = sh.nrm[cc][0][0], gy = sh.nrm[cc][0][1], gz = sh.nrm[cc][0][2];
-                const C pg = sh.pv[cc] + R.sigma2 * kappa;
-                const C rg = (C)3 * pg;
-                C fg[19];
-                feq_all<C>(rg, ugx, ugy, ugz, fg);
-                C fin[19];
-                fin[0] = fs[0];
-#pragma unroll
-                for (int a = 1; a < 19; ++a) {
-                    const int ab = opp(a);
-                    const uint8_t ty = sh.ty[cc][a];
-                    if (ty == OBS) {
-                        fin[a] = fs[ab];
-                    } else if (ty == LID) {
-                        const C cuw = cdot<C>(a, R.lid[0], R.lid[1], R.lid[2]);
-                        fin[a] = fs[ab] + ((C)6 * weightc<C>(a)) * cuw;
-                    } else if (ty == GAS) {
-                        fin[a] = (fg[a] + fg[ab]) - fs[ab];
+                const C gx = sh.nrm[c][0][0], gy = sh.nrm[c][0][1], gz = sh.nrm[c][0][2];
+                const C rg = (C)3 * (sh.pv[c] + R.sigma2 * kappa);
+                for (int a = q; a < 19; a += TPC) {
+                    C fin;
+                    if (a == 0) {
+                        fin = sh.fs[c][0];
                     } else {
-                        fin[a] = sh.fy[cc][a];
-                        if (D.normal_rule && cdot<C>(a, gx, gy, gz) > (C)0) fin[a] = (fg[a] + fg[ab]) - fs[ab];
+                        const int ab = opp(a);
+                        const C fsb = sh.fs[c][ab];
+                        const uint8_t ty = sh.ty[c][a];
+                        if (ty == OBS) {
+                            fin = fsb;
+                        } else if (ty == LID) {
+                            const C cuw = ((C)rcx(a) * R.lid[0] + (C)rcy(a) * R.lid[1]) + (C)rcz(a) * R.lid[2];
+                            fin = fsb + ((C)6 * weightc<C>(a)) * cuw;
+                        } else {
+                            C fp, fm;
+                            feq_pair<C>(a, rg, ugx, ugy, ugz, usg, fp, fm);
+                            const C fga = (a & 1) ? fp + fm : fp - fm;
+                            const C fgb = (a & 1) ? fp - fm : fp + fm;
+                            if (ty == GAS) {
+                                fin = (fga + fgb) - fsb;
+                            } else {
+                                fin = sh.fy[c][a];
+                                if (D.normal_rule && ((C)rcx(a) * gx + (C)rcy(a) * gy) + (C)rcz(a) * gz > (C)0)
+                                    fin = (fga + fgb) - fsb;
+                            }
+                        }
                     }
+                    sh.fin[c][a] = fin;
                 }
-                // mass exchange, summed in direction order (Eq. 10); the cell
-                // mass itself accumulates in FP64 for every form
-                C dm = (C)0;
-                bool has_gas = false, has_liq = false;
-#pragma unroll
-                for (int a = 1; a < 19; ++a) {
-                    const uint8_t tz = sh.tz[cc][a];
-                    if (tz == LIQ || tz == IFC) dm = dm + sh.ex[cc][a];
-                    has_gas |= tz == GAS;
-                    has_liq |= tz == LIQ;
-                }
-                const double mnew = sh.m[cc] + (double)dm;
-                C fout[19];
-                const C rho = collide_any<C>(D.has_force, fin, fout, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
-                if (!(rho == rho)) set_status(A.status, ST_NAN);
-#pragma unroll
-                for (int a = 0; a < 19; ++a) Form<T>::st(dst + (long long)a * S + g, a, fout[a]);
-                A.m[g] = mnew;
-                A.rhoi[g] = (double)rho;
-                bool filled, emptied;
-                if constexpr (sizeof(C) == 8) {
-                    filled = mnew > (1.0 + D.eps) * rho;
-                    emptied = mnew < (-D.eps) * rho;
+            }
+            __syncwarp();
+            if (act) {
+                const Dom D = get_dom(A, block_dom(A, g));
+                const Par<C> R = par_of<C>(D);
+                C rho;
+                if (D.has_force) {
+                    const CollidePrep<C> P = collide_prep<C, true>(sh.fin[c], R.g[0], R.g[1], R.g[2]);
+                    rho = P.rho;
+                    for (int a = q; a < 19; a += TPC)
+                        Form<T>::st(dst + (long long)a * S + g, a, collide_out<C, true>(a, sh.fin[c], P, R.omp, R.omm));
                 } else {
-                    const float mf = (float)mnew;
-                    filled = mf > (1.f + D.feps) * rho;
-                    emptied = mf < (-D.feps) * rho;
+                    const CollidePrep<C> P = collide_prep<C, false>(sh.fin[c], (C)0, (C)0, (C)0);
+                    rho = P.rho;
+                    for (int a = q; a < 19; a += TPC)
+                        Form<T>::st(dst + (long long)a * S + g, a, collide_out<C, false>(a, sh.fin[c], P, R.omp, R.omm));
                 }
-                if (filled) mk = MK_FILLED;
-                else if (emptied) mk = MK_EMPTIED;
-                else if (D.lonely_rule) {
-                    // a cell that no longer separates liquid from gas
-                    if (!has_gas) mk = MK_FILLED;
-                    else if (!has_liq) mk = MK_EMPTIED;
+                if (q == 0) {
+                    if (!(rho == rho)) set_status(A.status, ST_NAN);
+                    // mass exchange, summed in direction order (Eq. 10); the
+                    // cell mass itself accumulates in FP64 for every form
+                    C dm = (C)0;
+                    bool has_gas = false, has_liq = false;
+#pragma unroll
+                    for (int a = 1; a < 19; ++a) {
+                        const uint8_t tz = sh.tz[c][a];
+                        if (tz == LIQ || tz == IFC) dm = dm + sh.ex[c][a];
+                        has_gas |= tz == GAS;
+                        has_liq |= tz == LIQ;
+                    }
+                    const double mnew = sh.m[c] + (double)dm;
+                    A.m[g] = mnew;
+                    A.rhoi[g] = (double)rho;
+                    bool filled, emptied;
+                    if constexpr (sizeof(C) == 8) {
+                        filled = mnew > (1.0 + D.eps) * rho;
+                        emptied = mnew < (-D.eps) * rho;
+                    } else {
+                        const float mf = (float)mnew;
+                        filled = mf > (1.f + D.feps) * rho;
+                        emptied = mf < (-D.feps) * rho;
+                    }
+                    if (filled) mk = MK_FILLED;
+                    else if (emptied) mk = MK_EMPTIED;
+                    else if (D.lonely_rule) {
+                        // a cell that no longer separates liquid from gas
+                        if (!has_gas) mk = MK_FILLED;
+                        else if (!has_liq) mk = MK_EMPTIED;
+                    }
+                    A.mark[g] = mk;
                 }
-                A.mark[g] = mk;
             }
             list_append(A.mlist, A.mcount, mk != MK_NONE, (int)g);
         }
@@ -883,13 +1023,8 @@ __device__ inline bool still_emptied(const StepArgs& A, const Dom& D, long long 
 // emptied neighbour: the new cell keeps its PDFs, takes m = rho and joins the
 // emptied cell's bubble.
 template <typename T>
-__global__ void __launch_bounds__(128) k_convert_ab(StepArgs A) {
+__device__ inline void convert_ab_phase(const StepArgs& A) {
     using C = typename Form<T>::C;
-    if (blockIdx.x == 0) {
-        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
-        if (threadIdx.x == 0) *A.icount_next = 0;
-    }
-    pdl_trigger();
     const int nm = *A.mcount;
     const int total = 18 * nm;
     const long long S = A.stride;
@@ -972,6 +1107,537 @@ __global__ void __launch_bounds__(128) k_convert_ab(StepArgs A) {
     }
 }
 
+// Sum v over the warp into base[key] with one atomic when every lane has the
+// same key; key < 0 contributes nothing.  Every lane of the warp must call.
+__device__ inline void warp_add(long long* base, int key, long long v) {
+    const unsigned full = 0xffffffffu;
+    const int k0 = __shfl_sync(full, key, 0);
+    if (__all_sync(full, key == k0)) {
+        if (k0 < 0) return;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd((unsigned long long*)&base[k0], (unsigned long long)v);
+    } else if (key >= 0 && v != 0) {
+        atomicAdd((unsigned long long*)&base[key], (unsigned long long)v);
+    }
+}
+
+// 3x3x3 cube around a cell, bit k = (dx+1) + 3 (dy+1) + 9 (dz+1); bit 13 is the
+// centre.  Face or edge neighbours of cube cell k inside the cube, the centre
+// left out (a walk must not pass through the removed cell).
+__device__ inline unsigned cube_adj18(int k) {
+    const int kx = k % 3 - 1, ky = (k / 3) % 3 - 1, kz = k / 9 - 1;
+    unsigned a = 0;
+    for (int j = 0; j < 27; ++j) {
+        const int ax = j % 3 - 1 - kx, ay = (j / 3) % 3 - 1 - ky, az = j / 9 - 1 - kz;
+        if (ax < -1 || ax > 1 || ay < -1 || ay > 1 || az < -1 || az > 1) continue;
+        const int dist = (ax != 0) + (ay != 0) + (az != 0);
+        if (dist >= 1 && dist <= 2) a |= 1u << j;
+    }
+    return a & ~(1u << 13);
+}
+// bits of the 18 face / edge neighbours of the centre
+__host__ __device__ constexpr unsigned cube_mask18() {
+    unsigned m = 0;
+    for (int k = 0; k < 27; ++k) {
+        const int dk = (k % 3 != 1) + ((k / 3) % 3 != 1) + (k / 9 != 1);
+        if (dk >= 1 && dk <= 2) m |= 1u << k;
+    }
+    return m;
+}
+
+// Local test that removing the filled cell at the centre of the cube cannot
+// split its bubble: the gas/interface cells among its 18 neighbours must stay
+// connected inside the cube (18-connectivity) without the centre.  adj is
+// cube_adj18 tabulated (shared memory).
+__device__ inline bool removal_is_local(unsigned fg, const unsigned* adj) {
+    constexpr unsigned kMask18 = cube_mask18();
+    const unsigned targets = fg & kMask18;
+    if (targets == 0) return true;
+    unsigned reach = targets & (~targets + 1u);   // lowest target
+    for (int it = 0; it < 27; ++it) {
+        unsigned grow = reach;
+        unsigned r = reach;
+        while (r) {
+            const int k = __ffs(r) - 1;
+            r &= r - 1;
+            grow |= adj[k];
+        }
+        grow &= fg;
+        if (grow == reach) break;
+        reach = grow;
+    }
+    return (targets & ~reach) == 0;
+}
+
+// Phase C, over the marked list and the new-from-liquid list: excess mass of
+// converted cells (filled: m - rho, emptied: m) split equally among the
+// neighbours that are interface after conversion, else pooled; merge / split
+// triggers.  Taking the filled cells away one at a time in index order, each
+// removal must pass the local test with the lower-index filled cells already
+// gone and the higher-index ones still present, or the labelling runs.
+__device__ inline void convert_c_phase(const StepArgs& A, const unsigned* adj) {
+    const int nm = *A.mcount, nl = *A.lcount;
+    const int total = nm + nl;
+    const int step = *A.stepno;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const long long g = i < nm ? A.mlist[i] : A.llist[i - nm];
+        const int d = block_dom(A, g);
+        const Dom D = get_dom(A, d);
+        const Cell c = make_cell(D, g);
+        const uint8_t mk = A.mark[g];
+        if (i < nm) {
+            if (mk != MK_FILLED && mk != MK_EMPTIED) continue;   // emptied mark cancelled in phase A
+            const double mex = (mk == MK_FILLED) ? A.m[g] - A.rhoi[g] : A.m[g];
+            int k = 0;
+            for (int a = 1; a < 19; ++a) {
+                const long long z = c.at(cx(a), cy(a), cz(a));
+                if (new_type(ctype(A.flag[z]), A.mark[z]) == IFC) {
+                    ++k;
+                    A.recv[z] = step;   // z pulls a share in the update phase
+                }
+            }
+            if (k > 0) A.exs[g] = mex / (double)k;
+            else atomicAdd((unsigned long long*)&A.pool[d], (unsigned long long)__double2ll_rn(mex * 1099511627776.0));
+            if (mk == MK_FILLED) {
+                unsigned fgm = 0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (dx == 0 && dy == 0 && dz == 0) continue;
+                            const long long z = c.at(dx, dy, dz);
+                            const uint8_t tz = ctype(A.flag[z]), mz = A.mark[z];
+                            const uint8_t ntz = new_type(tz, mz);
+                            const bool later_filled = (tz == IFC && (mz == MK_FILLED || mz == MK_CFILLED) && z > g);
+                            if (ntz == GAS || ntz == IFC || later_filled)
+                                fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+                        }
+                if (!removal_is_local(fgm, adj)) {
+                    atomicExch(&A.trig[1 + d], 1);
+                    atomicExch(A.trig, 1);
+                }
+            }
+            A.cstep[g] = step;
+            A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
+            atomicAdd((unsigned long long*)&A.nif[d], (unsigned long long)-1LL);
+            continue;
+        }
+        // new interface cell from liquid: a neighbour of another bubble merges
+        const int b = A.id[g];
+        for (int a = 1; a < 19; ++a) {
+            const long long z = c.at(cx(a), cy(a), cz(a));
+            const uint8_t ntz = new_type(ctype(A.flag[z]), A.mark[z]);
+            if ((ntz == GAS || ntz == IFC) && A.id[z] != b) {
+                atomicExch(&A.trig[1 + d], 1);
+                atomicExch(A.trig, 1);
+                break;
+            }
+        }
+    }
+}
+
+// Phase D, over the interface list and the two new-interface lists: receivers
+// pull the excess shares of converted neighbours in direction order and the
+// pool share, phi = m / rho (Eq. 9); converted cells take their new type;
+// bubble volumes change by exact fixed-point differences; the interface list
+// of the next step; reservoir drain; the graph condition of the labelling.
+__device__ inline void convert_d_phase(const StepArgs& A) {
+    const int ni = *A.icount, ng = *A.gcount, nl = *A.lcount;
+    const int total = ni + ng + nl;
+    const int step = *A.stepno;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < total;
+        long long g = 0;
+        if (valid) g = i < ni ? A.ilist[i] : (i < ni + ng ? A.glist[i - ni] : A.llist[i - ni - ng]);
+        const int d = valid ? block_dom(A, g) : 0;
+        int key = -1;
+        long long dv = 0;
+        int ckey = -1;
+        long long dc = 0;
+        bool keep = false;
+        if (valid) {
+            // everything the cell needs, loaded together
+            const uint8_t f = A.flag[g];
+            const uint8_t mk = A.mark[g];
+            key = A.id[g];
+            const double m0 = A.m[g], rh = A.rhoi[g], ph0 = A.phi[g];
+            const int rs = A.recv[g];
+            const long long nI = A.nif[d];
+            const long long pool = A.pool[d];
+            const uint8_t t = ctype(f);
+            if (t == IFC && mk == MK_CFILLED) {
+                dv = -volume_term(IFC, ph0);
+                ckey = key;
+                dc = -1;
+                A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
+                A.phi[g] = 1.0;
+                A.phit[g] = 1.0;
+                if (A.phif) { A.phif[g] = 1.f; A.phitf[g] = 1.f; }
+                A.id[g] = -1;
+                A.mark[g] = MK_NONE;
+            } else if (t == IFC && mk == MK_CEMPTIED) {
+                dv = FSL_VOL_ONE - volume_term(IFC, ph0);
+                A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
+                A.phi[g] = 0.0;
+                A.phit[g] = 0.0;
+                if (A.phif) { A.phif[g] = 0.f; A.phitf[g] = 0.f; }
+                A.m[g] = 0.0;
+                A.mark[g] = MK_NONE;
+            } else {
+                double sm = m0;
+                if (rs == step) {
+                    // a converted neighbour listed this cell among its receivers
+                    const Dom D = get_dom(A, d);
+                    const Cell c = make_cell(D, g);
+                    for (int a = 1; a < 19; ++a) {
+                        const long long z = c.at(cx(a), cy(a), cz(a));
+                        if (A.cstep[z] == step) sm = sm + A.exs[z];
+                    }
+                }
+                if (nI > 0) {
+                    const double share = ((double)pool * 9.094947017729282379150390625e-13) / (double)nI;
+                    sm = sm + share;
+                }
+                const double phn = sm / rh;
+                const long long told = volume_term(t, ph0);
+                A.m[g] = sm;
+                A.phi[g] = phn;
+                const double pht = phn < 0.0 ? 0.0 : (phn > 1.0 ? 1.0 : phn);
+                A.phit[g] = pht;
+                if (A.phif) { A.phif[g] = (float)phn; A.phitf[g] = (float)pht; }
+                if (t != IFC) A.flag[g] = (uint8_t)((f & ~K_TYPE) | IFC);
+                dv = volume_term(IFC, phn) - told;
+                if (t == LIQ) { ckey = key; dc = 1; }
+                keep = true;
+            }
+        }
+        warp_add(A.vfx, dv != 0 ? key : -1, dv);
+        warp_add(A.ncells, ckey, dc);
+        warp_add(A.icnt, keep ? d : -1, 1);
+        list_append(A.ilist_next, A.icount_next, keep, (int)g);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // reservoir drain of every domain whose seed cell is still gas or
+        // interface (types read through the marks, which stay consistent
+        // while other threads update the flags)
+        for (int d = 0; d < A.ndom; ++d) {
+            const Dom D = get_dom(A, d);
+            if (D.seed < 0) continue;
+            const long long gs = D.off + D.seed;
+            const uint8_t nt = new_type(ctype(A.flag[gs]), A.mark[gs]);
+            const int b = A.id[gs];
+            if ((nt == GAS || nt == IFC) && b >= 0)
+                atomicAdd((unsigned long long*)&A.vxfx[b], (unsigned long long)(-D.rate_fx));
+        }
+        *A.mcount = 0;
+    }
+}
+
+// Scratch of the connected-component labelling and bubble-table rebuild.
+struct CclArgs {
+    int* lab;                    // union-find parent per cell (global index), -1 background
+    int* aux;                    // new slot of each root cell
+    unsigned long long* hkeys;   // (new slot << 32 | old slot) overlap keys, ~0 empty
+    long long* hvals;            // overlap volumes V_{c,b}, fixed point
+    long long hcap;              // power of two
+    long long* nvfx;             // new table (slot-indexed)
+    long long* nvxfx;
+    long long* nvsfx;
+    long long* nncells;
+    int* nconstp;
+    int* croot;                  // root cell (global index) of each new slot
+    long long* vtot;             // per old slot: total volume over all new components
+    int* minc;                   // per old slot: lowest root among its components
+    int* nslot;                  // per domain: slots in use
+    const int* slot_dom;         // slot -> domain
+    long long nslots_total;
+    long long* runs;             // labelling passes run after initialisation
+    long long* vsfx;             // bubble tables written by the install phase
+    int* constp;
+    int initial;                 // 1: first labelling after initialisation (V* = V)
+    int max_iter;                // cap on union / find loops
+};
+
+
+// --------------------------------------------- connected-component labelling
+// Bubbles are the 18-connected components of gas + interface cells (Sec. 2.3);
+// the paper's serial flood fill and its colour unification across processes
+// (Sec. 2.4.1) become one lock-free union-find over the whole lattice whose
+// roots are the minimum cell index of each component.  Each phase below walks
+// the lattice in 256-cell tiles, one cell per thread of a 256-thread block
+// (a tile lies in one domain), or a table with a thread-stride loop, so that
+// it runs both as a kernel of its own and inside the conversion kernel.
+
+__device__ inline bool is_fg(uint8_t f) { return ctype(f) == GAS || ctype(f) == IFC; }
+
+// Root of a; halves the path on the way (each cell is pointed at its
+// grandparent, still one of its ancestors, so the trees keep their roots).
+__device__ inline int find_root(int* L, int a, int cap, bool& ok) {
+    for (int it = 0; it < cap; ++it) {
+        const int p = L[a];
+        if (p == a) return a;
+        const int gp = L[p];
+        if (gp != p) L[a] = gp;
+        a = gp;
+    }
+    ok = false;
+    return a;
+}
+
+// Lock-free union: always hook the larger root under the smaller one, so the
+// final root of every component is its minimum cell index.
+__device__ inline bool unite(int* L, int a, int b, int cap) {
+    bool ok = true;
+    for (int it = 0; it < cap && ok; ++it) {
+        a = find_root(L, a, cap, ok);
+        b = find_root(L, b, cap, ok);
+        if (!ok) return false;
+        if (a == b) return true;
+        if (a < b) { const int tt = a; a = b; b = tt; }
+        const int old = atomicMin(&L[a], b);
+        if (old == a) return true;
+        a = old;
+    }
+    return false;
+}
+
+// Domain taking part in this labelling pass (every domain after
+// initialisation, else the domains whose step set the trigger).
+__device__ inline bool ccl_active(const StepArgs& A, const CclArgs& K, int d) {
+    return K.initial || A.trig[1 + d] != 0;
+}
+
+#define FSL_TILE_LOOP(A, tile) for (long long tile = blockIdx.x; tile < (A).stride / FSL_BLOCK; tile += gridDim.x)
+
+__device__ inline void ccl_init_phase(const StepArgs& A, const CclArgs& K) {
+    FSL_TILE_LOOP(A, t) {
+        const long long g = t * FSL_BLOCK + threadIdx.x;
+        if (ccl_active(A, K, block_dom(A, g))) K.lab[g] = is_fg(A.flag[g]) ? (int)g : -1;
+    }
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long h = i0; h < K.hcap; h += nth) {
+        K.hkeys[h] = ~0ull;
+        K.hvals[h] = 0;
+    }
+    for (long long sl = i0; sl < K.nslots_total; sl += nth) {
+        K.nvfx[sl] = 0; K.nvxfx[sl] = 0; K.nvsfx[sl] = 0; K.nncells[sl] = 0; K.nconstp[sl] = 0;
+        K.croot[sl] = -1;
+        K.vtot[sl] = 0;
+        K.minc[sl] = INT_MAX;
+    }
+    for (long long dd = i0; dd < A.ndom; dd += nth)
+        if (ccl_active(A, K, (int)dd)) K.nslot[dd] = 0;
+}
+
+__device__ inline void ccl_hook_phase(const StepArgs& A, const CclArgs& K) {
+    FSL_TILE_LOOP(A, t) {
+        const long long g = t * FSL_BLOCK + threadIdx.x;
+        const int d = block_dom(A, g);
+        if (!ccl_active(A, K, d) || !is_fg(A.flag[g])) continue;
+        const Dom D = get_dom(A, d);
+        const Cell c = make_cell(D, g);
+        // the nine directions 1, 3, ..., 17 cover each neighbour pair once
+        for (int a = 1; a < 19; a += 2) {
+            const long long h = c.at(cx(a), cy(a), cz(a));
+            if (is_fg(A.flag[h])) {
+                if (!unite(K.lab, (int)g, (int)h, K.max_iter)) {
+                    set_status(A.status, ST_CCL);
+                    break;
+                }
+            }
+        }
+    }
+}
+
+// Compress every cell onto its root; roots take a new bubble-table slot.
+__device__ inline void ccl_compress_phase(const StepArgs& A, const CclArgs& K) {
+    FSL_TILE_LOOP(A, t) {
+        const long long g = t * FSL_BLOCK + threadIdx.x;
+        const int d = block_dom(A, g);
+        if (!ccl_active(A, K, d) || !is_fg(A.flag[g])) continue;
+        bool ok = true;
+        const int r = find_root(K.lab, (int)g, K.max_iter, ok);
+        if (!ok) { set_status(A.status, ST_CCL); continue; }
+        K.lab[g] = r;
+        if (r == (int)g) {
+            const Dom D = get_dom(A, d);
+            const int k = atomicAdd(&K.nslot[d], 1);
+            if (k >= D.slot_cap) { set_status(A.status, ST_TABLE_FULL); K.aux[g] = -1; continue; }
+            K.aux[g] = D.slot_off + k;
+            K.croot[D.slot_off + k] = r;
+        }
+    }
+}
+
+__device__ inline void hash_add(const CclArgs& K, unsigned long long key, long long v, int* status) {
+    unsigned long long h = key * 0x9E3779B97F4A7C15ull;
+    long long pos = (long long)(h >> 20) & (K.hcap - 1);
+    for (long long probe = 0; probe < K.hcap; ++probe) {
+        const unsigned long long prev = atomicCAS(&K.hkeys[pos], ~0ull, key);
+        if (prev == ~0ull || prev == key) {
+            atomicAdd((unsigned long long*)&K.hvals[pos], (unsigned long long)v);
+            return;
+        }
+        pos = (pos + 1) & (K.hcap - 1);
+    }
+    set_status(status, ST_TABLE_FULL);
+}
+
+// New volumes and cell counts per component, overlap volumes V_{c,b} of new
+// component c with old bubble b, new ids.
+__device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
+    FSL_TILE_LOOP(A, t) {
+        const long long g = t * FSL_BLOCK + threadIdx.x;
+        const int d = block_dom(A, g);
+        if (!ccl_active(A, K, d)) continue;   // whole block: one domain
+        const uint8_t ty = ctype(A.flag[g]);
+        int c = -1;
+        long long term = 0;
+        if (ty == GAS || ty == IFC) {
+            const int r = K.lab[g];
+            c = K.aux[r];
+            term = volume_term(ty, A.phi[g]);
+        }
+        warp_add(K.nvfx, c, term);
+        warp_add(K.nncells, c, c >= 0 ? 1 : 0);
+        if (c < 0) continue;
+        if (!K.initial && A.id[g] >= 0) {
+            const int b = A.id[g];
+            const unsigned long long key = ((unsigned long long)(unsigned)c << 32) | (unsigned)b;
+            hash_add(K, key, term, A.status);
+            atomicAdd((unsigned long long*)&K.vtot[b], (unsigned long long)term);
+            atomicMin(&K.minc[b], K.lab[g]);
+            const Dom D = get_dom(A, d);
+            if (D.seed >= 0 && g - D.off == D.seed) {
+                const long long x = A.vxfx[b];
+                hash_add(K, key, x, A.status);
+                atomicAdd((unsigned long long*)&K.vtot[b], (unsigned long long)x);
+                K.nvxfx[c] = x;
+            }
+        }
+        A.id[g] = c;
+    }
+}
+
+// V*_c = sum over b of V*_b V_{c,b} / V_b, V*_b copied when c holds all of b
+// (Secs. 2.3.1, 2.3.2); a component touching a constant-pressure bubble
+// stays constant-pressure.
+__device__ inline void ccl_table_phase(const StepArgs& A, const CclArgs& K) {
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x; h < K.hcap; h += nth) {
+        const unsigned long long key = K.hkeys[h];
+        if (key == ~0ull) continue;
+        const int c = (int)(key >> 32);
+        const int b = (int)(key & 0xffffffffu);
+        const long long vcb = K.hvals[h];
+        const long long vt = K.vtot[b];
+        const long long vs = A.vsfx[b];
+        long long contrib;
+        if (vt == 0) contrib = (K.croot[c] == K.minc[b]) ? vs : 0;
+        else if (vcb == vt) contrib = vs;
+        else {
+            const double r = (double)vcb / (double)vt;
+            contrib = __double2ll_rn((double)vs * r);
+        }
+        atomicAdd((unsigned long long*)&K.nvsfx[c], (unsigned long long)contrib);
+        if (A.constp[b]) K.nconstp[c] = 1;
+    }
+}
+
+__device__ inline void ccl_install_phase(const StepArgs& A, const CclArgs& K) {
+    if (!K.initial && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)K.runs, 1ull);
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < K.nslots_total; sl += nth) {
+        const int d = K.slot_dom[sl];
+        if (!ccl_active(A, K, d)) continue;   // untouched domains keep their table
+        const Dom D = get_dom(A, d);
+        const int k = (int)(sl - D.slot_off);
+        if (k < K.nslot[d]) {
+            A.vfx[sl] = K.nvfx[sl];
+            A.vxfx[sl] = K.nvxfx[sl];
+            K.vsfx[sl] = K.initial ? K.nvfx[sl] + K.nvxfx[sl] : K.nvsfx[sl];
+            A.ncells[sl] = K.nncells[sl];
+            K.constp[sl] = K.nconstp[sl];
+        } else {
+            A.vfx[sl] = 0; A.vxfx[sl] = 0; K.vsfx[sl] = 0; A.ncells[sl] = 0; K.constp[sl] = 0;
+        }
+    }
+}
+
+// Barrier over all blocks of a cooperative launch (all of them resident).  The
+// last block to arrive resets the count and advances the generation; the others
+// wait for the generation to move, at most FSL_BARRIER_SPINS polls, after which
+// they record ST_SYNC and report failure (the caller returns).  The fences make
+// every write before the barrier visible to every read after it.
+#define FSL_BARRIER_SPINS (1 << 22)
+__device__ inline bool grid_barrier(const StepArgs& A) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* count = A.bar;
+        unsigned* gen = A.bar + 1;
+        unsigned g0;
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g0) : "l"(gen) : "memory");
+        __threadfence();
+        ok = 1;
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned gnow = g0;
+            int it = 0;
+            do {
+                __nanosleep(64);
+                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(gnow) : "l"(gen) : "memory");
+            } while (gnow == g0 && ++it < FSL_BARRIER_SPINS);
+            if (gnow == g0) {
+                set_status(A.status, ST_SYNC);
+                ok = 0;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Conversion (Sec. 2.2) in one cooperative launch: phases A+B, C and D
+// separated by grid barriers, then, when phase C set a merge / split trigger,
+// the labelling of the triggered domains (Secs. 2.3.1, 2.3.2).
+template <typename T>
+__global__ void __launch_bounds__(FSL_CONV_THREADS) k_convert(StepArgs A, CclArgs K) {
+    __shared__ unsigned adj[27];
+    if (threadIdx.x < 27) adj[threadIdx.x] = cube_adj18(threadIdx.x);
+    if (blockIdx.x == 0) {
+        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
+        if (threadIdx.x == 0) *A.icount_next = 0;
+    }
+    convert_ab_phase<T>(A);
+    if (!grid_barrier(A)) return;
+    convert_c_phase(A, adj);
+    if (!grid_barrier(A)) return;
+    const bool relabel = *(volatile int*)A.trig != 0;   // final after phase C
+    convert_d_phase(A);
+    if (!relabel) return;
+    if (!grid_barrier(A)) return;
+    ccl_init_phase(A, K);
+    if (!grid_barrier(A)) return;
+    ccl_hook_phase(A, K);
+    if (!grid_barrier(A)) return;
+    ccl_compress_phase(A, K);
+    if (!grid_barrier(A)) return;
+    ccl_pairs_phase(A, K);
+    if (!grid_barrier(A)) return;
+    ccl_table_phase(A, K);
+    if (!grid_barrier(A)) return;
+    ccl_install_phase(A, K);
+}
+
 // Initial state: validate the closed interface layer, f = f_eq(rho, u),
 // m = phi rho on interface cells (Eq. 9).
 template <typename T>
@@ -1044,7 +1710,8 @@ __global__ void k_export_pdf(const T* f, long long S, long long off, int n, doub
 template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, cudaStream_t s,
                                          cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,
                                          cudaEvent_t ei);
-template <typename T> void launch_convert_ab(const StepArgs& A, long long nblocks, cudaStream_t s);
+template <typename T> cudaError_t launch_convert(const StepArgs& A, const CclArgs& K, int nblocks, cudaStream_t s);
+template <typename T> int convert_blocks_per_sm();
 template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
                                              const double* rho, const double* u, cudaStream_t s);
 template <typename T> void launch_export_pdf(const void* f, long long S, long long off, int n, double* pdf,
@@ -1058,15 +1725,29 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         /* el / ei (optional) mark the end of each kernel */                                                \
         cudaEventRecord(fork, s);                                                                            \
         cudaStreamWaitEvent(s2, fork, 0);                                                                    \
-        k_stream_interface<T><<<(unsigned)(2 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                           \
+        k_stream_interface<T><<<(unsigned)(4 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                           \
         if (ei) cudaEventRecord(ei, s2);                                                                     \
         k_stream_liquid<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                           \
         if (el) cudaEventRecord(el, s);                                                                      \
         cudaEventRecord(join, s2);                                                                           \
         cudaStreamWaitEvent(s, join, 0);                                                                     \
     }                                                                                                        \
-    template <> void launch_convert_ab<T>(const StepArgs& A, long long nb, cudaStream_t s) {                 \
-        k_convert_ab<T><<<(unsigned)nb, 128, 0, s>>>(A);                                                    \
+    template <> cudaError_t launch_convert<T>(const StepArgs& A, const CclArgs& K, int nb, cudaStream_t s) {\
+        cudaLaunchConfig_t cfg = {};                                                                         \
+        cfg.gridDim = dim3((unsigned)nb);                                                                    \
+        cfg.blockDim = dim3(FSL_CONV_THREADS);                                                               \
+        cfg.stream = s;                                                                                      \
+        cudaLaunchAttribute at[1];                                                                           \
+        at[0].id = cudaLaunchAttributeCooperative;                                                           \
+        at[0].val.cooperative = 1;                                                                           \
+        cfg.attrs = at;                                                                                      \
+        cfg.numAttrs = 1;                                                                                    \
+        return cudaLaunchKernelEx(&cfg, k_convert<T>, A, K);                                                 \
+    }                                                                                                        \
+    template <> int convert_blocks_per_sm<T>() {                                                             \
+        int nb = 0;                                                                                          \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_convert<T>, FSL_CONV_THREADS, 0);               \
+        return nb;                                                                                           \
     }                                                                                                        \
     template <> void launch_init_state<T>(const StepArgs& A, int d, int n, const uint8_t* fl,                \
                                           const double* fill, const double* rho, const double* u,            \

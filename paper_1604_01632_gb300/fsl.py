@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libfsl.so")
 
 FSL_OK = 0
 STATUS_NAMES = {0: "FSL_OK", -1: "FSL_ERR_ARG", -2: "FSL_ERR_GEOMETRY", -3: "FSL_ERR_OOM", -4: "FSL_ERR_NAN",
-                -5: "FSL_ERR_CCL_NOT_CONVERGED", -6: "FSL_ERR_TABLE_FULL", -7: "FSL_ERR_CUDA"}
+                -5: "FSL_ERR_CCL_NOT_CONVERGED", -6: "FSL_ERR_TABLE_FULL", -7: "FSL_ERR_CUDA",
+                -8: "FSL_ERR_SYNC"}
 PRECISIONS = {"fp64": 0, "fp32": 1, "f16s": 2, "bf16s": 3}
 FIELD_BITS = {"flags": 1, "fill": 2, "mass": 4, "id": 8, "rho": 16, "u": 32, "pdf": 64}
 FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.float64, 1), "id": (np.int64, 1),
@@ -273,10 +274,9 @@ class Simulation:
         self._check(self.L.fsl_set_graphs(self._h, 1 if on else 0))
 
     def phase_ms(self) -> Dict[str, float]:
-        out = (ctypes.c_double * 7)()
+        out = (ctypes.c_double * 4)()
         self._check(self.L.fsl_phase_ms(self._h, out))
-        return dict(zip(("stream_collide", "liquid_end", "interface_end", "phase_ab", "excess", "update",
-                         "labelling"), list(out)))
+        return dict(zip(("stream_collide", "liquid_end", "interface_end", "conversion"), list(out)))
 
     def stream_collide_ms(self) -> float:
         return float(self.L.fsl_stream_collide_ms(self._h))
