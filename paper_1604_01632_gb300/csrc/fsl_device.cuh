@@ -151,6 +151,15 @@ struct StepArgs {
 // them from the kernel parameters, a batch from its device tables.
 __device__ inline Dom get_dom(const StepArgs& A, int d) { return A.ndom == 1 ? A.d0 : A.doms[d]; }
 __device__ inline int block_dom(const StepArgs& A, long long g) { return A.ndom == 1 ? 0 : A.blk_dom[g / FSL_BLOCK]; }
+// The same for the hot kernels, which exist once for a single domain (ONE:
+// the descriptor is read straight from the kernel parameters) and once for a
+// batch (read from the device table), so that no thread copies a descriptor
+// chosen at run time.
+template <bool ONE>
+__device__ inline const Dom& dom_at(const StepArgs& A, long long g) {
+    if constexpr (ONE) return A.d0;
+    else return A.doms[A.blk_dom[g / FSL_BLOCK]];
+}
 
 // D3Q19 velocities; constexpr so that unrolled loops fold them into offsets
 __host__ __device__ constexpr int cx(int a) {
@@ -510,13 +519,13 @@ __device__ inline Pull make_pull(const Dom& D, long long g) {
 // K1L: stream with half-way bounce-back (Eq. 7) and collide (Eq. 6) for
 // liquid cells.  Only cells flagged as touching a wall read the types of
 // their neighbours; a liquid cell never touches gas (closed interface layer).
-template <typename T>
-__global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 5) k_stream_liquid(StepArgs A) {
     using C = typename Form<T>::C;
     const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     const uint8_t f = A.flag[g];
     if (ctype(f) != LIQ) return;
-    const Dom D = get_dom(A, block_dom(A, g));
+    const Dom& D = dom_at<ONE>(A, g);
     const Par<C> R = par_of<C>(D);
     const Pull P = make_pull(D, g);
     const unsigned gi = (unsigned)g;
@@ -532,19 +541,15 @@ __global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
             for (int a = 1; a < 19; ++a)
                 d[a] = Form<T>::ld_dev(src + a * S + (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]));
         } else {
+            // all neighbour types first, then every load with its address
+            // chosen without a branch (two memory latencies, not eighteen)
 #pragma unroll
             for (int a = 1; a < 19; ++a) {
-                const int ab = opp(a);
                 const unsigned y = (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]);
-                const uint8_t ty = ctype(A.flag[y]);
-                if (ty == OBS) {
-                    d[a] = Form<T>::ld_dev(src + ab * S + gi);   // w_a = w_abar
-                } else if (ty == LID) {
-                    const float cuw = cdot<float>(a, R.lid[0], R.lid[1], R.lid[2]);
-                    d[a] = Form<T>::ld_dev(src + ab * S + gi) + (6.f * weightc<float>(a)) * cuw;
-                } else {
-                    d[a] = Form<T>::ld_dev(src + a * S + y);
-                }
+                const uint8_t t = ctype(A.flag[y]);
+                // bounce-back reads the cell's own opposite PDF (w_a = w_abar)
+                const float v = Form<T>::ld_dev(src + ((t == OBS || t == LID) ? opp(a) * S + gi : a * S + y));
+                d[a] = t == LID ? v + (6.f * weightc<float>(a)) * cdot<float>(a, R.lid[0], R.lid[1], R.lid[2]) : v;
             }
         }
         float dout[19];
@@ -563,19 +568,23 @@ __global__ void __launch_bounds__(FSL_BLOCK, 5) k_stream_liquid(StepArgs A) {
             for (int a = 1; a < 19; ++a)
                 fin[a] = Form<T>::ld(src + a * S + (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]), a);
         } else {
+            unsigned bm = 0, lm = 0;   // links from an obstacle / the lid
 #pragma unroll
             for (int a = 1; a < 19; ++a) {
-                const int ab = opp(a);
+                const uint8_t t = ctype(A.flag[(unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)])]);
+                bm |= (unsigned)(t == OBS || t == LID) << a;
+                lm |= (unsigned)(t == LID) << a;
+            }
+#pragma unroll
+            for (int a = 1; a < 19; ++a) {
                 const unsigned y = (unsigned)(gi + P.ox[1 - cx(a)] + P.oy[1 - cy(a)] + P.oz[1 - cz(a)]);
-                const uint8_t ty = ctype(A.flag[y]);
-                if (ty == OBS) {
-                    fin[a] = Form<T>::ld(src + ab * S + gi, ab);
-                } else if (ty == LID) {
-                    C cuw = cdot<C>(a, R.lid[0], R.lid[1], R.lid[2]);
-                    fin[a] = Form<T>::ld(src + ab * S + gi, ab) + ((C)6 * weightc<C>(a)) * cuw;
-                } else {
-                    fin[a] = Form<T>::ld(src + a * S + y, a);
-                }
+                // w_a = w_abar, so the stored form of direction abar reads the same
+                fin[a] = Form<T>::ld(src + (((bm >> a) & 1u) ? opp(a) * S + gi : a * S + y), a);
+            }
+            if (lm) {
+#pragma unroll
+                for (int a = 1; a < 19; ++a)
+                    if ((lm >> a) & 1u) fin[a] = fin[a] + ((C)6 * weightc<C>(a)) * cdot<C>(a, R.lid[0], R.lid[1], R.lid[2]);
             }
         }
         C fout[19];
@@ -731,7 +740,7 @@ struct IfStage {
 
 __device__ inline int ph_index(int dx, int dy, int dz) { return (dx + 2) + 5 * (dy + 2) + 25 * (dz + 2); }
 
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : 6) k_stream_interface(StepArgs A) {
     using C = typename Form<T>::C;
     constexpr int N = IfCells<T>::n;
@@ -768,7 +777,7 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : 6) k_stre
         // about two memory latencies (the list entry, then everything else)
         if (i0 + c < cnt) {
             const long long g = A.ilist[i0 + c];
-            const Dom D = get_dom(A, block_dom(A, g));
+            const Dom& D = dom_at<ONE>(A, g);
             const Stencil st = make_stencil(D, g);
             constexpr int NR = (25 + TPC - 1) / TPC;   // box rows of this thread
             constexpr int ND = (19 + TPC - 1) / TPC;   // directions of this thread
@@ -889,7 +898,7 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : 6) k_stre
             uint8_t mk = MK_NONE;
             if (act) {
                 g = sh.g[c];
-                const Dom D = get_dom(A, block_dom(A, g));
+                const Dom& D = dom_at<ONE>(A, g);
                 const Par<C> R = par_of<C>(D);
                 C rs, jsx, jsy, jsz;
                 moments<C>(sh.fs[c], rs, jsx, jsy, jsz);
@@ -933,7 +942,7 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : 6) k_stre
             }
             __syncwarp();
             if (act) {
-                const Dom D = get_dom(A, block_dom(A, g));
+                const Dom& D = dom_at<ONE>(A, g);
                 const Par<C> R = par_of<C>(D);
                 C rho;
                 if (D.has_force) {
@@ -1725,9 +1734,15 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         /* el / ei (optional) mark the end of each kernel */                                                \
         cudaEventRecord(fork, s);                                                                            \
         cudaStreamWaitEvent(s2, fork, 0);                                                                    \
-        k_stream_interface<T><<<(unsigned)(4 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                           \
+        if (A.ndom == 1)                                                                                     \
+            k_stream_interface<T, true><<<(unsigned)(4 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                  \
+        else                                                                                                 \
+            k_stream_interface<T, false><<<(unsigned)(4 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                 \
         if (ei) cudaEventRecord(ei, s2);                                                                     \
-        k_stream_liquid<T><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                           \
+        if (A.ndom == 1)                                                                                     \
+            k_stream_liquid<T, true><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                  \
+        else                                                                                                 \
+            k_stream_liquid<T, false><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                 \
         if (el) cudaEventRecord(el, s);                                                                      \
         cudaEventRecord(join, s2);                                                                           \
         cudaStreamWaitEvent(s, join, 0);                                                                     \
