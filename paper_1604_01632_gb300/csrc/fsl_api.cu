@@ -452,12 +452,11 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms > 0) h->ifblocks = 2 * sms;
-        // the cooperative conversion kernel: every block resident, at most
-        // two per SM (its phases are short lists; fewer blocks make cheaper
-        // barriers)
+        // the cooperative conversion kernel: one block per SM, all resident
+        // (its phases walk short lists; fewer blocks make cheaper barriers)
         const int per_sm = conv_blocks_per_sm(precision);
         if (per_sm < 1) e = cudaErrorInvalidConfiguration;
-        h->convblocks = std::max(1, sms) * std::min(2, std::max(1, per_sm));
+        h->convblocks = std::max(1, sms);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);

@@ -1131,10 +1131,67 @@ __device__ inline void warp_add(long long* base, int key, long long v) {
     }
 }
 
+// Block-wide forms of warp_add and list_append: one global atomic per block
+// and run of equal keys instead of one per warp.  Every thread of the block
+// must call (the caller's loop is block-uniform); scratch is shared memory.
+struct BlockScratch {
+    long long sum[32];
+    int key[32];
+    int cnt[32];
+    int base[32];
+};
+__device__ inline void block_add(long long* base, int key, long long v, BlockScratch& sc) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int k0 = __shfl_sync(full, key, 0);
+    const bool uni = __all_sync(full, key == k0);
+    if (uni) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
+        if (lane == 0) { sc.key[w] = k0; sc.sum[w] = v; }
+    } else {
+        if (key >= 0 && v != 0) atomicAdd((unsigned long long*)&base[key], (unsigned long long)v);
+        if (lane == 0) sc.key[w] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int kr = -1;
+        long long acc = 0;
+        for (int i = 0; i < nw; ++i) {
+            const int k = sc.key[i];
+            if (k < 0) continue;
+            if (k != kr) {
+                if (kr >= 0 && acc != 0) atomicAdd((unsigned long long*)&base[kr], (unsigned long long)acc);
+                kr = k;
+                acc = 0;
+            }
+            acc += sc.sum[i];
+        }
+        if (kr >= 0 && acc != 0) atomicAdd((unsigned long long*)&base[kr], (unsigned long long)acc);
+    }
+    __syncthreads();
+}
+__device__ inline void block_list_append(int* list, int* count, bool pred, int v, BlockScratch& sc) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const unsigned m = __ballot_sync(full, pred);
+    if (lane == 0) sc.cnt[w] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int i = 0; i < nw; ++i) { sc.base[i] = tot; tot += sc.cnt[i]; }
+        const int b = tot > 0 ? atomicAdd(count, tot) : 0;
+        for (int i = 0; i < nw; ++i) sc.base[i] += b;
+    }
+    __syncthreads();
+    if (pred) list[sc.base[w] + __popc(m & ((1u << lane) - 1u))] = v;
+    __syncthreads();
+}
+
 // 3x3x3 cube around a cell, bit k = (dx+1) + 3 (dy+1) + 9 (dz+1); bit 13 is the
 // centre.  Face or edge neighbours of cube cell k inside the cube, the centre
 // left out (a walk must not pass through the removed cell).
-__device__ inline unsigned cube_adj18(int k) {
+__host__ __device__ constexpr unsigned cube_adj18(int k) {
     const int kx = k % 3 - 1, ky = (k / 3) % 3 - 1, kz = k / 9 - 1;
     unsigned a = 0;
     for (int j = 0; j < 27; ++j) {
@@ -1145,6 +1202,13 @@ __device__ inline unsigned cube_adj18(int k) {
     }
     return a & ~(1u << 13);
 }
+// the table, folded at compile time
+__constant__ static const unsigned c_cube_adj18[27] = {
+    cube_adj18(0),  cube_adj18(1),  cube_adj18(2),  cube_adj18(3),  cube_adj18(4),  cube_adj18(5),  cube_adj18(6),
+    cube_adj18(7),  cube_adj18(8),  cube_adj18(9),  cube_adj18(10), cube_adj18(11), cube_adj18(12), cube_adj18(13),
+    cube_adj18(14), cube_adj18(15), cube_adj18(16), cube_adj18(17), cube_adj18(18), cube_adj18(19), cube_adj18(20),
+    cube_adj18(21), cube_adj18(22), cube_adj18(23), cube_adj18(24), cube_adj18(25), cube_adj18(26)};
+
 // bits of the 18 face / edge neighbours of the centre
 __host__ __device__ constexpr unsigned cube_mask18() {
     unsigned m = 0;
@@ -1157,9 +1221,8 @@ __host__ __device__ constexpr unsigned cube_mask18() {
 
 // Local test that removing the filled cell at the centre of the cube cannot
 // split its bubble: the gas/interface cells among its 18 neighbours must stay
-// connected inside the cube (18-connectivity) without the centre.  adj is
-// cube_adj18 tabulated (shared memory).
-__device__ inline bool removal_is_local(unsigned fg, const unsigned* adj) {
+// connected inside the cube (18-connectivity) without the centre.
+__device__ inline bool removal_is_local(unsigned fg) {
     constexpr unsigned kMask18 = cube_mask18();
     const unsigned targets = fg & kMask18;
     if (targets == 0) return true;
@@ -1170,7 +1233,7 @@ __device__ inline bool removal_is_local(unsigned fg, const unsigned* adj) {
         while (r) {
             const int k = __ffs(r) - 1;
             r &= r - 1;
-            grow |= adj[k];
+            grow |= c_cube_adj18[k];
         }
         grow &= fg;
         if (grow == reach) break;
@@ -1185,7 +1248,7 @@ __device__ inline bool removal_is_local(unsigned fg, const unsigned* adj) {
 // triggers.  Taking the filled cells away one at a time in index order, each
 // removal must pass the local test with the lower-index filled cells already
 // gone and the higher-index ones still present, or the labelling runs.
-__device__ inline void convert_c_phase(const StepArgs& A, const unsigned* adj) {
+__device__ inline void convert_c_phase(const StepArgs& A) {
     const int nm = *A.mcount, nl = *A.lcount;
     const int total = nm + nl;
     const int step = *A.stepno;
@@ -1222,7 +1285,7 @@ __device__ inline void convert_c_phase(const StepArgs& A, const unsigned* adj) {
                             if (ntz == GAS || ntz == IFC || later_filled)
                                 fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
                         }
-                if (!removal_is_local(fgm, adj)) {
+                if (!removal_is_local(fgm)) {
                     atomicExch(&A.trig[1 + d], 1);
                     atomicExch(A.trig, 1);
                 }
@@ -1251,7 +1314,7 @@ __device__ inline void convert_c_phase(const StepArgs& A, const unsigned* adj) {
 // pool share, phi = m / rho (Eq. 9); converted cells take their new type;
 // bubble volumes change by exact fixed-point differences; the interface list
 // of the next step; reservoir drain; the graph condition of the labelling.
-__device__ inline void convert_d_phase(const StepArgs& A) {
+__device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
     const int ni = *A.icount, ng = *A.gcount, nl = *A.lcount;
     const int total = ni + ng + nl;
     const int step = *A.stepno;
@@ -1306,7 +1369,7 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
                         if (A.cstep[z] == step) sm = sm + A.exs[z];
                     }
                 }
-                if (nI > 0) {
+                if (nI > 0 && pool != 0) {
                     const double share = ((double)pool * 9.094947017729282379150390625e-13) / (double)nI;
                     sm = sm + share;
                 }
@@ -1323,10 +1386,10 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
                 keep = true;
             }
         }
-        warp_add(A.vfx, dv != 0 ? key : -1, dv);
-        warp_add(A.ncells, ckey, dc);
-        warp_add(A.icnt, keep ? d : -1, 1);
-        list_append(A.ilist_next, A.icount_next, keep, (int)g);
+        block_add(A.vfx, dv != 0 ? key : -1, dv, sc);
+        block_add(A.ncells, ckey, dc, sc);
+        block_add(A.icnt, keep ? d : -1, 1, sc);
+        block_list_append(A.ilist_next, A.icount_next, keep, (int)g, sc);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // reservoir drain of every domain whose seed cell is still gas or
@@ -1580,8 +1643,10 @@ __device__ inline void ccl_install_phase(const StepArgs& A, const CclArgs& K) {
 // Barrier over all blocks of a cooperative launch (all of them resident).  The
 // last block to arrive resets the count and advances the generation; the others
 // wait for the generation to move, at most FSL_BARRIER_SPINS polls, after which
-// they record ST_SYNC and report failure (the caller returns).  The fences make
-// every write before the barrier visible to every read after it.
+// they record ST_SYNC and report failure (the caller returns).  The arrival is
+// an acquire-release atomic and the release of the generation and its polls
+// are release / acquire at GPU scope, so every write before the barrier is
+// visible to every read after it.
 #define FSL_BARRIER_SPINS (1 << 22)
 __device__ inline bool grid_barrier(const StepArgs& A) {
     __shared__ int ok;
@@ -1589,19 +1654,18 @@ __device__ inline bool grid_barrier(const StepArgs& A) {
     if (threadIdx.x == 0) {
         unsigned* count = A.bar;
         unsigned* gen = A.bar + 1;
-        unsigned g0;
-        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g0) : "l"(gen) : "memory");
-        __threadfence();
+        unsigned g0, old, gnow;
         ok = 1;
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            *count = 0;
-            __threadfence();
-            atomicAdd(gen, 1u);
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g0) : "l"(gen) : "memory");
+        // arrive: release this block's writes (ordered before by the block
+        // barrier), acquire those of the blocks that arrived before
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+        if (old == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(count) : "memory");
+            asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(gen) : "memory");
         } else {
-            unsigned gnow = g0;
             int it = 0;
             do {
-                __nanosleep(64);
                 asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(gnow) : "l"(gen) : "memory");
             } while (gnow == g0 && ++it < FSL_BARRIER_SPINS);
             if (gnow == g0) {
@@ -1609,7 +1673,6 @@ __device__ inline bool grid_barrier(const StepArgs& A) {
                 ok = 0;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
@@ -1620,18 +1683,17 @@ __device__ inline bool grid_barrier(const StepArgs& A) {
 // the labelling of the triggered domains (Secs. 2.3.1, 2.3.2).
 template <typename T>
 __global__ void __launch_bounds__(FSL_CONV_THREADS) k_convert(StepArgs A, CclArgs K) {
-    __shared__ unsigned adj[27];
-    if (threadIdx.x < 27) adj[threadIdx.x] = cube_adj18(threadIdx.x);
+    __shared__ BlockScratch sc;
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
         if (threadIdx.x == 0) *A.icount_next = 0;
     }
     convert_ab_phase<T>(A);
     if (!grid_barrier(A)) return;
-    convert_c_phase(A, adj);
+    convert_c_phase(A);
     if (!grid_barrier(A)) return;
     const bool relabel = *(volatile int*)A.trig != 0;   // final after phase C
-    convert_d_phase(A);
+    convert_d_phase(A, sc);
     if (!relabel) return;
     if (!grid_barrier(A)) return;
     ccl_init_phase(A, K);
@@ -1735,9 +1797,9 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         cudaEventRecord(fork, s);                                                                            \
         cudaStreamWaitEvent(s2, fork, 0);                                                                    \
         if (A.ndom == 1)                                                                                     \
-            k_stream_interface<T, true><<<(unsigned)(4 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                  \
+            k_stream_interface<T, true><<<(unsigned)(2 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                  \
         else                                                                                                 \
-            k_stream_interface<T, false><<<(unsigned)(4 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                 \
+            k_stream_interface<T, false><<<(unsigned)(2 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                 \
         if (ei) cudaEventRecord(ei, s2);                                                                     \
         if (A.ndom == 1)                                                                                     \
             k_stream_liquid<T, true><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                  \
