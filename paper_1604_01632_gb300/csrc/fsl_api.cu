@@ -452,11 +452,12 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms > 0) h->ifblocks = 2 * sms;
-        // the cooperative conversion kernel: one block per SM, all resident
-        // (its phases walk short lists; fewer blocks make cheaper barriers)
+        // the cooperative conversion kernel: all blocks resident; as many as
+        // fit, because on trigger steps its labelling phases sweep the whole
+        // lattice (a barrier over more blocks costs a little more)
         const int per_sm = conv_blocks_per_sm(precision);
         if (per_sm < 1) e = cudaErrorInvalidConfiguration;
-        h->convblocks = std::max(1, sms);
+        h->convblocks = std::max(1, sms) * std::max(1, per_sm);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);

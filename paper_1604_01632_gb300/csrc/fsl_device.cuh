@@ -718,8 +718,14 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 // (Eq. 6), then the filled / emptied marks.  The FP32-collide forms do all of
 // this in FP32 except the cell mass, which accumulates in FP64.
 #define FSL_IF_THREADS 128   // 16 cells per pass, eight threads per cell
+#ifndef FSL_IF_CELLS
+#define FSL_IF_CELLS 16   // cells per pass of an FP32-collide interface block
+#endif
+#ifndef FSL_IF_MINB
+#define FSL_IF_MINB 6     // resident interface blocks per SM (register bound)
+#endif
 template <typename T> struct IfCells {
-    static constexpr int n = 16;
+    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : FSL_IF_CELLS;
 };
 template <typename T>
 struct IfStage {
@@ -741,7 +747,7 @@ struct IfStage {
 __device__ inline int ph_index(int dx, int dy, int dz) { return (dx + 2) + 5 * (dy + 2) + 25 * (dz + 2); }
 
 template <typename T, bool ONE>
-__global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : 6) k_stream_interface(StepArgs A) {
+__global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MINB) k_stream_interface(StepArgs A) {
     using C = typename Form<T>::C;
     constexpr int N = IfCells<T>::n;
     constexpr int TPC = FSL_IF_THREADS / N;   // threads per cell
