@@ -101,7 +101,10 @@ enum {
 
 /* Create a handle for n_domains independent domains; params[d] describes
  * domain d.  cuda_stream: the cudaStream_t every call enqueues on (NULL =
- * legacy default stream).  Allocates all device state. */
+ * legacy default stream).  Allocates all device state.  FSL_ERR_ARG when a
+ * parameter is out of range or the domains, each padded to a multiple of 256
+ * cells, hold more than 226,050,910 cells together (19 PDFs per cell must be
+ * addressable with 32-bit offsets). */
 fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t precision,
                       void* cuda_stream, fsl_domain** out);
 

@@ -427,7 +427,8 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         off += padded;
         soff += cap;
     }
-    if (off >= (1LL << 31) || soff >= (1LL << 31)) { delete h; return FSL_ERR_ARG; }
+    // cell numbers are 31-bit and the kernels address PDFs with 32-bit offsets
+    if (off >= (1LL << 31) || 19 * off >= (1LL << 32) || soff >= (1LL << 31)) { delete h; return FSL_ERR_ARG; }
     h->stride = off;
     h->nblocks = off / FSL_BLOCK;
     h->nslots = soff;

@@ -605,13 +605,15 @@ __device__ inline int wrap2(int v, int n) {   // v in [-2, n+1]
     return v;
 }
 
+// (32-bit cell numbers: the library keeps every cell number, and 19 times the
+// lattice size, below 2^32)
 struct Stencil {
-    int x, y, z, nx, ny, nz;
-    long long off, g;
+    int x, y, z, nx, ny, nz, sz;
+    unsigned off, g;
     bool inner;   // two cells from every face: no wrap needed
-    __device__ inline long long at(int dx, int dy, int dz) const {
-        if (inner) return g + dx + (long long)nx * (dy + (long long)ny * dz);
-        return off + wrap2(x + dx, nx) + (long long)nx * (wrap2(y + dy, ny) + (long long)ny * wrap2(z + dz, nz));
+    __device__ inline unsigned at(int dx, int dy, int dz) const {
+        if (inner) return g + (unsigned)(dx + nx * dy + sz * dz);
+        return off + (unsigned)(wrap2(x + dx, nx) + nx * wrap2(y + dy, ny) + sz * wrap2(z + dz, nz));
     }
 };
 
@@ -619,8 +621,9 @@ __device__ inline Stencil make_stencil(const Dom& D, long long g) {
     Stencil s;
     local_xyz(D, (int)(g - D.off), s.x, s.y, s.z);
     s.nx = D.nx; s.ny = D.ny; s.nz = D.nz;
-    s.off = D.off;
-    s.g = g;
+    s.sz = D.nx * D.ny;
+    s.off = (unsigned)D.off;
+    s.g = (unsigned)g;
     s.inner = s.x >= 2 && s.x < D.nx - 2 && s.y >= 2 && s.y < D.ny - 2 && s.z >= 2 && s.z < D.nz - 2;
     return s;
 }
@@ -767,7 +770,7 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
         }
     }
     const int cnt = *A.icount;
-    const long long S = A.stride;
+    const unsigned S = (unsigned)A.stride;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
     // fill levels in the arithmetic type (FP32 copies for the FP32-collide forms)
@@ -795,7 +798,7 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
                 if (r < 25) {
                     const int dy = r % 5 - 2, dz = r / 5 - 2;
                     if (xin) {
-                        const long long b = st.at(0, dy, dz);
+                        const unsigned b = st.at(0, dy, dz);
 #pragma unroll
                         for (int e = 0; e < 5; ++e) rowv[k][e] = phtc[b + (e - 2)];
                     } else {
@@ -810,16 +813,16 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
             for (int k = 0; k < ND; ++k) {
                 const int a = q + TPC * k;
                 if (a < 19) {
-                    fsv[k] = Form<T>::ld(src + (long long)a * S + g, a);
+                    fsv[k] = Form<T>::ld(src + ((unsigned)a * S + (unsigned)g), a);
                     if (a > 0) {
                         const int ab = opp(a);
                         const int ax = rcx(a), ay = rcy(a), az = rcz(a);
-                        const long long y = st.at(-ax, -ay, -az);
-                        const long long z = st.at(ax, ay, az);
+                        const unsigned y = st.at(-ax, -ay, -az);
+                        const unsigned z = st.at(ax, ay, az);
                         tyv[k] = ctype(A.flag[y]);
-                        fyv[k] = Form<T>::ld(src + (long long)a * S + y, a);
+                        fyv[k] = Form<T>::ld(src + ((unsigned)a * S + y), a);
                         tzv[k] = ctype(A.flag[z]);
-                        fzv[k] = Form<T>::ld(src + (long long)ab * S + z, ab);
+                        fzv[k] = Form<T>::ld(src + ((unsigned)ab * S + z), ab);
                         phz[k] = phic[z];
                     }
                 }
@@ -955,12 +958,12 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
                     const CollidePrep<C> P = collide_prep<C, true>(sh.fin[c], R.g[0], R.g[1], R.g[2]);
                     rho = P.rho;
                     for (int a = q; a < 19; a += TPC)
-                        Form<T>::st(dst + (long long)a * S + g, a, collide_out<C, true>(a, sh.fin[c], P, R.omp, R.omm));
+                        Form<T>::st(dst + ((unsigned)a * S + (unsigned)g), a, collide_out<C, true>(a, sh.fin[c], P, R.omp, R.omm));
                 } else {
                     const CollidePrep<C> P = collide_prep<C, false>(sh.fin[c], (C)0, (C)0, (C)0);
                     rho = P.rho;
                     for (int a = q; a < 19; a += TPC)
-                        Form<T>::st(dst + (long long)a * S + g, a, collide_out<C, false>(a, sh.fin[c], P, R.omp, R.omm));
+                        Form<T>::st(dst + ((unsigned)a * S + (unsigned)g), a, collide_out<C, false>(a, sh.fin[c], P, R.omp, R.omm));
                 }
                 if (q == 0) {
                     if (!(rho == rho)) set_status(A.status, ST_NAN);
