@@ -219,18 +219,34 @@ def run_gpu(args, rank: int, world: int):
         phases = {k: round(v / 20 * 1e3, 2) for k, v in ph.phase_ms().items()}
         ph.close()
 
+    def measure(sim, cells, prec, K):
+        """Uninstrumented step time, then the stream-collide pair by events."""
+        vms, _, _, vc, _ = timed_steps(sim, K, args.warmup, timing=False)
+        _, vk1, _, _, _ = timed_steps(sim, K, args.warmup, timing=True)
+        vb = algorithmic_bytes(vc, BYTES[prec])
+        return {"mlups": round(cells * K / (vms * 1e-3) / 1e6, 1), "ms_per_step": round(vms / K, 5),
+                "stream_collide_gbs": round(vb / (vk1 / K * 1e-3) / 1e9, 1),
+                "stream_collide_frac": round(vb / (vk1 / K * 1e-3) / 1e9 / peak, 3)}
+
     variants = {}
     if not args.no_variants:
         for prec in ("fp32", "bf16s", "fp64"):
             if prec == args.precision:
                 continue
             v = make(prec)
-            vms, vk1, _, vc, _ = timed_steps(v, max(5, args.steps // 2), args.warmup)
-            kk = max(5, args.steps // 2)
-            vb = algorithmic_bytes(vc, BYTES[prec])
-            variants[prec] = {"mlups": round(n * kk / (vms * 1e-3) / 1e6, 1),
-                              "stream_collide_gbs": round(vb / (vk1 / kk * 1e-3) / 1e9, 1),
-                              "stream_collide_frac": round(vb / (vk1 / kk * 1e-3) / 1e9 / peak, 3)}
+            variants[prec] = measure(v, n, prec, max(5, args.steps // 2))
+            v.close()
+
+    # the same path on larger lattices of the paper's shapes (one domain each)
+    at_scale = {}
+    if not args.no_scale and world == 1:
+        from paper_1604_01632_gb300 import scenarios as S
+        for key, (sc2, desc) in (("gas_thread_large", workload("gas_thread_large")),
+                                 ("orifice", (S.orifice(), "orifice 128x128x256 TRT g=1e-5 sigma=2e-3 hole r=6"))):
+            v = fsl.Simulation.from_scenarios([sc2], precision=args.precision, stream=int(stream.cuda_stream))
+            r = measure(v, sc2.n, args.precision, 10)
+            r.update({"workload": desc, "cells": sc2.n, "storage": args.precision})
+            at_scale[key] = r
             v.close()
 
     # batched bubble populations: 64 independent domains in one handle (one
@@ -284,6 +300,7 @@ def run_gpu(args, rank: int, world: int):
                                    "kernel pair, second timed pass of the same run"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "variants": variants, "phase_us_per_step_direct_launch": phases, "batched": batched,
+            "at_scale": at_scale,
         }
         print(json.dumps(line))
 
@@ -410,6 +427,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="direct kernel launches (for ncu)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-scale", action="store_true", help="skip the larger-lattice measurements")
     ap.add_argument("--flush", default="write+read", choices=["write", "write+read"],
                     help="L2 flush between timed steps")
     args = ap.parse_args()

@@ -708,7 +708,7 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 
 // K1I: interface cells, from the list of interface cells built at the end of
 // the previous step.  A block of 128 threads takes 16 cells per pass, eight
-// threads per cell.  Load phase: the 5x5x5 box of fill levels around the cell
+// threads per cell.  Load phase: the 81 fill levels of the curvature stencil
 // (rows along x), and for the directions q, q+8, q+16 the cell's PDFs, the PDF
 // streaming in, the neighbour types and the mass-exchange terms.  Gradient
 // phase: Parker-Youngs gradients at the cell and at its six face neighbours
@@ -748,6 +748,19 @@ struct IfStage {
 };
 
 __device__ inline int ph_index(int dx, int dy, int dz) { return (dx + 2) + 5 * (dy + 2) + 25 * (dz + 2); }
+// (dy, dz) of stencil row r (0-20): rows 0-8 are |dy|,|dz| <= 1 (five points
+// along x), rows 9-20 have |dy| = 2 or |dz| = 2 (three points along x)
+__device__ inline void ph_row(int r, int& dy, int& dz) {
+    if (r < 9) {
+        dy = r % 3 - 1;
+        dz = r / 3 - 1;
+    } else {
+        const int e = r - 9, side = e / 3, t = e % 3 - 1;
+        const int s2 = (side & 1) ? -2 : 2;
+        if (side < 2) { dy = s2; dz = t; }
+        else { dy = t; dz = s2; }
+    }
+}
 
 template <typename T, bool ONE>
 __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MINB) k_stream_interface(StepArgs A) {
@@ -788,22 +801,29 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
             const long long g = A.ilist[i0 + c];
             const Dom& D = dom_at<ONE>(A, g);
             const Stencil st = make_stencil(D, g);
-            constexpr int NR = (25 + TPC - 1) / TPC;   // box rows of this thread
+            // the 81 stencil points as 21 rows along x: 9 rows |dy|,|dz| <= 1 of
+            // five points (x = -2..2), then 12 rows with |dy| = 2 or |dz| = 2 of
+            // three points (x = -1..1); no other point is read
+            constexpr int NR = (21 + TPC - 1) / TPC;   // rows of this thread
             constexpr int ND = (19 + TPC - 1) / TPC;   // directions of this thread
             C rowv[NR][5];
             const bool xin = st.x >= 2 && st.x < st.nx - 2;
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 const int r = q + TPC * k;
-                if (r < 25) {
-                    const int dy = r % 5 - 2, dz = r / 5 - 2;
+                if (r < 21) {
+                    int dy, dz;
+                    ph_row(r, dy, dz);
+                    const int w = r < 9 ? 2 : 1;   // half width of the row
                     if (xin) {
                         const unsigned b = st.at(0, dy, dz);
 #pragma unroll
-                        for (int e = 0; e < 5; ++e) rowv[k][e] = phtc[b + (e - 2)];
+                        for (int e = 0; e < 5; ++e)
+                            if (e - 2 >= -w && e - 2 <= w) rowv[k][e] = phtc[b + (e - 2)];
                     } else {
 #pragma unroll
-                        for (int e = 0; e < 5; ++e) rowv[k][e] = phtc[st.at(e - 2, dy, dz)];
+                        for (int e = 0; e < 5; ++e)
+                            if (e - 2 >= -w && e - 2 <= w) rowv[k][e] = phtc[st.at(e - 2, dy, dz)];
                     }
                 }
             }
@@ -841,9 +861,14 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 const int r = q + TPC * k;
-                if (r < 25) {
+                if (r < 21) {
+                    int dy, dz;
+                    ph_row(r, dy, dz);
+                    const int w = r < 9 ? 2 : 1;
+                    C* row = &sh.ph[c][ph_index(0, dy, dz)];
 #pragma unroll
-                    for (int e = 0; e < 5; ++e) sh.ph[c][5 * r + e] = rowv[k][e];
+                    for (int e = 0; e < 5; ++e)
+                        if (e - 2 >= -w && e - 2 <= w) row[e - 2] = rowv[k][e];
                 }
             }
 #pragma unroll
