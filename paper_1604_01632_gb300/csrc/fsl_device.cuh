@@ -279,6 +279,7 @@ template <> struct Form<__half> {
     using C = float;
     static constexpr bool shifted = true;
     __device__ static inline float ld_dev(const __half* p) { return __half2float(*p); }
+    __device__ static inline void st_dev2(__half* p, float2 v) { *(__half2*)p = __floats2half2_rn(v.x, v.y); }
     __device__ static inline void st_dev(__half* p, float v) { *p = __float2half_rn(v); }
     __device__ static inline float ld(const __half* p, int a) { return weightc<float>(a) + __half2float(*p); }
     __device__ static inline void st(__half* p, int a, float v) { *p = __float2half_rn(v - weightc<float>(a)); }
@@ -287,6 +288,7 @@ template <> struct Form<__nv_bfloat16> {
     using C = float;
     static constexpr bool shifted = true;
     __device__ static inline float ld_dev(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static inline void st_dev2(__nv_bfloat16* p, float2 v) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(v.x, v.y); }
     __device__ static inline void st_dev(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static inline float ld(const __nv_bfloat16* p, int a) {
         return weightc<float>(a) + __bfloat162float(*p);
@@ -439,6 +441,109 @@ __device__ inline void collide_dev(const float* d, float* dout, float omp, float
     }
 }
 
+// Packed FP32 (two cells in one float2, Blackwell's paired FP32 add / mul /
+// fma): collide_dev for two cells at once, the same formulas with the
+// operations regrouped for fused multiply-adds.
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p2(float x) { return make_float2(x, x); }
+
+// c_a . v for an odd direction a (its first non-zero component is +1)
+template <int a>
+__device__ __forceinline__ float2 cdot2(float2 vx, float2 vy, float2 vz) {
+    constexpr int X = cx(a), Y = cy(a), Z = cz(a);
+    if constexpr (X != 0) {
+        if constexpr (Y > 0) return p2add(vx, vy);
+        else if constexpr (Y < 0) return p2sub(vx, vy);
+        else if constexpr (Z > 0) return p2add(vx, vz);
+        else if constexpr (Z < 0) return p2sub(vx, vz);
+        else return vx;
+    } else if constexpr (Y != 0) {
+        if constexpr (Z > 0) return p2add(vy, vz);
+        else if constexpr (Z < 0) return p2sub(vy, vz);
+        else return vy;
+    } else {
+        return vz;
+    }
+}
+
+struct Collide2 {
+    float2 ux, uy, uz, drho, rho, nusq15, hp, hm, Fx, Fy, Fz, uF;
+};
+
+// One TRT pair (a, a+1) of two cells; w = w_a, cp/cm the forcing prefactors.
+template <int a, bool FORCE>
+__device__ __forceinline__ void trt_pair2(const float2* d, float2* o, const Collide2& K, float omp, float omm,
+                                          float w, float cp, float cm) {
+    constexpr int b = a + 1;
+    const float2 cu = cdot2<a>(K.ux, K.uy, K.uz);
+    // f_eq+ - w = w [drho + rho (9/2 (c.u)^2 - 3/2 u.u)],  A = omp (f+ - f_eq+)
+    float2 t = p2fma(p2mul(p2(4.5f), cu), cu, K.nusq15);
+    t = p2fma(K.rho, t, K.drho);
+    const float2 A = p2fma(K.hp, p2add(d[a], d[b]), p2mul(p2(-omp * w), t));
+    // f_eq- = 3 w rho c.u,  B = omm (f- - f_eq-)
+    const float2 B = p2fma(K.hm, p2sub(d[a], d[b]), p2mul(p2mul(K.rho, p2(-omm * 3.f * w)), cu));
+    float2 oa = p2sub(d[a], p2add(A, B));
+    float2 ob = p2sub(d[b], p2sub(A, B));
+    if constexpr (FORCE) {
+        const float2 cF = cdot2<a>(K.Fx, K.Fy, K.Fz);
+        const float2 sp = p2fma(p2(9.f * cp * w), p2mul(cu, cF), p2mul(p2(-3.f * cp * w), K.uF));
+        const float2 sm = p2mul(p2(3.f * cm * w), cF);
+        oa = p2add(oa, p2add(sp, sm));
+        ob = p2add(ob, p2sub(sp, sm));
+    }
+    o[a] = oa;
+    o[b] = ob;
+}
+
+template <bool FORCE>
+__device__ __forceinline__ void collide_dev2(const float2* d, float2* o, float omp, float omm, float gx, float gy,
+                                             float gz) {
+    Collide2 K;
+    K.drho = p2add(p2add(p2add(p2add(d[0], d[1]), p2add(d[2], d[3])), p2add(p2add(d[4], d[5]), p2add(d[6], d[7]))),
+                   p2add(p2add(p2add(p2add(d[8], d[9]), p2add(d[10], d[11])),
+                               p2add(p2add(d[12], d[13]), p2add(d[14], d[15]))),
+                         p2add(p2add(d[16], d[17]), d[18])));
+    K.rho = p2add(K.drho, p2(1.f));
+    const float2 e78 = p2sub(d[7], d[8]), e1112 = p2sub(d[11], d[12]), e1516 = p2sub(d[15], d[16]);
+    float2 jx = p2add(p2add(p2add(p2sub(d[1], d[2]), e78), p2add(p2sub(d[9], d[10]), e1112)), p2sub(d[13], d[14]));
+    float2 jy = p2add(p2add(p2add(p2sub(d[3], d[4]), e78), p2add(p2sub(d[10], d[9]), e1516)), p2sub(d[17], d[18]));
+    float2 jz = p2add(p2add(p2add(p2sub(d[5], d[6]), e1112), p2add(p2sub(d[14], d[13]), e1516)), p2sub(d[18], d[17]));
+    K.Fx = p2(0.f); K.Fy = p2(0.f); K.Fz = p2(0.f); K.uF = p2(0.f);
+    if constexpr (FORCE) {
+        K.Fx = p2mul(K.rho, p2(gx)); K.Fy = p2mul(K.rho, p2(gy)); K.Fz = p2mul(K.rho, p2(gz));
+        jx = p2fma(p2(0.5f), K.Fx, jx);
+        jy = p2fma(p2(0.5f), K.Fy, jy);
+        jz = p2fma(p2(0.5f), K.Fz, jz);
+    }
+    const float2 ir = make_float2(1.f / K.rho.x, 1.f / K.rho.y);
+    K.ux = p2mul(jx, ir); K.uy = p2mul(jy, ir); K.uz = p2mul(jz, ir);
+    K.nusq15 = p2mul(p2fma(K.uz, K.uz, p2fma(K.uy, K.uy, p2mul(K.ux, K.ux))), p2(-1.5f));
+    if constexpr (FORCE) K.uF = p2fma(K.uz, K.Fz, p2fma(K.uy, K.Fy, p2mul(K.ux, K.Fx)));
+    K.hp = p2(0.5f * omp);
+    K.hm = p2(0.5f * omm);
+    const float cp = 1.f - 0.5f * omp, cm = 1.f - 0.5f * omm;
+    const float w0 = weightc<float>(0), w1 = weightc<float>(1), w2 = weightc<float>(7);
+    {
+        // rest direction: d0 - omp (d0 - w0 (drho - rho 3/2 u.u))
+        const float2 t = p2fma(K.rho, K.nusq15, K.drho);
+        float2 o0 = p2fma(p2(-omp), p2sub(d[0], p2mul(p2(w0), t)), d[0]);
+        if constexpr (FORCE) o0 = p2fma(p2(cp * w0 * -3.f), K.uF, o0);
+        o[0] = o0;
+    }
+    trt_pair2<1, FORCE>(d, o, K, omp, omm, w1, cp, cm);
+    trt_pair2<3, FORCE>(d, o, K, omp, omm, w1, cp, cm);
+    trt_pair2<5, FORCE>(d, o, K, omp, omm, w1, cp, cm);
+    trt_pair2<7, FORCE>(d, o, K, omp, omm, w2, cp, cm);
+    trt_pair2<9, FORCE>(d, o, K, omp, omm, w2, cp, cm);
+    trt_pair2<11, FORCE>(d, o, K, omp, omm, w2, cp, cm);
+    trt_pair2<13, FORCE>(d, o, K, omp, omm, w2, cp, cm);
+    trt_pair2<15, FORCE>(d, o, K, omp, omm, w2, cp, cm);
+    trt_pair2<17, FORCE>(d, o, K, omp, omm, w2, cp, cm);
+}
+
 template <typename C>
 __device__ inline C collide_any(bool force, const C* fin, C* fout, C omp, C omm, C gx, C gy, C gz) {
     return force ? collide<C, true>(fin, fout, omp, omm, gx, gy, gz) : collide<C, false>(fin, fout, omp, omm, gx, gy, gz);
@@ -520,11 +625,8 @@ __device__ inline Pull make_pull(const Dom& D, long long g) {
 // liquid cells.  Only cells flagged as touching a wall read the types of
 // their neighbours; a liquid cell never touches gas (closed interface layer).
 template <typename T, bool ONE>
-__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 5) k_stream_liquid(StepArgs A) {
+__device__ __forceinline__ void liquid_one(const StepArgs& A, long long g, uint8_t f) {
     using C = typename Form<T>::C;
-    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
-    const uint8_t f = A.flag[g];
-    if (ctype(f) != LIQ) return;
     const Dom& D = dom_at<ONE>(A, g);
     const Par<C> R = par_of<C>(D);
     const Pull P = make_pull(D, g);
@@ -592,6 +694,83 @@ __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 5) k_stream_li
         if (!(rho == rho)) set_status(A.status, ST_NAN);
 #pragma unroll
         for (int a = 0; a < 19; ++a) Form<T>::st(dst + a * S + gi, a, fout[a]);
+    }
+}
+
+// One liquid cell per thread (FP32 and FP64 storage).
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 5) k_stream_liquid(StepArgs A) {
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    const uint8_t f = A.flag[g];
+    if (ctype(f) != LIQ) return;
+    liquid_one<T, ONE>(A, g, f);
+}
+
+// Two cells per thread, cells 2t and 2t+1 (16-bit shifted storage), collided
+// together in packed FP32.  A pair with a cell next to a wall reads that
+// cell's neighbour types first and picks each link's address without a
+// branch; a pair with one liquid cell computes both lanes and stores only the
+// liquid one (the other lane's loads stay inside the lattice and its result
+// is dropped).  Both liquid: one 32-bit store per direction.  (Cells 2t and
+// 2t+1 always lie in the same domain: domains start on multiples of 256.)
+#ifndef FSL_LIQ2_MINB
+#define FSL_LIQ2_MINB 3   // resident two-cell liquid blocks per SM (register bound)
+#endif
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(FSL_BLOCK, FSL_LIQ2_MINB) k_stream_liquid2(StepArgs A) {
+    const long long g0 = 2 * ((long long)blockIdx.x * FSL_BLOCK + threadIdx.x);
+    if (g0 >= A.stride) return;
+    const unsigned short ff = *(const unsigned short*)(A.flag + g0);
+    const uint8_t f0 = (uint8_t)(ff & 0xff), f1 = (uint8_t)(ff >> 8);
+    const bool v0 = ctype(f0) == LIQ, v1 = ctype(f1) == LIQ;
+    if (!v0 && !v1) return;
+    const Dom& D = dom_at<ONE>(A, g0);
+    const Par<float> R = par_of<float>(D);
+    const Pull P0 = make_pull(D, g0), P1 = make_pull(D, g0 + 1);
+    const unsigned S = (unsigned)A.stride, gi = (unsigned)g0;
+    const T* __restrict__ src = (const T*)A.fsrc;
+    T* __restrict__ dst = (T*)A.fdst;
+    float2 d[19];
+    if (!((f0 | f1) & K_WALL)) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) {
+            const unsigned y0 = gi + (unsigned)(P0.ox[1 - cx(a)] + P0.oy[1 - cy(a)] + P0.oz[1 - cz(a)]);
+            const unsigned y1 = gi + 1u + (unsigned)(P1.ox[1 - cx(a)] + P1.oy[1 - cy(a)] + P1.oz[1 - cz(a)]);
+            d[a] = make_float2(Form<T>::ld_dev(src + (a * S + y0)), Form<T>::ld_dev(src + (a * S + y1)));
+        }
+    } else {
+        const bool w0 = v0 && (f0 & K_WALL), w1 = v1 && (f1 & K_WALL);
+        d[0] = make_float2(Form<T>::ld_dev(src + gi), Form<T>::ld_dev(src + gi + 1u));
+#pragma unroll
+        for (int a = 1; a < 19; ++a) {
+            const unsigned y0 = gi + (unsigned)(P0.ox[1 - cx(a)] + P0.oy[1 - cy(a)] + P0.oz[1 - cz(a)]);
+            const unsigned y1 = gi + 1u + (unsigned)(P1.ox[1 - cx(a)] + P1.oy[1 - cy(a)] + P1.oz[1 - cz(a)]);
+            const uint8_t t0 = w0 ? ctype(A.flag[y0]) : (uint8_t)LIQ;
+            const uint8_t t1 = w1 ? ctype(A.flag[y1]) : (uint8_t)LIQ;
+            // bounce-back reads the cell's own opposite PDF (w_a = w_abar)
+            float x0 = Form<T>::ld_dev(src + ((t0 == OBS || t0 == LID) ? opp(a) * S + gi : a * S + y0));
+            float x1 = Form<T>::ld_dev(src + ((t1 == OBS || t1 == LID) ? opp(a) * S + gi + 1u : a * S + y1));
+            const float lidt = (6.f * weightc<float>(a)) * cdot<float>(a, R.lid[0], R.lid[1], R.lid[2]);
+            if (t0 == LID) x0 += lidt;
+            if (t1 == LID) x1 += lidt;
+            d[a] = make_float2(x0, x1);
+        }
+    }
+    float2 o[19];
+    if (D.has_force)
+        collide_dev2<true>(d, o, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
+    else
+        collide_dev2<false>(d, o, R.omp, R.omm, 0.f, 0.f, 0.f);
+    if ((v0 && !(o[0].x == o[0].x)) || (v1 && !(o[0].y == o[0].y))) set_status(A.status, ST_NAN);
+    if (v0 && v1) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Form<T>::st_dev2(dst + (a * S + gi), o[a]);
+    } else if (v0) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Form<T>::st_dev(dst + (a * S + gi), o[a].x);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Form<T>::st_dev(dst + (a * S + gi + 1u), o[a].y);
     }
 }
 
@@ -1835,10 +2014,17 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         else                                                                                                 \
             k_stream_interface<T, false><<<(unsigned)(2 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                 \
         if (ei) cudaEventRecord(ei, s2);                                                                     \
-        if (A.ndom == 1)                                                                                     \
-            k_stream_liquid<T, true><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                  \
-        else                                                                                                 \
-            k_stream_liquid<T, false><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                                 \
+        if constexpr (Form<T>::shifted) {                                                                    \
+            if (A.ndom == 1)                                                                                 \
+                k_stream_liquid2<T, true><<<(unsigned)((nb + 1) / 2), FSL_BLOCK, 0, s>>>(A);                 \
+            else                                                                                             \
+                k_stream_liquid2<T, false><<<(unsigned)((nb + 1) / 2), FSL_BLOCK, 0, s>>>(A);                \
+        } else {                                                                                             \
+            if (A.ndom == 1)                                                                                 \
+                k_stream_liquid<T, true><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                              \
+            else                                                                                             \
+                k_stream_liquid<T, false><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                             \
+        }                                                                                                    \
         if (el) cudaEventRecord(el, s);                                                                      \
         cudaEventRecord(join, s2);                                                                           \
         cudaStreamWaitEvent(s, join, 0);                                                                     \
