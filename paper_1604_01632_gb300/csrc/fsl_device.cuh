@@ -149,7 +149,10 @@ struct StepArgs {
 
 // Domain descriptor and domain of a cell: a handle with one domain reads
 // them from the kernel parameters, a batch from its device tables.
-__device__ inline Dom get_dom(const StepArgs& A, int d) { return A.ndom == 1 ? A.d0 : A.doms[d]; }
+// (the device table holds every domain, the single one too; reading fields
+// through the reference loads only those fields, where a copy of a descriptor
+// chosen at run time would go through local memory)
+__device__ inline const Dom& get_dom(const StepArgs& A, int d) { return A.doms[d]; }
 __device__ inline int block_dom(const StepArgs& A, long long g) { return A.ndom == 1 ? 0 : A.blk_dom[g / FSL_BLOCK]; }
 // The same for the hot kernels, which exist once for a single domain (ONE:
 // the descriptor is read straight from the kernel parameters) and once for a
@@ -581,6 +584,26 @@ __device__ inline long long volume_term(uint8_t t, double phi) {
         return __double2ll_rn((1.0 - c) * 4294967296.0);
     }
     return 0;
+}
+
+// The same term from an FP32 fill level, for the FP32-collide forms (every
+// place that forms a volume term of those forms uses this one, so the
+// per-step differences stay exact): (1 - c) 2^32 with c = clamp(phi, 0, 1)
+// taken apart into its 24-bit significand and exponent, integer arithmetic
+// only (the FP64 pipe of this GPU is slow), rounded half up.
+__device__ inline long long volume_term_f(uint8_t t, float phi) {
+    if (t == GAS) return FSL_VOL_ONE;
+    if (t != IFC) return 0;
+    const float c = fminf(fmaxf(phi, 0.f), 1.f);
+    const unsigned u = __float_as_uint(c);
+    const int E = (int)(u >> 23);
+    const unsigned long long M = (u & 0x7fffffu) | (E ? 0x800000u : 0u);
+    const int sh = (E ? E : 1) - 150 + 32;   // c 2^32 = M 2^sh
+    unsigned long long v;
+    if (sh >= 0) v = M << sh;
+    else if (sh > -40) v = (M + (1ull << (-sh - 1))) >> (-sh);
+    else v = 0;
+    return FSL_VOL_ONE - (long long)v;
 }
 
 __device__ inline uint8_t new_type(uint8_t t, uint8_t mk) {
@@ -1212,26 +1235,38 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
 
 // First neighbour of cell z (direction order) that is an interface cell
 // carrying mark `want`, or -1.
-__device__ inline long long first_marked(const StepArgs& A, const Dom& D, long long z, uint8_t want) {
-    const Cell c = make_cell(D, z);
+//
+// The neighbour scans below load all eighteen neighbours first and then test
+// them (one memory latency, not one per neighbour): bit a of the mask is set
+// when neighbour a (1-18) is an interface cell carrying mark `want`.
+__device__ inline unsigned marked_mask(const StepArgs& A, const Cell& c, uint8_t want) {
+    uint8_t fl[19], mk[19];
+#pragma unroll
     for (int a = 1; a < 19; ++a) {
         const long long w = c.at(cx(a), cy(a), cz(a));
-        if (ctype(A.flag[w]) == IFC && A.mark[w] == want) return w;
+        fl[a] = A.flag[w];
+        mk[a] = A.mark[w];
     }
-    return -1;
+    unsigned m = 0;
+#pragma unroll
+    for (int a = 1; a < 19; ++a) m |= (unsigned)(ctype(fl[a]) == IFC && mk[a] == want) << a;
+    return m;
+}
+__device__ inline long long first_marked(const StepArgs& A, const Dom& D, long long z, uint8_t want) {
+    const Cell c = make_cell(D, z);
+    const unsigned m = marked_mask(A, c, want);
+    if (m == 0) return -1;
+    const int a = __ffs(m) - 1;
+    return c.at(rcx(a), rcy(a), rcz(a));
 }
 
 // An interface cell carrying an emptied mark that phase A does not cancel (no
 // filled neighbour).  Written as a test on the marks K1I set, so it holds
 // whether or not another thread has already cleared the cancelled mark.
 __device__ inline bool still_emptied(const StepArgs& A, const Dom& D, long long w) {
-    if (ctype(A.flag[w]) != IFC || A.mark[w] != MK_EMPTIED) return false;
-    const Cell c = make_cell(D, w);
-    for (int a = 1; a < 19; ++a) {
-        const long long v = c.at(cx(a), cy(a), cz(a));
-        if (ctype(A.flag[v]) == IFC && A.mark[v] == MK_FILLED) return false;
-    }
-    return true;
+    const uint8_t fw = A.flag[w], mw = A.mark[w];
+    const unsigned filled = marked_mask(A, make_cell(D, w), MK_FILLED);   // loaded with w's own
+    return ctype(fw) == IFC && mw == MK_EMPTIED && filled == 0;
 }
 
 // Conversion phases A and B (Sec. 2.2, cell conversion), one thread per
@@ -1260,7 +1295,7 @@ __device__ inline void convert_ab_phase(const StepArgs& A) {
             const long long p = A.mlist[t / 18];
             const int a = 1 + t % 18;
             const int d = block_dom(A, p);
-            const Dom D = get_dom(A, d);
+            const Dom& D = get_dom(A, d);
             const uint8_t mp = A.mark[p];
             const Cell c = make_cell(D, p);
             z = c.at(rcx(a), rcy(a), rcz(a));
@@ -1272,12 +1307,32 @@ __device__ inline void convert_ab_phase(const StepArgs& A) {
                         // f = f_eq of the mean density and velocity of the liquid
                         // and non-emptied interface neighbours, in direction order
                         const Cell cz_ = make_cell(D, z);
+                        // which neighbours enter the mean: types and marks of all
+                        // eighteen first, the cancellation test only for the
+                        // emptied ones
+                        uint8_t fl[19], mk[19];
+#pragma unroll
+                        for (int q = 1; q < 19; ++q) {
+                            const long long w = cz_.at(cx(q), cy(q), cz(q));
+                            fl[q] = A.flag[w];
+                            mk[q] = A.mark[w];
+                        }
+                        unsigned use = 0, emp = 0;
+#pragma unroll
+                        for (int q = 1; q < 19; ++q) {
+                            const uint8_t tw = ctype(fl[q]);
+                            use |= (unsigned)(tw == LIQ || (tw == IFC && mk[q] != MK_EMPTIED)) << q;
+                            emp |= (unsigned)(tw == IFC && mk[q] == MK_EMPTIED) << q;
+                        }
+                        for (unsigned e = emp; e; e &= e - 1) {
+                            const int q = __ffs(e) - 1;
+                            if (!still_emptied(A, D, cz_.at(rcx(q), rcy(q), rcz(q)))) use |= 1u << q;
+                        }
                         C sr = (C)0, sux = (C)0, suy = (C)0, suz = (C)0;
                         int cnt = 0;
                         for (int q = 1; q < 19; ++q) {
-                            const long long w = cz_.at(cx(q), cy(q), cz(q));
-                            const uint8_t tw = ctype(A.flag[w]);
-                            if (tw == LIQ || (tw == IFC && !still_emptied(A, D, w))) {
+                            const long long w = cz_.at(rcx(q), rcy(q), rcz(q));
+                            if ((use >> q) & 1u) {
                                 C fo[19];
 #pragma unroll
                                 for (int r = 0; r < 19; ++r) fo[r] = Form<T>::ld(f + (long long)r * S + w, r);
@@ -1308,8 +1363,9 @@ __device__ inline void convert_ab_phase(const StepArgs& A) {
                 // is p the first emptied-and-not-cancelled neighbour of z?
                 const Cell cz_ = make_cell(D, z);
                 long long first = -1;
-                for (int q = 1; q < 19 && first < 0; ++q) {
-                    const long long w = cz_.at(cx(q), cy(q), cz(q));
+                for (unsigned e = marked_mask(A, cz_, MK_EMPTIED); e && first < 0; e &= e - 1) {
+                    const int q = __ffs(e) - 1;
+                    const long long w = cz_.at(rcx(q), rcy(q), rcz(q));
                     if (still_emptied(A, D, w)) first = w;
                 }
                 if (first == p) {
@@ -1469,19 +1525,26 @@ __device__ inline void convert_c_phase(const StepArgs& A) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
         const long long g = i < nm ? A.mlist[i] : A.llist[i - nm];
         const int d = block_dom(A, g);
-        const Dom D = get_dom(A, d);
+        const Dom& D = get_dom(A, d);
         const Cell c = make_cell(D, g);
         const uint8_t mk = A.mark[g];
         if (i < nm) {
             if (mk != MK_FILLED && mk != MK_EMPTIED) continue;   // emptied mark cancelled in phase A
             const double mex = (mk == MK_FILLED) ? A.m[g] - A.rhoi[g] : A.m[g];
-            int k = 0;
+            uint8_t fl[19], mz[19];
+#pragma unroll
             for (int a = 1; a < 19; ++a) {
                 const long long z = c.at(cx(a), cy(a), cz(a));
-                if (new_type(ctype(A.flag[z]), A.mark[z]) == IFC) {
-                    ++k;
-                    A.recv[z] = step;   // z pulls a share in the update phase
-                }
+                fl[a] = A.flag[z];
+                mz[a] = A.mark[z];
+            }
+            unsigned rcv = 0;
+#pragma unroll
+            for (int a = 1; a < 19; ++a) rcv |= (unsigned)(new_type(ctype(fl[a]), mz[a]) == IFC) << a;
+            const int k = __popc(rcv);
+            for (unsigned e = rcv; e; e &= e - 1) {
+                const int a = __ffs(e) - 1;
+                A.recv[c.at(rcx(a), rcy(a), rcz(a))] = step;   // pulls a share in phase D
             }
             if (k > 0) A.exs[g] = mex / (double)k;
             else atomicAdd((unsigned long long*)&A.pool[d], (unsigned long long)__double2ll_rn(mex * 1099511627776.0));
@@ -1510,14 +1573,24 @@ __device__ inline void convert_c_phase(const StepArgs& A) {
         }
         // new interface cell from liquid: a neighbour of another bubble merges
         const int b = A.id[g];
+        uint8_t fl[19], mz[19];
+        int iz[19];
+#pragma unroll
         for (int a = 1; a < 19; ++a) {
             const long long z = c.at(cx(a), cy(a), cz(a));
-            const uint8_t ntz = new_type(ctype(A.flag[z]), A.mark[z]);
-            if ((ntz == GAS || ntz == IFC) && A.id[z] != b) {
-                atomicExch(&A.trig[1 + d], 1);
-                atomicExch(A.trig, 1);
-                break;
-            }
+            fl[a] = A.flag[z];
+            mz[a] = A.mark[z];
+            iz[a] = A.id[z];
+        }
+        bool merge = false;
+#pragma unroll
+        for (int a = 1; a < 19; ++a) {
+            const uint8_t ntz = new_type(ctype(fl[a]), mz[a]);
+            merge |= (ntz == GAS || ntz == IFC) && iz[a] != b;
+        }
+        if (merge) {
+            atomicExch(&A.trig[1 + d], 1);
+            atomicExch(A.trig, 1);
         }
     }
 }
@@ -1530,6 +1603,10 @@ __device__ inline void convert_c_phase(const StepArgs& A) {
 __device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
     const int ni = *A.icount, ng = *A.gcount, nl = *A.lcount;
     const int total = ni + ng + nl;
+    // one pass over the list: aggregate the atomics over the block (they hit
+    // few addresses); several passes: over the warp only, so that the block's
+    // warps do not wait for one another in every pass
+    const bool blocked = total <= (int)(gridDim.x * blockDim.x);
     const int step = *A.stepno;
     const int stride = gridDim.x * blockDim.x;
     for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
@@ -1548,13 +1625,17 @@ __device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
             const uint8_t f = A.flag[g];
             const uint8_t mk = A.mark[g];
             key = A.id[g];
-            const double m0 = A.m[g], rh = A.rhoi[g], ph0 = A.phi[g];
+            const double m0 = A.m[g], rh = A.rhoi[g];
+            // FP32-collide forms: fill levels and volume terms from the FP32 copy
+            const bool f32 = A.phif != nullptr;
+            const double ph0 = f32 ? 0.0 : A.phi[g];
+            const float ph0f = f32 ? A.phif[g] : 0.f;
             const int rs = A.recv[g];
             const long long nI = A.nif[d];
             const long long pool = A.pool[d];
             const uint8_t t = ctype(f);
             if (t == IFC && mk == MK_CFILLED) {
-                dv = -volume_term(IFC, ph0);
+                dv = f32 ? -volume_term_f(IFC, ph0f) : -volume_term(IFC, ph0);
                 ckey = key;
                 dc = -1;
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
@@ -1564,7 +1645,7 @@ __device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
                 A.id[g] = -1;
                 A.mark[g] = MK_NONE;
             } else if (t == IFC && mk == MK_CEMPTIED) {
-                dv = FSL_VOL_ONE - volume_term(IFC, ph0);
+                dv = FSL_VOL_ONE - (f32 ? volume_term_f(IFC, ph0f) : volume_term(IFC, ph0));
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
                 A.phi[g] = 0.0;
                 A.phit[g] = 0.0;
@@ -1574,42 +1655,64 @@ __device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
             } else {
                 double sm = m0;
                 if (rs == step) {
-                    // a converted neighbour listed this cell among its receivers
-                    const Dom D = get_dom(A, d);
+                    // a converted neighbour listed this cell among its receivers:
+                    // all eighteen step stamps first, then the shares of the
+                    // converted ones, added in direction order
+                    const Dom& D = get_dom(A, d);
                     const Cell c = make_cell(D, g);
-                    for (int a = 1; a < 19; ++a) {
-                        const long long z = c.at(cx(a), cy(a), cz(a));
-                        if (A.cstep[z] == step) sm = sm + A.exs[z];
-                    }
+                    int cs[19];
+#pragma unroll
+                    for (int a = 1; a < 19; ++a) cs[a] = A.cstep[c.at(cx(a), cy(a), cz(a))];
+                    double ex[19];
+#pragma unroll
+                    for (int a = 1; a < 19; ++a) ex[a] = cs[a] == step ? A.exs[c.at(cx(a), cy(a), cz(a))] : 0.0;
+#pragma unroll
+                    for (int a = 1; a < 19; ++a)
+                        if (cs[a] == step) sm = sm + ex[a];
                 }
                 if (nI > 0 && pool != 0) {
                     const double share = ((double)pool * 9.094947017729282379150390625e-13) / (double)nI;
                     sm = sm + share;
                 }
-                const double phn = sm / rh;
-                const long long told = volume_term(t, ph0);
                 A.m[g] = sm;
-                A.phi[g] = phn;
-                const double pht = phn < 0.0 ? 0.0 : (phn > 1.0 ? 1.0 : phn);
-                A.phit[g] = pht;
-                if (A.phif) { A.phif[g] = (float)phn; A.phitf[g] = (float)pht; }
+                if (f32) {
+                    // phi = m / rho in FP32 (Eq. 9); three conversions are the
+                    // only FP64-pipe work of the cell
+                    const float phf = (float)sm / (float)rh;
+                    A.phi[g] = (double)phf;
+                    A.phif[g] = phf;
+                    A.phitf[g] = fminf(fmaxf(phf, 0.f), 1.f);
+                    dv = volume_term_f(IFC, phf) - volume_term_f(t, ph0f);
+                } else {
+                    const double phn = sm / rh;
+                    const long long told = volume_term(t, ph0);
+                    A.phi[g] = phn;
+                    A.phit[g] = phn < 0.0 ? 0.0 : (phn > 1.0 ? 1.0 : phn);
+                    dv = volume_term(IFC, phn) - told;
+                }
                 if (t != IFC) A.flag[g] = (uint8_t)((f & ~K_TYPE) | IFC);
-                dv = volume_term(IFC, phn) - told;
                 if (t == LIQ) { ckey = key; dc = 1; }
                 keep = true;
             }
         }
-        block_add(A.vfx, dv != 0 ? key : -1, dv, sc);
-        block_add(A.ncells, ckey, dc, sc);
-        block_add(A.icnt, keep ? d : -1, 1, sc);
-        block_list_append(A.ilist_next, A.icount_next, keep, (int)g, sc);
+        if (blocked) {
+            block_add(A.vfx, dv != 0 ? key : -1, dv, sc);
+            block_add(A.ncells, ckey, dc, sc);
+            block_add(A.icnt, keep ? d : -1, 1, sc);
+            block_list_append(A.ilist_next, A.icount_next, keep, (int)g, sc);
+        } else {
+            warp_add(A.vfx, dv != 0 ? key : -1, dv);
+            warp_add(A.ncells, ckey, dc);
+            warp_add(A.icnt, keep ? d : -1, 1);
+            list_append(A.ilist_next, A.icount_next, keep, (int)g);
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0) {
         // reservoir drain of every domain whose seed cell is still gas or
         // interface (types read through the marks, which stay consistent
-        // while other threads update the flags)
-        for (int d = 0; d < A.ndom; ++d) {
-            const Dom D = get_dom(A, d);
+        // while other threads update the flags), one thread per domain
+        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
+            const Dom& D = get_dom(A, d);
             if (D.seed < 0) continue;
             const long long gs = D.off + D.seed;
             const uint8_t nt = new_type(ctype(A.flag[gs]), A.mark[gs]);
@@ -1617,7 +1720,7 @@ __device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
             if ((nt == GAS || nt == IFC) && b >= 0)
                 atomicAdd((unsigned long long*)&A.vxfx[b], (unsigned long long)(-D.rate_fx));
         }
-        *A.mcount = 0;
+        if (threadIdx.x == 0) *A.mcount = 0;
     }
 }
 
@@ -1652,9 +1755,10 @@ struct CclArgs {
 // the paper's serial flood fill and its colour unification across processes
 // (Sec. 2.4.1) become one lock-free union-find over the whole lattice whose
 // roots are the minimum cell index of each component.  Each phase below walks
-// the lattice in 256-cell tiles, one cell per thread of a 256-thread block
-// (a tile lies in one domain), or a table with a thread-stride loop, so that
-// it runs both as a kernel of its own and inside the conversion kernel.
+// the tiles (256 cells) of the domains taking part, one cell per thread of a
+// 256-thread block (a tile lies in one domain), or a table with a
+// thread-stride loop, so that it runs both as a kernel of its own and inside
+// the conversion kernel.
 
 __device__ inline bool is_fg(uint8_t f) { return ctype(f) == GAS || ctype(f) == IFC; }
 
@@ -1695,10 +1799,26 @@ __device__ inline bool ccl_active(const StepArgs& A, const CclArgs& K, int d) {
     return K.initial || A.trig[1 + d] != 0;
 }
 
-#define FSL_TILE_LOOP(A, tile) for (long long tile = blockIdx.x; tile < (A).stride / FSL_BLOCK; tile += gridDim.x)
+// First tile and tile count of domain d (read field by field).
+__device__ inline long long dom_tile0(const StepArgs& A, int d) {
+    return (A.ndom == 1 ? A.d0.off : A.doms[d].off) / FSL_BLOCK;
+}
+__device__ inline long long dom_ntiles(const StepArgs& A, int d) {
+    return ((long long)(A.ndom == 1 ? A.d0.n : A.doms[d].n) + FSL_BLOCK - 1) / FSL_BLOCK;
+}
+// The tiles of the domains taking part in a pass: after initialisation every
+// tile in order; otherwise the tiles of each triggered domain, spread over the
+// whole grid one domain after the other (on a typical step of a large batch a
+// few domains trigger, and the others are not visited at all).
+#define FSL_TILE_LOOP(A, K, tile)                                                                            \
+    for (int dd_ = 0, nd_ = (K).initial ? 1 : (A).ndom; dd_ < nd_; ++dd_)                                   \
+        if ((K).initial || (A).trig[1 + dd_] != 0)                                                           \
+            for (long long tile = ((K).initial ? 0 : dom_tile0(A, dd_)) + blockIdx.x,                        \
+                           tend_ = (K).initial ? (A).stride / FSL_BLOCK : dom_tile0(A, dd_) + dom_ntiles(A, dd_); \
+                 tile < tend_; tile += gridDim.x)
 
 __device__ inline void ccl_init_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, t) {
+    FSL_TILE_LOOP(A, K, t) {
         const long long g = t * FSL_BLOCK + threadIdx.x;
         if (ccl_active(A, K, block_dom(A, g))) K.lab[g] = is_fg(A.flag[g]) ? (int)g : -1;
     }
@@ -1719,11 +1839,11 @@ __device__ inline void ccl_init_phase(const StepArgs& A, const CclArgs& K) {
 }
 
 __device__ inline void ccl_hook_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, t) {
+    FSL_TILE_LOOP(A, K, t) {
         const long long g = t * FSL_BLOCK + threadIdx.x;
         const int d = block_dom(A, g);
         if (!ccl_active(A, K, d) || !is_fg(A.flag[g])) continue;
-        const Dom D = get_dom(A, d);
+        const Dom& D = get_dom(A, d);
         const Cell c = make_cell(D, g);
         // the nine directions 1, 3, ..., 17 cover each neighbour pair once
         for (int a = 1; a < 19; a += 2) {
@@ -1740,7 +1860,7 @@ __device__ inline void ccl_hook_phase(const StepArgs& A, const CclArgs& K) {
 
 // Compress every cell onto its root; roots take a new bubble-table slot.
 __device__ inline void ccl_compress_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, t) {
+    FSL_TILE_LOOP(A, K, t) {
         const long long g = t * FSL_BLOCK + threadIdx.x;
         const int d = block_dom(A, g);
         if (!ccl_active(A, K, d) || !is_fg(A.flag[g])) continue;
@@ -1749,7 +1869,7 @@ __device__ inline void ccl_compress_phase(const StepArgs& A, const CclArgs& K) {
         if (!ok) { set_status(A.status, ST_CCL); continue; }
         K.lab[g] = r;
         if (r == (int)g) {
-            const Dom D = get_dom(A, d);
+            const Dom& D = get_dom(A, d);
             const int k = atomicAdd(&K.nslot[d], 1);
             if (k >= D.slot_cap) { set_status(A.status, ST_TABLE_FULL); K.aux[g] = -1; continue; }
             K.aux[g] = D.slot_off + k;
@@ -1775,7 +1895,7 @@ __device__ inline void hash_add(const CclArgs& K, unsigned long long key, long l
 // New volumes and cell counts per component, overlap volumes V_{c,b} of new
 // component c with old bubble b, new ids.
 __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, t) {
+    FSL_TILE_LOOP(A, K, t) {
         const long long g = t * FSL_BLOCK + threadIdx.x;
         const int d = block_dom(A, g);
         if (!ccl_active(A, K, d)) continue;   // whole block: one domain
@@ -1785,7 +1905,7 @@ __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
         if (ty == GAS || ty == IFC) {
             const int r = K.lab[g];
             c = K.aux[r];
-            term = volume_term(ty, A.phi[g]);
+            term = A.phif ? volume_term_f(ty, A.phif[g]) : volume_term(ty, A.phi[g]);
         }
         warp_add(K.nvfx, c, term);
         warp_add(K.nncells, c, c >= 0 ? 1 : 0);
@@ -1796,7 +1916,7 @@ __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
             hash_add(K, key, term, A.status);
             atomicAdd((unsigned long long*)&K.vtot[b], (unsigned long long)term);
             atomicMin(&K.minc[b], K.lab[g]);
-            const Dom D = get_dom(A, d);
+            const Dom& D = get_dom(A, d);
             if (D.seed >= 0 && g - D.off == D.seed) {
                 const long long x = A.vxfx[b];
                 hash_add(K, key, x, A.status);
@@ -1839,7 +1959,7 @@ __device__ inline void ccl_install_phase(const StepArgs& A, const CclArgs& K) {
     for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < K.nslots_total; sl += nth) {
         const int d = K.slot_dom[sl];
         if (!ccl_active(A, K, d)) continue;   // untouched domains keep their table
-        const Dom D = get_dom(A, d);
+        const Dom& D = get_dom(A, d);
         const int k = (int)(sl - D.slot_off);
         if (k < K.nslot[d]) {
             A.vfx[sl] = K.nvfx[sl];
@@ -1895,7 +2015,7 @@ __device__ inline bool grid_barrier(const StepArgs& A) {
 // separated by grid barriers, then, when phase C set a merge / split trigger,
 // the labelling of the triggered domains (Secs. 2.3.1, 2.3.2).
 template <typename T>
-__global__ void __launch_bounds__(FSL_CONV_THREADS) k_convert(StepArgs A, CclArgs K) {
+__global__ void __launch_bounds__(FSL_CONV_THREADS, 3) k_convert(StepArgs A, CclArgs K) {
     __shared__ BlockScratch sc;
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
@@ -1928,7 +2048,7 @@ template <typename T>
 __global__ void __launch_bounds__(FSL_BLOCK) k_init_state(StepArgs A, int d, const uint8_t* flags_in,
                                                          const double* fill, const double* rho, const double* u) {
     using C = typename Form<T>::C;
-    const Dom D = get_dom(A, d);
+    const Dom& D = get_dom(A, d);
     const long long l = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
     if (l >= D.n) return;
     const long long g = D.off + l;
