@@ -241,11 +241,16 @@ def run_gpu(args, rank: int, world: int):
     at_scale = {}
     if not args.no_scale and world == 1:
         from paper_1604_01632_gb300 import scenarios as S
-        for key, (sc2, desc) in (("gas_thread_large", workload("gas_thread_large")),
-                                 ("orifice", (S.orifice(), "orifice 128x128x256 TRT g=1e-5 sigma=2e-3 hole r=6"))):
-            v = fsl.Simulation.from_scenarios([sc2], precision=args.precision, stream=int(stream.cuda_stream))
-            r = measure(v, sc2.n, args.precision, 10)
-            r.update({"workload": desc, "cells": sc2.n, "storage": args.precision})
+        large = workload("gas_thread_large")
+        runs = (("gas_thread_large", large, args.precision),
+                ("gas_thread_large_fp32", large, "fp32"),
+                ("orifice", (S.orifice(), "orifice 128x128x256 TRT g=1e-5 sigma=2e-3 hole r=6"), args.precision))
+        for key, (sc2, desc), prec in runs:
+            if prec == args.precision and key.endswith("_fp32"):
+                continue
+            v = fsl.Simulation.from_scenarios([sc2], precision=prec, stream=int(stream.cuda_stream))
+            r = measure(v, sc2.n, prec, 10)
+            r.update({"workload": desc, "cells": sc2.n, "storage": prec})
             at_scale[key] = r
             v.close()
 

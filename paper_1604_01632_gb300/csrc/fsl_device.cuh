@@ -926,6 +926,9 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 #ifndef FSL_IF_CELLS
 #define FSL_IF_CELLS 16   // cells per pass of an FP32-collide interface block
 #endif
+#ifndef FSL_IF_GRID
+#define FSL_IF_GRID 4     // interface blocks per SM in the grid (ifb is two per SM)
+#endif
 #ifndef FSL_IF_MINB
 #define FSL_IF_MINB 6     // resident interface blocks per SM (register bound)
 #endif
@@ -2130,9 +2133,9 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         cudaEventRecord(fork, s);                                                                            \
         cudaStreamWaitEvent(s2, fork, 0);                                                                    \
         if (A.ndom == 1)                                                                                     \
-            k_stream_interface<T, true><<<(unsigned)(2 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                  \
+            k_stream_interface<T, true><<<(unsigned)(FSL_IF_GRID * ifb / 2), FSL_IF_THREADS, 0, s2>>>(A);                  \
         else                                                                                                 \
-            k_stream_interface<T, false><<<(unsigned)(2 * ifb), FSL_IF_THREADS, 0, s2>>>(A);                 \
+            k_stream_interface<T, false><<<(unsigned)(FSL_IF_GRID * ifb / 2), FSL_IF_THREADS, 0, s2>>>(A);                 \
         if (ei) cudaEventRecord(ei, s2);                                                                     \
         if constexpr (Form<T>::shifted) {                                                                    \
             if (A.ndom == 1)                                                                                 \
