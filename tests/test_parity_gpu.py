@@ -246,3 +246,53 @@ def test_rayleigh_plateau_gas_thread_full_size(fsl):
     assert n0 == 1
     assert len(b) == 4
     assert np.allclose(b["volume"], b["volume"].mean(), rtol=1e-3)
+
+
+def test_accuracy_report_reduced_forms(fsl, oracle_mod):
+    """The accuracy figures of the FP32-collide forms against the FP64 oracle on a
+    gas thread of the benchmark's shape at a quarter of its size (128x32x32,
+    R = 4(1 + 0.1 sin(2 pi x/32)), sigma = 5e-3, TRT), 300 steps: relative L2 and
+    L-infinity errors of the pressure p = rho/3 and of the velocity on cells that
+    are fluid on both sides, the worst per-bubble relative volume error, the
+    relative drift of the total liquid mass against the oracle's, and the bubble
+    counts.  Printed as one line per storage form; the asserts are loose bounds
+    (the figures themselves go to the design notes)."""
+    import json
+    sc = S.gas_thread(nx=128, ny=32, nz=32, radius=4.0, wavelength=32.0)
+    o = oracle_mod.Oracle.from_scenario(sc)
+    m0 = o.total_mass()
+    o.step(300)
+    r = oracle_state(o)
+    mo = o.total_mass()
+    rr, ur = macro(r["f"])
+    for precision in ("fp32", "f16s", "bf16s"):
+        sim = fsl.Simulation.from_scenarios([sc], precision=precision)
+        sim.step(300)
+        g = gpu_state(sim)
+        fl = np.isin(r["flags"], (S.LIQUID, S.INTERFACE)) & np.isin(g["flags"], (S.LIQUID, S.INTERFACE))
+        rg, ug = macro(g["f"])
+        pg, pr = rg[fl] / 3.0, rr[fl] / 3.0
+        du = ug[:, fl] - ur[:, fl]
+        umax = np.abs(ur[:, fl]).max()
+        lm = np.isin(g["flags"], (S.LIQUID,))
+        mg = float(rg[lm].sum() + g["mass"][g["flags"] == S.INTERFACE].sum())
+        gb, rb = g["bubbles"], r["bubbles"]
+        dv = 0.0
+        if len(gb) == len(rb):
+            dv = float(np.max(np.abs(np.sort(gb["volume"]) / np.sort(rb["volume"]) - 1.0)))
+        rep = {"storage": precision,
+               "p_rel_l2": float(np.linalg.norm(pg - pr) / np.linalg.norm(pr)),
+               "p_rel_linf": float(np.abs(pg - pr).max() / np.abs(pr).max()),
+               "u_rel_l2": float(np.linalg.norm(du) / max(np.linalg.norm(ur[:, fl]), 1e-300)),
+               "u_linf_over_umax": float(np.abs(du).max() / max(umax, 1e-300)),
+               "bubble_volume_rel_max": dv,
+               "mass_drift_vs_oracle": float((mg - mo) / mo),
+               "oracle_mass_drift": float((mo - m0) / m0),
+               "bubbles_gpu": int(len(gb)), "bubbles_oracle": int(len(rb)),
+               "flag_agreement": float((g["flags"] == r["flags"]).mean())}
+        print("ACCURACY " + json.dumps(rep))
+        assert rep["bubbles_gpu"] == rep["bubbles_oracle"]
+        assert rep["p_rel_linf"] < 1e-2
+        assert rep["bubble_volume_rel_max"] < 2e-2
+        assert abs(rep["mass_drift_vs_oracle"]) < 1e-2
+        sim.close()
