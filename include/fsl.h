@@ -164,11 +164,9 @@ int64_t fsl_labelling_runs(fsl_domain* h);
 fsl_status fsl_set_timing(fsl_domain* h, int32_t on);
 double fsl_stream_collide_ms(const fsl_domain* h);
 
-/* on = 1 (default): fsl_step replays CUDA graphs of one or two steps in which
- * the labelling runs as a conditional node; on = 0: every kernel is a separate
- * launch and the labelling kernels return at once in steps without a trigger
- * (for profilers that cannot look inside graphs with conditional nodes).
- * Results are identical. */
+/* on = 1 (default): fsl_step replays CUDA graphs of one or two steps; on = 0:
+ * every kernel of a step is a separate launch (for per-phase timing and
+ * profilers).  Results are identical. */
 fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
 
 /* Device time per phase of the steps timed since fsl_set_timing(h, 1), summed,

@@ -323,11 +323,11 @@ fsl_status ensure_initial(fsl_domain* h) {
     return FSL_OK;
 }
 
-// One or two steps starting from buffer `start` as one graph.  After each
-// step's conversion kernels a conditional node runs the labelling only when
-// the step set the merge/split trigger (the last conversion kernel sets the
-// condition).  kind 2 brackets the stream-collide kernels with event-record
-// nodes whose events are swapped before every launch.
+// One or two steps starting from buffer `start` as one graph (per step: the
+// stream-collide pair on two captured streams, then the cooperative
+// conversion kernel, which also runs the labelling on trigger steps).  kind 2
+// brackets the stream-collide kernels with event-record nodes whose events
+// are swapped before every launch.
 fsl_status build_graph(fsl_domain* h, int start, int kind) {
     const int nsteps = kind == 0 ? 2 : 1;
     cudaGraph_t G = nullptr;

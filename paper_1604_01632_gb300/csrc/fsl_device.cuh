@@ -1,7 +1,7 @@
 // fsl_device.cuh -- device-side definitions of the GB300 FSLBM library:
 // lattice constants, cell/mark codes, per-domain descriptors, PDF storage
-// forms and the templated per-cell kernels (stream-collide and the second
-// conversion phase) that exist once per storage precision.
+// forms, the stream-collide kernels, the cooperative conversion kernel and
+// the labelling phases, templated on the storage form where they differ.
 //
 // Method: Anderl et al., arXiv:1604.01632.  Equation numbers count the
 // paper's displayed equations in order (Eq. 3 equilibrium, Eqs. 4-5 moments,
@@ -131,9 +131,9 @@ struct StepArgs {
     int ndom;
     int* ilist;                 // interface cells at the start of this step
     int* icount;
-    int* ilist_next;            // interface cells after this step's conversion (C4)
+    int* ilist_next;            // interface cells after this step's conversion (phase D)
     int* icount_next;
-    int* mlist;                 // interface cells marked filled / emptied (K1I)
+    int* mlist;                 // interface cells marked filled / emptied (interface kernel)
     int* mcount;
     int* glist;                 // gas cells that become interface (phase A)
     int* gcount;
@@ -644,7 +644,7 @@ __device__ inline Pull make_pull(const Dom& D, long long g) {
     return p;
 }
 
-// K1L: stream with half-way bounce-back (Eq. 7) and collide (Eq. 6) for
+// Liquid cells: stream with half-way bounce-back (Eq. 7) and collide (Eq. 6) for
 // liquid cells.  Only cells flagged as touching a wall read the types of
 // their neighbours; a liquid cell never touches gas (closed interface layer).
 template <typename T, bool ONE>
@@ -908,7 +908,7 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
     return out;
 }
 
-// K1I: interface cells, from the list of interface cells built at the end of
+// Interface cells: from the list of interface cells built at the end of
 // the previous step.  A block of 128 threads takes 16 cells per pass, eight
 // threads per cell.  Load phase: the 81 fill levels of the curvature stencil
 // (rows along x), and for the directions q, q+8, q+16 the cell's PDFs, the PDF
@@ -1264,8 +1264,9 @@ __device__ inline long long first_marked(const StepArgs& A, const Dom& D, long l
 }
 
 // An interface cell carrying an emptied mark that phase A does not cancel (no
-// filled neighbour).  Written as a test on the marks K1I set, so it holds
-// whether or not another thread has already cleared the cancelled mark.
+// filled neighbour).  Written as a test on the marks the interface kernel
+// set, so it holds whether or not another thread has already cleared the
+// cancelled mark.
 __device__ inline bool still_emptied(const StepArgs& A, const Dom& D, long long w) {
     const uint8_t fw = A.flag[w], mw = A.mark[w];
     const unsigned filled = marked_mask(A, make_cell(D, w), MK_FILLED);   // loaded with w's own
