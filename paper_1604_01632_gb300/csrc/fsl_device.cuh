@@ -720,10 +720,11 @@ __device__ __forceinline__ void liquid_one(const StepArgs& A, long long g, uint8
     }
 }
 
-// One liquid cell per thread (FP32 and FP64 storage).
+// One liquid cell per thread (FP32 and FP64 storage); block `bid` of the
+// liquid part of the stream-collide kernel.
 template <typename T, bool ONE>
-__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 5) k_stream_liquid(StepArgs A) {
-    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+__device__ __forceinline__ void liquid_single(const StepArgs& A, long long bid) {
+    const long long g = bid * FSL_BLOCK + threadIdx.x;
     const uint8_t f = A.flag[g];
     if (ctype(f) != LIQ) return;
     liquid_one<T, ONE>(A, g, f);
@@ -736,12 +737,9 @@ __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 5) k_stream_li
 // liquid one (the other lane's loads stay inside the lattice and its result
 // is dropped).  Both liquid: one 32-bit store per direction.  (Cells 2t and
 // 2t+1 always lie in the same domain: domains start on multiples of 256.)
-#ifndef FSL_LIQ2_MINB
-#define FSL_LIQ2_MINB 3   // resident two-cell liquid blocks per SM (register bound)
-#endif
 template <typename T, bool ONE>
-__global__ void __launch_bounds__(FSL_BLOCK, FSL_LIQ2_MINB) k_stream_liquid2(StepArgs A) {
-    const long long g0 = 2 * ((long long)blockIdx.x * FSL_BLOCK + threadIdx.x);
+__device__ __forceinline__ void liquid_pairs(const StepArgs& A, long long bid) {
+    const long long g0 = 2 * (bid * FSL_BLOCK + threadIdx.x);
     if (g0 >= A.stride) return;
     const unsigned short ff = *(const unsigned short*)(A.flag + g0);
     const uint8_t f0 = (uint8_t)(ff & 0xff), f1 = (uint8_t)(ff >> 8);
@@ -922,18 +920,11 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 // 1/2 div n_hat by central differences of the face normals), collision
 // (Eq. 6), then the filled / emptied marks.  The FP32-collide forms do all of
 // this in FP32 except the cell mass, which accumulates in FP64.
-#define FSL_IF_THREADS 128   // 16 cells per pass, eight threads per cell
-#ifndef FSL_IF_CELLS
-#define FSL_IF_CELLS 16   // cells per pass of an FP32-collide interface block
-#endif
 #ifndef FSL_IF_GRID
-#define FSL_IF_GRID 4     // interface blocks per SM in the grid (ifb is two per SM)
+#define FSL_IF_GRID 2     // interface blocks per SM in the grid (ifb is two per SM)
 #endif
-#ifndef FSL_IF_MINB
-#define FSL_IF_MINB 6     // resident interface blocks per SM (register bound)
-#endif
-template <typename T> struct IfCells {
-    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : FSL_IF_CELLS;
+template <typename T> struct IfCells {   // cells per pass of a 256-thread block
+    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : 32;
 };
 template <typename T>
 struct IfStage {
@@ -967,13 +958,14 @@ __device__ inline void ph_row(int r, int& dy, int& dz) {
     }
 }
 
+// Block `bid` of the `nbl` blocks of the interface part of the stream-collide
+// kernel.
 template <typename T, bool ONE>
-__global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MINB) k_stream_interface(StepArgs A) {
+__device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int nbl, IfStage<T>& sh) {
     using C = typename Form<T>::C;
     constexpr int N = IfCells<T>::n;
-    constexpr int TPC = FSL_IF_THREADS / N;   // threads per cell
-    __shared__ IfStage<T> sh;
-    if (blockIdx.x == 0) {
+    constexpr int TPC = FSL_BLOCK / N;   // threads per cell
+    if (bid == 0) {
         // per-step counters; the previous step's kernels are done with them
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
             if (A.nif[d] > 0) A.pool[d] = 0;   // the pool was shared out last step
@@ -998,7 +990,7 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
     else { phic = A.phif; phtc = A.phitf; }
     const int c = threadIdx.x / TPC;      // cell of this thread in the load and gradient phases
     const int q = threadIdx.x % TPC;
-    for (int i0 = blockIdx.x * N; i0 < cnt; i0 += gridDim.x * N) {
+    for (int i0 = bid * N; i0 < cnt; i0 += nbl * N) {
         // ---------------- load phase: every global load of the thread is
         // issued before the first shared-memory store, so that the phase costs
         // about two memory latencies (the list entry, then everything else)
@@ -1233,6 +1225,21 @@ __global__ void __launch_bounds__(FSL_IF_THREADS, sizeof(T) == 8 ? 4 : FSL_IF_MI
             list_append(A.mlist, A.mcount, mk != MK_NONE, (int)g);
         }
         __syncthreads();
+    }
+}
+
+// The stream-collide step (Eqs. 6, 7, 10, 11) as one kernel: blocks
+// [0, nif) take the interface cells from the list (they are launched first,
+// so they are placed first), the other blocks the liquid cells.
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream(StepArgs A, int nif) {
+    __shared__ IfStage<T> sh;
+    if ((int)blockIdx.x < nif) {
+        interface_cells<T, ONE>(A, (int)blockIdx.x, nif, sh);
+    } else if constexpr (Form<T>::shifted) {
+        liquid_pairs<T, ONE>(A, (long long)blockIdx.x - nif);
+    } else {
+        liquid_single<T, ONE>(A, (long long)blockIdx.x - nif);
     }
 }
 
@@ -2129,29 +2136,17 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
     template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, cudaStream_t s,               \
                                       cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,   \
                                       cudaEvent_t ei) {                                                      \
-        /* liquid cells on s, interface cells on s2 at the same time (disjoint outputs); */                 \
-        /* el / ei (optional) mark the end of each kernel */                                                \
-        cudaEventRecord(fork, s);                                                                            \
-        cudaStreamWaitEvent(s2, fork, 0);                                                                    \
+        /* one kernel: interface blocks first, then the liquid blocks; el / ei */                           \
+        /* (optional) both mark its end */                                                                   \
+        (void)s2; (void)fork; (void)join;                                                                    \
+        const int nif = FSL_IF_GRID * ifb / 2;                                                               \
+        const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                         \
         if (A.ndom == 1)                                                                                     \
-            k_stream_interface<T, true><<<(unsigned)(FSL_IF_GRID * ifb / 2), FSL_IF_THREADS, 0, s2>>>(A);                  \
+            k_stream<T, true><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                          \
         else                                                                                                 \
-            k_stream_interface<T, false><<<(unsigned)(FSL_IF_GRID * ifb / 2), FSL_IF_THREADS, 0, s2>>>(A);                 \
-        if (ei) cudaEventRecord(ei, s2);                                                                     \
-        if constexpr (Form<T>::shifted) {                                                                    \
-            if (A.ndom == 1)                                                                                 \
-                k_stream_liquid2<T, true><<<(unsigned)((nb + 1) / 2), FSL_BLOCK, 0, s>>>(A);                 \
-            else                                                                                             \
-                k_stream_liquid2<T, false><<<(unsigned)((nb + 1) / 2), FSL_BLOCK, 0, s>>>(A);                \
-        } else {                                                                                             \
-            if (A.ndom == 1)                                                                                 \
-                k_stream_liquid<T, true><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                              \
-            else                                                                                             \
-                k_stream_liquid<T, false><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);                             \
-        }                                                                                                    \
+            k_stream<T, false><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                         \
+        if (ei) cudaEventRecord(ei, s);                                                                      \
         if (el) cudaEventRecord(el, s);                                                                      \
-        cudaEventRecord(join, s2);                                                                           \
-        cudaStreamWaitEvent(s, join, 0);                                                                     \
     }                                                                                                        \
     template <> cudaError_t launch_convert<T>(const StepArgs& A, const CclArgs& K, int nb, cudaStream_t s) {\
         cudaLaunchConfig_t cfg = {};                                                                         \
