@@ -40,7 +40,7 @@ METRIC = "FSLBM MLUPS & HBM roofline fraction: FP16-store/batched vs plain FP32/
 UNIT = "MLUPS"
 BYTES = {"fp64": 8, "fp32": 4, "f16s": 2, "bf16s": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "f16s": "f32", "bf16s": "f32"}
-KERNEL = "k_stream_collide"
+KERNEL = "k_stream (stream-collide: interface blocks + liquid blocks)"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1604_01632_gb300", "csrc", f) for f in
                   ("fsl_device.cuh", "fsl_fast.cu", "fsl_core.cu")]
@@ -301,8 +301,8 @@ def run_gpu(args, rank: int, world: int):
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": KERNEL, "algorithmic_bytes_per_launch": int(abytes),
                          "avg_launch_ms": round(k1_avg, 5), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                         "timing": "CUDA events on the launching stream around the concurrent liquid + interface "
-                                   "kernel pair, second timed pass of the same run"},
+                         "timing": "CUDA events on the launching stream around the stream-collide kernel "
+                                   "(liquid and interface blocks), second timed pass of the same run"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "variants": variants, "phase_us_per_step_direct_launch": phases, "batched": batched,
             "at_scale": at_scale,

@@ -283,6 +283,7 @@ template <> struct Form<__half> {
     static constexpr bool shifted = true;
     __device__ static inline float ld_dev(const __half* p) { return __half2float(*p); }
     __device__ static inline void st_dev2(__half* p, float2 v) { *(__half2*)p = __floats2half2_rn(v.x, v.y); }
+    __device__ static inline float2 ld_dev2(const __half* p) { return __half22float2(*(const __half2*)p); }
     __device__ static inline void st_dev(__half* p, float v) { *p = __float2half_rn(v); }
     __device__ static inline float ld(const __half* p, int a) { return weightc<float>(a) + __half2float(*p); }
     __device__ static inline void st(__half* p, int a, float v) { *p = __float2half_rn(v - weightc<float>(a)); }
@@ -292,6 +293,7 @@ template <> struct Form<__nv_bfloat16> {
     static constexpr bool shifted = true;
     __device__ static inline float ld_dev(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     __device__ static inline void st_dev2(__nv_bfloat16* p, float2 v) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(v.x, v.y); }
+    __device__ static inline float2 ld_dev2(const __nv_bfloat16* p) { return __bfloat1622float2(*(const __nv_bfloat162*)p); }
     __device__ static inline void st_dev(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
     __device__ static inline float ld(const __nv_bfloat16* p, int a) {
         return weightc<float>(a) + __bfloat162float(*p);
@@ -752,14 +754,24 @@ __device__ __forceinline__ void liquid_pairs(const StepArgs& A, long long bid) {
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
     float2 d[19];
-    if (!((f0 | f1) & K_WALL)) {
+    if (!((f0 | f1) & K_WALL) && !(D.nx & 1)) {
+        // even nx: the two cells share their row, so for the links along
+        // x = const the two sources are neighbours at an even offset: one
+        // aligned 32-bit load
 #pragma unroll
         for (int a = 0; a < 19; ++a) {
             const unsigned y0 = gi + (unsigned)(P0.ox[1 - cx(a)] + P0.oy[1 - cy(a)] + P0.oz[1 - cz(a)]);
-            const unsigned y1 = gi + 1u + (unsigned)(P1.ox[1 - cx(a)] + P1.oy[1 - cy(a)] + P1.oz[1 - cz(a)]);
-            d[a] = make_float2(Form<T>::ld_dev(src + (a * S + y0)), Form<T>::ld_dev(src + (a * S + y1)));
+            if (cx(a) == 0) {
+                d[a] = Form<T>::ld_dev2(src + (a * S + y0));
+            } else {
+                const unsigned y1 = gi + 1u + (unsigned)(P1.ox[1 - cx(a)] + P1.oy[1 - cy(a)] + P1.oz[1 - cz(a)]);
+                d[a] = make_float2(Form<T>::ld_dev(src + (a * S + y0)), Form<T>::ld_dev(src + (a * S + y1)));
+            }
         }
     } else {
+        // walls, or odd nx (the pair may straddle two rows): every link of
+        // each cell on its own, a wall cell's bounced links chosen without a
+        // branch
         const bool w0 = v0 && (f0 & K_WALL), w1 = v1 && (f1 & K_WALL);
         d[0] = make_float2(Form<T>::ld_dev(src + gi), Form<T>::ld_dev(src + gi + 1u));
 #pragma unroll
