@@ -1423,63 +1423,6 @@ __device__ inline void warp_add(long long* base, int key, long long v) {
     }
 }
 
-// Block-wide forms of warp_add and list_append: one global atomic per block
-// and run of equal keys instead of one per warp.  Every thread of the block
-// must call (the caller's loop is block-uniform); scratch is shared memory.
-struct BlockScratch {
-    long long sum[32];
-    int key[32];
-    int cnt[32];
-    int base[32];
-};
-__device__ inline void block_add(long long* base, int key, long long v, BlockScratch& sc) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    const int k0 = __shfl_sync(full, key, 0);
-    const bool uni = __all_sync(full, key == k0);
-    if (uni) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
-        if (lane == 0) { sc.key[w] = k0; sc.sum[w] = v; }
-    } else {
-        if (key >= 0 && v != 0) atomicAdd((unsigned long long*)&base[key], (unsigned long long)v);
-        if (lane == 0) sc.key[w] = -1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int kr = -1;
-        long long acc = 0;
-        for (int i = 0; i < nw; ++i) {
-            const int k = sc.key[i];
-            if (k < 0) continue;
-            if (k != kr) {
-                if (kr >= 0 && acc != 0) atomicAdd((unsigned long long*)&base[kr], (unsigned long long)acc);
-                kr = k;
-                acc = 0;
-            }
-            acc += sc.sum[i];
-        }
-        if (kr >= 0 && acc != 0) atomicAdd((unsigned long long*)&base[kr], (unsigned long long)acc);
-    }
-    __syncthreads();
-}
-__device__ inline void block_list_append(int* list, int* count, bool pred, int v, BlockScratch& sc) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    const unsigned m = __ballot_sync(full, pred);
-    if (lane == 0) sc.cnt[w] = __popc(m);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tot = 0;
-        for (int i = 0; i < nw; ++i) { sc.base[i] = tot; tot += sc.cnt[i]; }
-        const int b = tot > 0 ? atomicAdd(count, tot) : 0;
-        for (int i = 0; i < nw; ++i) sc.base[i] += b;
-    }
-    __syncthreads();
-    if (pred) list[sc.base[w] + __popc(m & ((1u << lane) - 1u))] = v;
-    __syncthreads();
-}
-
 // 3x3x3 cube around a cell, bit k = (dx+1) + 3 (dy+1) + 9 (dz+1); bit 13 is the
 // centre.  Face or edge neighbours of cube cell k inside the cube, the centre
 // left out (a walk must not pass through the removed cell).
@@ -1623,13 +1566,9 @@ __device__ inline void convert_c_phase(const StepArgs& A) {
 // pool share, phi = m / rho (Eq. 9); converted cells take their new type;
 // bubble volumes change by exact fixed-point differences; the interface list
 // of the next step; reservoir drain; the graph condition of the labelling.
-__device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
+__device__ inline void convert_d_phase(const StepArgs& A) {
     const int ni = *A.icount, ng = *A.gcount, nl = *A.lcount;
     const int total = ni + ng + nl;
-    // one pass over the list: aggregate the atomics over the block (they hit
-    // few addresses); several passes: over the warp only, so that the block's
-    // warps do not wait for one another in every pass
-    const bool blocked = total <= (int)(gridDim.x * blockDim.x);
     const int step = *A.stepno;
     const int stride = gridDim.x * blockDim.x;
     for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
@@ -1718,17 +1657,10 @@ __device__ inline void convert_d_phase(const StepArgs& A, BlockScratch& sc) {
                 keep = true;
             }
         }
-        if (blocked) {
-            block_add(A.vfx, dv != 0 ? key : -1, dv, sc);
-            block_add(A.ncells, ckey, dc, sc);
-            block_add(A.icnt, keep ? d : -1, 1, sc);
-            block_list_append(A.ilist_next, A.icount_next, keep, (int)g, sc);
-        } else {
-            warp_add(A.vfx, dv != 0 ? key : -1, dv);
-            warp_add(A.ncells, ckey, dc);
-            warp_add(A.icnt, keep ? d : -1, 1);
-            list_append(A.ilist_next, A.icount_next, keep, (int)g);
-        }
+        warp_add(A.vfx, dv != 0 ? key : -1, dv);
+        warp_add(A.ncells, ckey, dc);
+        warp_add(A.icnt, keep ? d : -1, 1);
+        list_append(A.ilist_next, A.icount_next, keep, (int)g);
     }
     if (blockIdx.x == 0) {
         // reservoir drain of every domain whose seed cell is still gas or
@@ -2039,7 +1971,6 @@ __device__ inline bool grid_barrier(const StepArgs& A) {
 // the labelling of the triggered domains (Secs. 2.3.1, 2.3.2).
 template <typename T>
 __global__ void __launch_bounds__(FSL_CONV_THREADS, 3) k_convert(StepArgs A, CclArgs K) {
-    __shared__ BlockScratch sc;
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
         if (threadIdx.x == 0) *A.icount_next = 0;
@@ -2049,7 +1980,7 @@ __global__ void __launch_bounds__(FSL_CONV_THREADS, 3) k_convert(StepArgs A, Ccl
     convert_c_phase(A);
     if (!grid_barrier(A)) return;
     const bool relabel = *(volatile int*)A.trig != 0;   // final after phase C
-    convert_d_phase(A, sc);
+    convert_d_phase(A);
     if (!relabel) return;
     if (!grid_barrier(A)) return;
     ccl_init_phase(A, K);
