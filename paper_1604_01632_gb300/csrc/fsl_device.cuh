@@ -1246,6 +1246,7 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
 template <typename T, bool ONE>
 __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream(StepArgs A, int nif) {
     __shared__ IfStage<T> sh;
+    pdl_trigger();   // the conversion kernel may be placed as blocks finish
     if ((int)blockIdx.x < nif) {
         interface_cells<T, ONE>(A, (int)blockIdx.x, nif, sh);
     } else if constexpr (Form<T>::shifted) {
@@ -1971,6 +1972,7 @@ __device__ inline bool grid_barrier(const StepArgs& A) {
 // the labelling of the triggered domains (Secs. 2.3.1, 2.3.2).
 template <typename T>
 __global__ void __launch_bounds__(FSL_CONV_THREADS, 3) k_convert(StepArgs A, CclArgs K) {
+    pdl_wait();   // the stream-collide kernel has finished and its writes are visible
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
         if (threadIdx.x == 0) *A.icount_next = 0;
@@ -2096,11 +2098,13 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         cfg.gridDim = dim3((unsigned)nb);                                                                    \
         cfg.blockDim = dim3(FSL_CONV_THREADS);                                                               \
         cfg.stream = s;                                                                                      \
-        cudaLaunchAttribute at[1];                                                                           \
+        cudaLaunchAttribute at[2];                                                                           \
         at[0].id = cudaLaunchAttributeCooperative;                                                           \
         at[0].val.cooperative = 1;                                                                           \
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;                                       \
+        at[1].val.programmaticStreamSerializationAllowed = 1;                                                \
         cfg.attrs = at;                                                                                      \
-        cfg.numAttrs = 1;                                                                                    \
+        cfg.numAttrs = 2;                                                                                    \
         return cudaLaunchKernelEx(&cfg, k_convert<T>, A, K);                                                 \
     }                                                                                                        \
     template <> int convert_blocks_per_sm<T>() {                                                             \
