@@ -169,9 +169,9 @@ def run_gpu(args, rank: int, world: int):
         sim.sync()
         sim.set_timing(timing)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        c0 = sim.cell_counts(0)   # (its export kernel is not a step kernel)
         l0 = sim.launches
         r0 = sim.labelling_runs
-        c0 = sim.cell_counts(0)
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
