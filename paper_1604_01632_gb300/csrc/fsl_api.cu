@@ -723,9 +723,9 @@ fsl_status fsl_sync(fsl_domain* h) {
             tot += ms;
         }
         h->k1_ms = tot;
-        // direct mode, three phase events per step: the ends of the liquid
-        // and interface kernels (timed from the start of the pair), then the
-        // end of the conversion kernel (timed from the end of the pair)
+        // direct mode, three phase events per step: two at the end of the
+        // stream-collide kernel (timed from its start), then the end of the
+        // conversion kernel (timed from the end of the stream-collide kernel)
         if (h->phused >= 3 && h->phused == 3 * (h->evused / 2)) {
             for (int k = 0; k < 4; ++k) h->phase_ms[k] = 0.0;
             for (size_t n = 0; n < h->evused / 2; ++n) {

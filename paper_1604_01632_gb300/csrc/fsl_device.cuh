@@ -133,7 +133,7 @@ struct StepArgs {
     int* icount;
     int* ilist_next;            // interface cells after this step's conversion (phase D)
     int* icount_next;
-    int* mlist;                 // interface cells marked filled / emptied (interface kernel)
+    int* mlist;                 // interface cells marked filled / emptied (stream-collide kernel)
     int* mcount;
     int* glist;                 // gas cells that become interface (phase A)
     int* gcount;
@@ -943,6 +943,11 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 #ifndef FSL_IF_GRID
 #define FSL_IF_GRID 2     // interface blocks per SM in the grid (ifb is two per SM)
 #endif
+// Interface blocks of the stream-collide grid per SM: FP32 storage moves
+// twice the liquid bytes of the 16-bit forms and gains more from leaving the
+// slots to liquid blocks (1 M-cell gas thread: 53.0 us per step with one, 54.5
+// with two; FP16 storage: 50.9 with two, 52.4 with one or three).
+template <typename T> constexpr int if_grid() { return sizeof(T) == 4 ? 1 : FSL_IF_GRID; }
 template <typename T> struct IfCells {   // cells per pass of a 256-thread block
     static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : 32;
 };
@@ -1289,7 +1294,7 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
 // SHARE, then what is left of the interface list.  SHARE is chosen per handle
 // from the share of interface cells (foams, batches of small domains); the
 // variant without it leaves the liquid blocks' code as short as a pure
-// liquid kernel's (a run-time switch measurably slowed them).
+// liquid-only kernel's (a run-time switch measurably slowed them).
 template <typename T, bool ONE, bool SHARE>
 __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream(StepArgs A, int nif) {
     __shared__ IfStage<T> sh;
@@ -1339,8 +1344,8 @@ __device__ inline long long first_marked(const StepArgs& A, const Dom& D, long l
 }
 
 // An interface cell carrying an emptied mark that phase A does not cancel (no
-// filled neighbour).  Written as a test on the marks the interface kernel
-// set, so it holds whether or not another thread has already cleared the
+// filled neighbour).  Written as a test on the marks the stream-collide
+// kernel set, so it holds whether or not another thread has already cleared the
 // cancelled mark.
 __device__ inline bool still_emptied(const StepArgs& A, const Dom& D, long long w) {
     const uint8_t fw = A.flag[w], mw = A.mark[w];
@@ -2244,7 +2249,7 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
         /* one kernel: interface blocks first, then the liquid blocks, which */                            \
         /* join the interface cells after their own when `share`; el / ei */                                \
         /* (optional) both mark its end */                                                                   \
-        const int nif = FSL_IF_GRID * ifb / 2;                                                               \
+        const int nif = if_grid<T>() * ifb / 2;                                                              \
         const unsigned g = (unsigned)(nif + (Form<T>::shifted ? (nb + 1) / 2 : nb));                         \
         if (A.ndom == 1) {                                                                                   \
             if (share) k_stream<T, true, true><<<g, FSL_BLOCK, 0, s>>>(A, nif);                              \
