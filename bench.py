@@ -260,20 +260,27 @@ def run_gpu(args, rank: int, world: int):
     if not args.no_batched and world == 1:
         batched = run_batched(args, fsl, torch, stream, flush)
 
-    # end to end through the C ABI from host buffers: upload the initial state,
-    # K steps, read back the fields and the bubble table
+    # end to end through the C ABI from pinned host buffers: upload the initial
+    # state, K steps, read back the fields and the bubble table
     e2e = None
     if not args.no_e2e:
-        flags = np.ascontiguousarray(sc.flags.reshape(-1))
-        fill = np.ascontiguousarray(sc.fill.reshape(-1))
-        rho = np.ascontiguousarray(sc.rho.reshape(-1))
-        u = np.ascontiguousarray(sc.u.reshape(-1))
+        def pinned(shape, dtype):
+            t = torch.empty(int(np.prod(shape)), dtype=getattr(torch, np.dtype(dtype).name), pin_memory=True)
+            return t.numpy().reshape(shape)
+        flags, fill = pinned(n, np.uint8), pinned(n, np.float64)
+        rho, u = pinned(n, np.float64), pinned(3 * n, np.float64)
+        np.copyto(flags, sc.flags.reshape(-1))
+        np.copyto(fill, sc.fill.reshape(-1))
+        np.copyto(rho, sc.rho.reshape(-1))
+        np.copyto(u, sc.u.reshape(-1))
+        res = {"flags": pinned(n, np.uint8), "fill": pinned(n, np.float64), "id": pinned(n, np.int64),
+               "rho": pinned(n, np.float64), "u": pinned(3 * n, np.float64)}
         sim = fsl.Simulation([sc.params()], precision=args.precision, stream=int(stream.cuda_stream))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.init_geometry(0, flags, fill, rho, u)
         sim.step(args.steps)
-        out = sim.fields(0, ("flags", "fill", "id", "rho", "u"))
+        out = sim.fields(0, ("flags", "fill", "id", "rho", "u"), out=res)
         bub = sim.bubbles(0)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0

@@ -99,6 +99,8 @@ struct fsl_domain {
     size_t phused = 0;
     double phase_ms[4] = {0, 0, 0, 0};
     std::vector<void*> allocs;
+    void* stage = nullptr;        // device staging of host transfers (init, export), grown on demand
+    size_t stage_bytes = 0;
     std::string err;
 };
 
@@ -145,6 +147,29 @@ int order_effective(const fsl_domain* h) {
 cudaError_t write_order(fsl_domain* h) {
     const unsigned v = (unsigned)order_effective(h);
     return cudaMemcpy(h->bar + 3, &v, sizeof(unsigned), cudaMemcpyHostToDevice);
+}
+
+// Device staging for transfers from or to host buffers: one buffer owned by
+// the handle, grown when a call needs more (freeing the old one waits for the
+// device), so that repeated calls neither allocate nor synchronise the device
+// for an allocation.  parts[i] receives a 256-byte aligned slice of bytes[i].
+cudaError_t staging(fsl_domain* h, const size_t* bytes, int n, void** parts) {
+    size_t tot = 0;
+    for (int i = 0; i < n; ++i) tot += (bytes[i] + 255) / 256 * 256;
+    if (tot > h->stage_bytes) {
+        if (h->stage) cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->stage, tot);
+        if (e != cudaSuccess) return e;
+        h->stage_bytes = tot;
+    }
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        parts[i] = (char*)h->stage + off;
+        off += (bytes[i] + 255) / 256 * 256;
+    }
+    return cudaSuccess;
 }
 
 StepArgs step_args(fsl_domain* h, int src) {
@@ -605,12 +630,12 @@ fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, con
     const size_t n = (size_t)D.n;
     uint8_t* dfl = nullptr;
     double *dfi = nullptr, *drh = nullptr, *du = nullptr;
-    bool staged = !on_device;
-    if (staged) {
-        CK(h, cudaMalloc(&dfl, n));
-        CK(h, cudaMalloc(&dfi, 8 * n));
-        CK(h, cudaMalloc(&drh, 8 * n));
-        CK(h, cudaMalloc(&du, 24 * n));
+    if (!on_device) {
+        CK(h, cudaStreamSynchronize(h->ls));   // queued work first (the copies below are synchronous)
+        const size_t bytes[4] = {n, 8 * n, 8 * n, 24 * n};
+        void* parts[4];
+        CK(h, staging(h, bytes, 4, parts));
+        dfl = (uint8_t*)parts[0]; dfi = (double*)parts[1]; drh = (double*)parts[2]; du = (double*)parts[3];
         CK(h, cudaMemcpy(dfl, flags, n, cudaMemcpyHostToDevice));
         CK(h, cudaMemcpy(dfi, fill, 8 * n, cudaMemcpyHostToDevice));
         CK(h, cudaMemcpy(drh, rho, 8 * n, cudaMemcpyHostToDevice));
@@ -629,9 +654,6 @@ fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, con
     h->launches += 1;
     CK(h, cudaGetLastError());
     CK(h, cudaStreamSynchronize(h->ls));
-    if (staged) {
-        cudaFree(dfl); cudaFree(dfi); cudaFree(drh); cudaFree(du);
-    }
     fsl_status st = latch(h);
     if (st != FSL_OK) return st;
     h->inited[d] = true;
@@ -857,22 +879,25 @@ fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst,
         st = compute_minidx(h, d);
         if (st != FSL_OK) return st;
     }
-    // device targets: the caller's buffers, or temporaries copied out after
+    // device targets: the caller's buffers, or slices of the staging buffer
+    // copied out after (the previous calls on the handle's stream, which may
+    // read the staging buffer, are done: every call ends synchronised)
     size_t sizes[7] = {n, 8 * n, 8 * n, 8 * n, 8 * n, 24 * n, 152 * n};
     void* dev[7] = {nullptr};
-    std::vector<void*> tmp;
-    int k = 0;
-    for (int bit = 0; bit < 7; ++bit) {
-        if (!(mask & (1u << bit))) continue;
-        if (on_device) {
-            dev[bit] = dst[k];
-        } else {
-            void* p = nullptr;
-            CK(h, cudaMalloc(&p, sizes[bit]));
-            tmp.push_back(p);
-            dev[bit] = p;
-        }
-        ++k;
+    if (on_device) {
+        int k = 0;
+        for (int bit = 0; bit < 7; ++bit)
+            if (mask & (1u << bit)) dev[bit] = dst[k++];
+    } else {
+        size_t want[7];
+        void* parts[7];
+        int m = 0;
+        for (int bit = 0; bit < 7; ++bit)
+            if (mask & (1u << bit)) want[m++] = sizes[bit];
+        CK(h, staging(h, want, m, parts));
+        m = 0;
+        for (int bit = 0; bit < 7; ++bit)
+            if (mask & (1u << bit)) dev[bit] = parts[m++];
     }
     if (mask & (FSL_F_FLAGS | FSL_F_FILL | FSL_F_MASS | FSL_F_ID)) {
         launch_export_cells(h->flag, h->phi, h->m, h->id, h->minidx, D.off, D.n, (uint8_t*)dev[0], (double*)dev[1],
@@ -890,7 +915,7 @@ fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst,
     }
     CK(h, cudaGetLastError());
     if (!on_device) {
-        k = 0;
+        int k = 0;
         for (int bit = 0; bit < 7; ++bit) {
             if (!(mask & (1u << bit))) continue;
             CK(h, cudaMemcpyAsync(dst[k], dev[bit], sizes[bit], cudaMemcpyDeviceToHost, h->ls));
@@ -898,7 +923,6 @@ fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst,
         }
     }
     CK(h, cudaStreamSynchronize(h->ls));
-    for (void* p : tmp) cudaFree(p);
     join_out(h);
     return latch(h);
 }
@@ -930,6 +954,7 @@ fsl_status fsl_destroy(fsl_domain* h) {
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
     for (cudaEvent_t e : h->phpool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->stage) cudaFree(h->stage);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ls) cudaStreamDestroy(h->ls);

@@ -231,21 +231,31 @@ class Simulation:
             out[k] = (b.id, b.volume, b.init_volume, b.pressure, b.n_cells, b.const_pressure, b.extra_volume)
         return out
 
-    def fields(self, d: int = 0, names: Iterable[str] = ("flags", "fill", "mass", "id", "pdf")) -> Dict[str, np.ndarray]:
+    def fields(self, d: int = 0, names: Iterable[str] = ("flags", "fill", "mass", "id", "pdf"),
+               out: Optional[Dict[str, np.ndarray]] = None) -> Dict[str, np.ndarray]:
+        """Selected fields of domain d in host arrays; `out` may supply some of
+        them (C-contiguous, of the field's dtype and size, e.g. views of pinned
+        host memory), the others are allocated."""
         names = [k for k in FIELD_BITS if k in set(names)]
         n = self.n(d)
-        out = {}
+        res = {}
         mask = 0
         ptrs = []
         for k in names:
             dt, m = FIELD_DTYPES[k]
-            a = np.empty(m * n, dtype=dt)
-            out[k] = a if m == 1 else a.reshape(m, n)
+            if out is not None and k in out:
+                a = out[k]
+                if a.dtype != dt or a.size != m * n or not a.flags.c_contiguous:
+                    raise ValueError(f"out[{k!r}] must be a C-contiguous {np.dtype(dt)} array of {m * n} elements")
+                a = a.reshape(-1)
+            else:
+                a = np.empty(m * n, dtype=dt)
+            res[k] = a if m == 1 else a.reshape(m, n)
             mask |= FIELD_BITS[k]
             ptrs.append(a.ctypes.data)
         arr = (ctypes.c_void_p * max(len(ptrs), 1))(*ptrs)
         self._check(self.L.fsl_fields(self._h, d, mask, ctypes.cast(arr, ctypes.c_void_p), 0))
-        return out
+        return res
 
     def fields_to(self, d: int, dst: Dict[str, "object"]):
         """Write selected fields into caller-owned device buffers (torch tensors)."""
