@@ -169,25 +169,6 @@ double fsl_stream_collide_ms(const fsl_domain* h);
  * profilers).  Results are identical. */
 fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
 
-/* Order of the interface list (an implementation device; the paper keeps no
- * list of interface cells).  mode 1: after the cell conversion of every step
- * the conversion kernel rebuilds the list of the next step's interface cells
- * in increasing cell index from the cell types (two passes over the types,
- * two more grid barriers), so that the stream-collide kernel, which takes the
- * list in order, has neighbouring cells in flight together and reads their
- * shared neighbour data from L2 instead of DRAM.  mode 0: the list is the one
- * the conversion appends, in the order its warps finish.  mode -1 (default):
- * when the PDF arrays read and written by a step exceed twice the device's L2
- * cache, the kernel rebuilds the list on the steps that start with more than
- * 1/16 of the cells in the interface (the rebuild reads every cell type
- * twice, the saving grows with the interface cells), else never.  Results
- * are identical in every mode.  Waits for the handle's queued work; takes
- * effect from the next step, also in graphs.  FSL_ERR_ARG for another mode.
- * fsl_interface_order returns the rule in effect: 0 never, 1 every step, 2
- * by the interface share; -1 for a null handle. */
-fsl_status fsl_set_interface_order(fsl_domain* h, int32_t mode);
-int32_t fsl_interface_order(const fsl_domain* h);
-
 /* Device time per phase of the steps timed since fsl_set_timing(h, 1), summed,
  * in milliseconds, when the handle runs without graphs (fsl_set_graphs(h, 0)):
  * out (array of 4): [0] stream-collide kernel (liquid and interface cells in

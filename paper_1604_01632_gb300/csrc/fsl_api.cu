@@ -30,13 +30,11 @@ struct fsl_domain {
     size_t fbytes = 8;            // bytes per stored PDF
     cudaStream_t user = nullptr;  // caller's stream (may be the legacy default)
     cudaStream_t ls = nullptr;    // library stream (capturable)
+    cudaStream_t ls3 = nullptr;   // interface kernels, concurrent with the liquid kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     int ifblocks = 304;           // grid of the list kernels (2 blocks per SM)
     int convblocks = 152;         // grid of the cooperative conversion kernel
-    int order_mode = -1;          // interface list in cell order: 1 on, 0 off, -1 by lattice size
-    bool share_if = false;        // liquid blocks join the interface cells (set at the first step)
-    long long l2bytes = 0;        // L2 cache of the device
-    int* ocnt = nullptr;          // interface cells per conversion block (ordered list)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
     std::vector<Dom> hdoms;
@@ -61,8 +59,7 @@ struct fsl_domain {
     long long *pool = nullptr, *nif = nullptr;
     int* trig = nullptr;
     int* status = nullptr;
-    unsigned* bar = nullptr;      // grid barrier of the conversion kernel (count, generation),
-                                  // then the stream-collide kernel's interface-chunk queue
+    unsigned* bar = nullptr;      // grid barrier of the conversion kernel
     int* ilist[2] = {nullptr, nullptr};   // interface list read by a step starting from buffer k
     int* icount[2] = {nullptr, nullptr};
     int *mlist = nullptr, *mcount = nullptr, *glist = nullptr, *gcount = nullptr, *llist = nullptr, *lcount = nullptr;
@@ -132,23 +129,6 @@ cudaError_t dalloc(fsl_domain* h, P** p, size_t bytes) {
     return e;
 }
 
-// Whether the conversion kernel rebuilds the interface list in cell order:
-// 0 never, 1 every step, 2 on the steps that start with more than 1/16 of the
-// cells in the interface (decided by the kernel).  By default 2 when the two
-// PDF arrays of a step (read and written) exceed twice the L2 cache, where
-// the interface cells' neighbour data would otherwise be fetched from DRAM
-// again for every cell that reads it, else 0; the rebuild reads every cell
-// type twice, so it pays where interface cells are a large share.
-int order_effective(const fsl_domain* h) {
-    if (h->order_mode >= 0) return h->order_mode;
-    const double pdf_bytes = 2.0 * 19.0 * (double)h->stride * (double)h->fbytes;
-    return h->l2bytes > 0 && pdf_bytes > 2.0 * (double)h->l2bytes ? 2 : 0;
-}
-cudaError_t write_order(fsl_domain* h) {
-    const unsigned v = (unsigned)order_effective(h);
-    return cudaMemcpy(h->bar + 3, &v, sizeof(unsigned), cudaMemcpyHostToDevice);
-}
-
 // Device staging for transfers from or to host buffers: one buffer owned by
 // the handle, grown when a call needs more (freeing the old one waits for the
 // device), so that repeated calls neither allocate nor synchronise the device
@@ -199,9 +179,6 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.trig = h->trig;
     A.status = h->status;
     A.bar = h->bar;
-    A.ifq = (int*)(h->bar + 2);
-    A.order = (const int*)(h->bar + 3);
-    A.ocnt = h->ocnt;
     A.ndom = h->ndom;
     A.ilist = h->ilist[src];
     A.icount = h->icount[src];
@@ -252,10 +229,10 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
 
 void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st, cudaEvent_t el = nullptr, cudaEvent_t ei = nullptr) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, h->share_if, st, el, ei); break;
-    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, h->share_if, st, el, ei); break;
-    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, h->share_if, st, el, ei); break;
-    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, h->share_if, st, el, ei); break;
+    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
+    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
+    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
+    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
     }
 }
 
@@ -368,12 +345,6 @@ fsl_status ensure_initial(fsl_domain* h) {
     launch_build_ilist(A, h->nblocks, h->ls);
     h->launches += 1;
     CK(h, cudaGetLastError());
-    // where interface cells are more than 1/16 of the cells, the liquid blocks
-    // of the stream-collide kernel take part of them after their own cells
-    int ni = 0;
-    CK(h, cudaMemcpyAsync(&ni, h->icount[h->cur], sizeof(int), cudaMemcpyDeviceToHost, h->ls));
-    CK(h, cudaStreamSynchronize(h->ls));
-    h->share_if = 16LL * ni > h->stride;
     h->need_initial_ccl = false;
     return FSL_OK;
 }
@@ -494,6 +465,16 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
 
     cudaError_t e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
+        // the interface kernel is a short latency-bound chain: give its stream
+        // the highest priority so that its blocks are placed before the
+        // liquid kernel's
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        e = cudaStreamCreateWithPriority(&h->ls3, cudaStreamNonBlocking, hi);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -504,9 +485,6 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         const int per_sm = conv_blocks_per_sm(precision);
         if (per_sm < 1) e = cudaErrorInvalidConfiguration;
         h->convblocks = std::max(1, sms) * std::max(1, per_sm);
-        int l2 = 0;
-        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-        h->l2bytes = l2;
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
@@ -538,8 +516,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->nif, 8 * n_domains);
     AL(h->trig, sizeof(int) * (n_domains + 1));
     AL(h->status, sizeof(int));
-    AL(h->bar, 4 * sizeof(unsigned));
-    AL(h->ocnt, sizeof(int) * h->convblocks);
+    AL(h->bar, 2 * sizeof(unsigned));
     AL(h->ilist[0], 4 * N);
     AL(h->ilist[1], 4 * N);
     AL(h->icount[0], sizeof(int));
@@ -597,8 +574,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->nif, 0, 8 * n_domains);
     if (e == cudaSuccess) e = cudaMemset(h->trig, 0, sizeof(int) * (n_domains + 1));
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(h->bar, 0, 4 * sizeof(unsigned));
-    if (e == cudaSuccess) e = write_order(h);
+    if (e == cudaSuccess) e = cudaMemset(h->bar, 0, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(h->icount[0], 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->icount[1], 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->mcount, 0, sizeof(int));
@@ -791,16 +767,6 @@ fsl_status fsl_set_graphs(fsl_domain* h, int32_t on) {
     return FSL_OK;
 }
 
-fsl_status fsl_set_interface_order(fsl_domain* h, int32_t mode) {
-    if (!h || mode < -1 || mode > 1) return FSL_ERR_ARG;
-    CK(h, cudaStreamSynchronize(h->ls));
-    h->order_mode = mode;
-    CK(h, write_order(h));
-    return FSL_OK;
-}
-
-int32_t fsl_interface_order(const fsl_domain* h) { return h ? order_effective(h) : -1; }
-
 int64_t fsl_kernel_launches(const fsl_domain* h) { return h ? h->launches : 0; }
 
 int64_t fsl_labelling_runs(fsl_domain* h) {
@@ -958,6 +924,9 @@ fsl_status fsl_destroy(fsl_domain* h) {
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ls) cudaStreamDestroy(h->ls);
+    if (h->ls3) cudaStreamDestroy(h->ls3);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return FSL_OK;
 }

@@ -133,7 +133,7 @@ struct StepArgs {
     int* icount;
     int* ilist_next;            // interface cells after this step's conversion (phase D)
     int* icount_next;
-    int* mlist;                 // interface cells marked filled / emptied (stream-collide kernel)
+    int* mlist;                 // interface cells marked filled / emptied (interface kernel)
     int* mcount;
     int* glist;                 // gas cells that become interface (phase A)
     int* gcount;
@@ -144,14 +144,6 @@ struct StepArgs {
     int* stepno;                // device step counter
     long long* icnt;            // per-domain interface count at the end of the step
     unsigned* bar;              // grid barrier of the conversion kernel: count, generation
-    int* ifq;                   // interface chunks handed out beyond the first nif this step
-                                // (zero when the stream-collide kernel starts: the
-                                // conversion kernel resets it)
-    const int* order;           // the conversion kernel rebuilds the interface list in cell
-                                // order: 1 every step, 2 when more than 1/16 of the cells
-                                // are interface cells, 0 never (device value, so that
-                                // graphs follow changes)
-    int* ocnt;                  // interface cells per conversion block (list rebuild)
     Dom d0;                     // domain 0, read from the parameter space when ndom == 1
 };
 
@@ -943,11 +935,6 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 #ifndef FSL_IF_GRID
 #define FSL_IF_GRID 2     // interface blocks per SM in the grid (ifb is two per SM)
 #endif
-// Interface blocks of the stream-collide grid per SM: FP32 storage moves
-// twice the liquid bytes of the 16-bit forms and gains more from leaving the
-// slots to liquid blocks (1 M-cell gas thread: 53.0 us per step with one, 54.5
-// with two; FP16 storage: 50.9 with two, 52.4 with one or three).
-template <typename T> constexpr int if_grid() { return sizeof(T) == 4 ? 1 : FSL_IF_GRID; }
 template <typename T> struct IfCells {   // cells per pass of a 256-thread block
     static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : 32;
 };
@@ -959,16 +946,13 @@ struct IfStage {
     C fs[N][19];       // own post-collision PDFs of the previous step
     C fy[N][19];       // PDF streaming in from the source cell
     C fin[N][19];      // PDFs after streaming and reconstruction
-    C ex[N][19];       // mass-exchange term of each link (Eq. 10); until the
-                       // gradient phase, the fill level of the link's neighbour
+    C ex[N][19];       // mass-exchange term of each link (Eq. 10)
     C nrm[N][7][3];    // gradient at the cell, unit normals at the face neighbours
     C pv[N];           // bubble pressure (Eq. 13)
-    C px[N];           // fill level of the cell
     double m[N];       // mass
     int g[N];          // cell
-    int next;          // the block's next chunk of the interface list
-    int first;         // a liquid block's first chunk
-    uint8_t tz[N][19]; // type of the neighbour x + c_a (the source of direction opp(a))
+    uint8_t ty[N][19];
+    uint8_t tz[N][19];
 };
 
 __device__ inline int ph_index(int dx, int dy, int dz) { return (dx + 2) + 5 * (dy + 2) + 25 * (dz + 2); }
@@ -986,11 +970,8 @@ __device__ inline void ph_row(int r, int& dy, int& dz) {
     }
 }
 
-// The interface part of the stream-collide kernel.  The interface list is cut
-// into chunks of N cells; interface block `bid` (of nbl) takes chunk bid, then
-// chunks nbl, nbl + 1, ... from a counter; in the sharing variant a liquid
-// block (bid < 0) joins the counter once its own cells are done, so that all
-// resident blocks work on the interface cells when they are a large share.
+// Block `bid` of the `nbl` blocks of the interface part of the stream-collide
+// kernel.
 template <typename T, bool ONE>
 __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int nbl, IfStage<T>& sh) {
     using C = typename Form<T>::C;
@@ -1011,13 +992,6 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
         }
     }
     const int cnt = *A.icount;
-    const int nch = (cnt + N - 1) / N;
-    int ch = bid;
-    if (bid < 0) {
-        if (threadIdx.x == 0) sh.first = nbl + atomicAdd(A.ifq, 1);
-        __syncthreads();
-        ch = sh.first;
-    }
     const unsigned S = (unsigned)A.stride;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
@@ -1028,18 +1002,12 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
     else { phic = A.phif; phtc = A.phitf; }
     const int c = threadIdx.x / TPC;      // cell of this thread in the load and gradient phases
     const int q = threadIdx.x % TPC;
-    // list entry of this thread's cell in the chunk being processed; the next
-    // chunk's entry is read during the pass
-    int gcur = ch < nch && ch * N + c < cnt ? A.ilist[ch * N + c] : 0;
-    while (ch < nch) {
-        const int i0 = ch * N;
-        int nxt = 0;
-        if (threadIdx.x == 0) nxt = nbl + atomicAdd(A.ifq, 1);   // used after the loads
+    for (int i0 = bid * N; i0 < cnt; i0 += nbl * N) {
         // ---------------- load phase: every global load of the thread is
         // issued before the first shared-memory store, so that the phase costs
-        // about one memory latency (the list entry was read in the last pass)
+        // about two memory latencies (the list entry, then everything else)
         if (i0 + c < cnt) {
-            const long long g = gcur;
+            const long long g = A.ilist[i0 + c];
             const Dom& D = dom_at<ONE>(A, g);
             const Stencil st = make_stencil(D, g);
             // the 81 stencil points as 21 rows along x: 9 rows |dy|,|dz| <= 1 of
@@ -1068,30 +1036,28 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
                     }
                 }
             }
-            // per direction a: the own PDF, the PDF streaming in from x - c_a,
-            // and type and fill level of x + c_a.  The source x - c_a of
-            // direction a is the neighbour x + c_b of b = opp(a), so the type
-            // of the source and the PDF f_b(x + c_a) of the mass exchange are
-            // the loads of the opposite direction (no cell is read twice).
-            C fsv[ND], fyv[ND], phz[ND];
-            uint8_t tzv[ND];
+            C fsv[ND], fyv[ND], fzv[ND], phz[ND];
+            uint8_t tyv[ND], tzv[ND];
 #pragma unroll
             for (int k = 0; k < ND; ++k) {
                 const int a = q + TPC * k;
                 if (a < 19) {
                     fsv[k] = Form<T>::ld(src + ((unsigned)a * S + (unsigned)g), a);
                     if (a > 0) {
+                        const int ab = opp(a);
                         const int ax = rcx(a), ay = rcy(a), az = rcz(a);
                         const unsigned y = st.at(-ax, -ay, -az);
                         const unsigned z = st.at(ax, ay, az);
+                        tyv[k] = ctype(A.flag[y]);
                         fyv[k] = Form<T>::ld(src + ((unsigned)a * S + y), a);
                         tzv[k] = ctype(A.flag[z]);
+                        fzv[k] = Form<T>::ld(src + ((unsigned)ab * S + z), ab);
                         phz[k] = phic[z];
                     }
                 }
             }
+            const C phx = phic[g];
             if (q == TPC - 1) {
-                sh.px[c] = phic[g];
                 sh.m[c] = A.m[g];
                 sh.g[c] = (int)g;
                 const int bub = A.id[g];
@@ -1120,33 +1086,21 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
                 if (a < 19) {
                     sh.fs[c][a] = fsv[k];
                     if (a > 0) {
+                        sh.ty[c][a] = tyv[k];
                         sh.fy[c][a] = fyv[k];
                         sh.tz[c][a] = tzv[k];
-                        sh.ex[c][a] = phz[k];
+                        if (tzv[k] == LIQ || tzv[k] == IFC) {
+                            const C e = fzv[k] - fsv[k];
+                            sh.ex[c][a] = tzv[k] == IFC ? ((C)0.5 * (phx + phz[k])) * e : e;
+                        }
                     }
                 }
             }
         }
-        // every thread read the previous sh.next before the barriers of the
-        // previous pass
-        if (threadIdx.x == 0) sh.next = nxt;
         __syncthreads();
-        const int chn = sh.next;
-        int gnext = 0;
-        if (chn < nch && chn * N + c < cnt) gnext = A.ilist[chn * N + c];   // used in the next pass
         // ---------------- gradient phase: point j (the cell, then its +x, -x,
-        // +y, -y, +z, -z neighbours) for j = q, q + TPC, ...; before it, the
-        // exchange term of each of the thread's directions a (Eq. 10) from
-        // f_b(x + c_a) - f_a(x), b = opp(a), weighted by the mean fill level
-        // when x + c_a is an interface cell
+        // +y, -y, +z, -z neighbours) for j = q, q + TPC, ...
         if (i0 + c < cnt) {
-            for (int a = q > 0 ? q : TPC; a < 19; a += TPC) {
-                const uint8_t tz = sh.tz[c][a];
-                if (tz == LIQ || tz == IFC) {
-                    const C e = sh.fy[c][opp(a)] - sh.fs[c][a];
-                    sh.ex[c][a] = tz == IFC ? ((C)0.5 * (sh.px[c] + sh.ex[c][a])) * e : e;
-                }
-            }
             for (int j = q; j < 7; j += TPC) {
                 const int ox = j == 1 ? 1 : (j == 2 ? -1 : 0);
                 const int oy = j == 3 ? 1 : (j == 4 ? -1 : 0);
@@ -1206,7 +1160,7 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
                     } else {
                         const int ab = opp(a);
                         const C fsb = sh.fs[c][ab];
-                        const uint8_t ty = sh.tz[c][ab];   // type of x - c_a
+                        const uint8_t ty = sh.ty[c][a];
                         if (ty == OBS) {
                             fin = fsb;
                         } else if (ty == LID) {
@@ -1283,37 +1237,23 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
             list_append(A.mlist, A.mcount, mk != MK_NONE, (int)g);
         }
         __syncthreads();
-        ch = chn;
-        gcur = gnext;
     }
 }
 
 // The stream-collide step (Eqs. 6, 7, 10, 11) as one kernel: blocks
 // [0, nif) take the interface cells from the list (they are launched first,
-// so they are placed first), the other blocks the liquid cells and, with
-// SHARE, then what is left of the interface list.  SHARE is chosen per handle
-// from the share of interface cells (foams, batches of small domains); the
-// variant without it leaves the liquid blocks' code as short as a pure
-// liquid-only kernel's (a run-time switch measurably slowed them).
-template <typename T, bool ONE, bool SHARE>
+// so they are placed first), the other blocks the liquid cells.
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream(StepArgs A, int nif) {
     __shared__ IfStage<T> sh;
     pdl_trigger();   // the conversion kernel may be placed as blocks finish
-    int bid = (int)blockIdx.x;
-    if (bid >= nif) {
-        // the queue counter is read (by one thread) before the liquid cells,
-        // so that the check after them costs no memory round trip; it only
-        // grows, so a value at or past the end is final
-        constexpr int N = IfCells<T>::n;
-        bool left = false;
-        if (SHARE && threadIdx.x == 0) left = nif + *(volatile int*)A.ifq < (*A.icount + N - 1) / N;
-        if constexpr (Form<T>::shifted) liquid_pairs<T, ONE>(A, (long long)bid - nif);
-        else liquid_single<T, ONE>(A, (long long)bid - nif);
-        if constexpr (!SHARE) return;
-        if (!__syncthreads_or(left)) return;
-        bid = -1;
+    if ((int)blockIdx.x < nif) {
+        interface_cells<T, ONE>(A, (int)blockIdx.x, nif, sh);
+    } else if constexpr (Form<T>::shifted) {
+        liquid_pairs<T, ONE>(A, (long long)blockIdx.x - nif);
+    } else {
+        liquid_single<T, ONE>(A, (long long)blockIdx.x - nif);
     }
-    interface_cells<T, ONE>(A, bid, nif, sh);
 }
 
 // First neighbour of cell z (direction order) that is an interface cell
@@ -1344,8 +1284,8 @@ __device__ inline long long first_marked(const StepArgs& A, const Dom& D, long l
 }
 
 // An interface cell carrying an emptied mark that phase A does not cancel (no
-// filled neighbour).  Written as a test on the marks the stream-collide
-// kernel set, so it holds whether or not another thread has already cleared the
+// filled neighbour).  Written as a test on the marks the interface kernel
+// set, so it holds whether or not another thread has already cleared the
 // cancelled mark.
 __device__ inline bool still_emptied(const StepArgs& A, const Dom& D, long long w) {
     const uint8_t fw = A.flag[w], mw = A.mark[w];
@@ -1627,7 +1567,7 @@ __device__ inline void convert_c_phase(const StepArgs& A) {
 // pool share, phi = m / rho (Eq. 9); converted cells take their new type;
 // bubble volumes change by exact fixed-point differences; the interface list
 // of the next step; reservoir drain; the graph condition of the labelling.
-__device__ inline void convert_d_phase(const StepArgs& A, bool order) {
+__device__ inline void convert_d_phase(const StepArgs& A) {
     const int ni = *A.icount, ng = *A.gcount, nl = *A.lcount;
     const int total = ni + ng + nl;
     const int step = *A.stepno;
@@ -1721,7 +1661,7 @@ __device__ inline void convert_d_phase(const StepArgs& A, bool order) {
         warp_add(A.vfx, dv != 0 ? key : -1, dv);
         warp_add(A.ncells, ckey, dc);
         warp_add(A.icnt, keep ? d : -1, 1);
-        if (!order) list_append(A.ilist_next, A.icount_next, keep, (int)g);
+        list_append(A.ilist_next, A.icount_next, keep, (int)g);
     }
     if (blockIdx.x == 0) {
         // reservoir drain of every domain whose seed cell is still gas or
@@ -1738,102 +1678,6 @@ __device__ inline void convert_d_phase(const StepArgs& A, bool order) {
         }
         if (threadIdx.x == 0) *A.mcount = 0;
     }
-}
-
-// ------------------------------------------- interface list in cell order
-// On lattices larger than the L2 cache the interface list of the next step is
-// rebuilt from the cell types after phase D, in increasing cell index.  The
-// stream-collide kernel hands out its chunks in list order, so the cells in
-// flight at any time are close together and share their neighbours' data in
-// L2; the list that phase D appends is in an arbitrary order (warps append in
-// the order they finish).  Block b of the conversion kernel owns the cells
-// [16 lo_b, 16 hi_b) (16 cell types per 16-byte load; the padded lattice is a
-// multiple of 256 cells).
-
-__device__ inline void order_range(const StepArgs& A, long long& lo, long long& hi) {
-    const long long G = A.stride / 16, nb = gridDim.x;
-    lo = G * blockIdx.x / nb;
-    hi = G * (blockIdx.x + 1) / nb;
-}
-
-// Byte masks (0xff per interface cell) of 16 cell types.
-__device__ inline uint4 ifc_masks(const uint8_t* flag, long long j) {
-    const uint4 v = ((const uint4*)flag)[j];
-    uint4 m;
-    m.x = __vcmpeq4(v.x & 0x07070707u, 0x01010101u);
-    m.y = __vcmpeq4(v.y & 0x07070707u, 0x01010101u);
-    m.z = __vcmpeq4(v.z & 0x07070707u, 0x01010101u);
-    m.w = __vcmpeq4(v.w & 0x07070707u, 0x01010101u);
-    return m;
-}
-__device__ inline int ifc_count(const uint4& m) {
-    return (__popc(m.x) + __popc(m.y) + __popc(m.z) + __popc(m.w)) >> 3;
-}
-
-// Exclusive prefix sum of v over the block (blockDim.x a multiple of 32, at
-// most 1024); *total receives the block's sum.  Ends with a barrier.
-__device__ inline int block_exclusive_sum(int v, int* total) {
-    __shared__ int wsum[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int t = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        wsum[lane] = t;   // inclusive sums of the warps
-    }
-    __syncthreads();
-    const int before = w > 0 ? wsum[w - 1] : 0;
-    *total = wsum[nw - 1];
-    __syncthreads();   // wsum may be reused by the next call
-    return before + x - v;
-}
-
-// Pass 1: interface cells of each block's range.
-__device__ inline void order_count_phase(const StepArgs& A) {
-    long long lo, hi;
-    order_range(A, lo, hi);
-    int n = 0;
-    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) n += ifc_count(ifc_masks(A.flag, j));
-    int tot;
-    block_exclusive_sum(n, &tot);
-    if (threadIdx.x == 0) A.ocnt[blockIdx.x] = tot;
-}
-
-// Pass 2: the block's interface cells in order, after those of the blocks
-// before it; the last block stores the list length.
-__device__ inline void order_write_phase(const StepArgs& A) {
-    long long lo, hi;
-    order_range(A, lo, hi);
-    int part = 0;
-    for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) part += A.ocnt[k];
-    int off;
-    block_exclusive_sum(part, &off);
-    for (long long j0 = lo; j0 < hi; j0 += blockDim.x) {
-        const long long j = j0 + threadIdx.x;
-        uint4 m = make_uint4(0u, 0u, 0u, 0u);
-        if (j < hi) m = ifc_masks(A.flag, j);
-        int tot;
-        int pos = off + block_exclusive_sum(ifc_count(m), &tot);
-        const unsigned w[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if ((w[k] >> (8 * b)) & 1u) A.ilist_next[pos++] = (int)(16 * j + 4 * k + b);
-        off += tot;
-    }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *A.icount_next = off;
 }
 
 // Scratch of the connected-component labelling and bubble-table rebuild.
@@ -2131,25 +1975,14 @@ __global__ void __launch_bounds__(FSL_CONV_THREADS, 3) k_convert(StepArgs A, Ccl
     pdl_wait();   // the stream-collide kernel has finished and its writes are visible
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
-        if (threadIdx.x == 0) {
-            *A.icount_next = 0;
-            *A.ifq = 0;   // for the next stream-collide kernel
-        }
+        if (threadIdx.x == 0) *A.icount_next = 0;
     }
     convert_ab_phase<T>(A);
     if (!grid_barrier(A)) return;
     convert_c_phase(A);
     if (!grid_barrier(A)) return;
     const bool relabel = *(volatile int*)A.trig != 0;   // final after phase C
-    const int om = *A.order;
-    const bool order = om == 1 || (om == 2 && 16LL * *A.icount > A.stride);
-    convert_d_phase(A, order);
-    if (order) {
-        if (!grid_barrier(A)) return;
-        order_count_phase(A);
-        if (!grid_barrier(A)) return;
-        order_write_phase(A);
-    }
+    convert_d_phase(A);
     if (!relabel) return;
     if (!grid_barrier(A)) return;
     ccl_init_phase(A, K);
@@ -2234,8 +2067,9 @@ __global__ void k_export_pdf(const T* f, long long S, long long off, int n, doub
 }
 
 // Launch helpers instantiated once per storage form.
-template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, bool share,
-                                         cudaStream_t s, cudaEvent_t el, cudaEvent_t ei);
+template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, cudaStream_t s,
+                                         cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,
+                                         cudaEvent_t ei);
 template <typename T> cudaError_t launch_convert(const StepArgs& A, const CclArgs& K, int nblocks, cudaStream_t s);
 template <typename T> int convert_blocks_per_sm();
 template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
@@ -2244,20 +2078,18 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
                                              double* rho, double* u, cudaStream_t s);
 
 #define FSL_INSTANTIATE_FORM(T)                                                                              \
-    template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, bool share, cudaStream_t s,   \
-                                      cudaEvent_t el, cudaEvent_t ei) {                                      \
-        /* one kernel: interface blocks first, then the liquid blocks, which */                            \
-        /* join the interface cells after their own when `share`; el / ei */                                \
+    template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, cudaStream_t s,               \
+                                      cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,   \
+                                      cudaEvent_t ei) {                                                      \
+        /* one kernel: interface blocks first, then the liquid blocks; el / ei */                           \
         /* (optional) both mark its end */                                                                   \
-        const int nif = if_grid<T>() * ifb / 2;                                                              \
-        const unsigned g = (unsigned)(nif + (Form<T>::shifted ? (nb + 1) / 2 : nb));                         \
-        if (A.ndom == 1) {                                                                                   \
-            if (share) k_stream<T, true, true><<<g, FSL_BLOCK, 0, s>>>(A, nif);                              \
-            else k_stream<T, true, false><<<g, FSL_BLOCK, 0, s>>>(A, nif);                                   \
-        } else {                                                                                             \
-            if (share) k_stream<T, false, true><<<g, FSL_BLOCK, 0, s>>>(A, nif);                             \
-            else k_stream<T, false, false><<<g, FSL_BLOCK, 0, s>>>(A, nif);                                  \
-        }                                                                                                    \
+        (void)s2; (void)fork; (void)join;                                                                    \
+        const int nif = FSL_IF_GRID * ifb / 2;                                                               \
+        const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                         \
+        if (A.ndom == 1)                                                                                     \
+            k_stream<T, true><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                          \
+        else                                                                                                 \
+            k_stream<T, false><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                         \
         if (ei) cudaEventRecord(ei, s);                                                                      \
         if (el) cudaEventRecord(el, s);                                                                      \
     }                                                                                                        \

@@ -29,7 +29,7 @@ FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.flo
 EXPORTS = ["fsl_create", "fsl_init_geometry", "fsl_set_bubble_source", "fsl_step", "fsl_sync", "fsl_bubbles",
            "fsl_fields", "fsl_destroy", "fsl_last_error", "fsl_kernel_launches", "fsl_set_timing",
            "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs",
-           "fsl_label_bubbles_static", "fsl_phase_ms", "fsl_set_interface_order", "fsl_interface_order"]
+           "fsl_label_bubbles_static", "fsl_phase_ms"]
 
 
 class FslError(RuntimeError):
@@ -98,10 +98,6 @@ def load_library():
     L.fsl_phase_ms.argtypes = [vp, vp]
     L.fsl_set_graphs.restype = i32
     L.fsl_set_graphs.argtypes = [vp, i32]
-    L.fsl_set_interface_order.restype = i32
-    L.fsl_set_interface_order.argtypes = [vp, i32]
-    L.fsl_interface_order.restype = i32
-    L.fsl_interface_order.argtypes = [vp]
     L.fsl_labelling_runs.restype = i64
     L.fsl_labelling_runs.argtypes = [vp]
     L.fsl_cell_counts.restype = i32
@@ -286,17 +282,6 @@ class Simulation:
 
     def set_graphs(self, on: bool):
         self._check(self.L.fsl_set_graphs(self._h, 1 if on else 0))
-
-    def set_interface_order(self, mode: int):
-        """1: interface list rebuilt in cell order every step, 0: as appended,
-        -1 (the default): on large lattices, on the steps where more than 1/16
-        of the cells are interface cells.  interface_order reads the rule in
-        effect: 0 never, 1 always, 2 by the interface share."""
-        self._check(self.L.fsl_set_interface_order(self._h, int(mode)))
-
-    @property
-    def interface_order(self) -> int:
-        return int(self.L.fsl_interface_order(self._h))
 
     def phase_ms(self) -> Dict[str, float]:
         out = (ctypes.c_double * 4)()

@@ -3,8 +3,8 @@
 against the oracle on the whole orifice lattice and on sampled domains of the
 population (every domain of the batch runs in one handle; four are compared,
 each against its own oracle).  Then the population in the benchmark's form
-(FP16-shifted storage, CUDA graphs, the interface list rebuilt in cell order)
-on the same sampled domains, within reduced-precision tolerances."""
+(FP16-shifted storage, CUDA graphs) on the same sampled domains, within
+reduced-precision tolerances."""
 import numpy as np
 import pytest
 
@@ -67,7 +67,6 @@ def test_full_size_population_f16s_sampled_domains(fsl, oracle_mod, population):
     and 5e-3 (measured: up to 7e-6 and 4e-4; velocities are at most ~0.02);
     bubble volumes summed over each domain within 1e-3; same bubble count."""
     sim = fsl.Simulation.from_scenarios(population, precision="f16s")
-    assert sim.interface_order == 2
     sim.step(10)
     sim.sync()
     for d in SAMPLE:
