@@ -67,6 +67,23 @@ def algorithmic_bytes(counts, s: int) -> float:
     return n_all * 1.0 + (n_liq + n_if) * 38.0 * s + n_if * 37.0
 
 
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest x over the ranks (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Million lattice-cell updates per second of the whole job: every rank
+    advances its own copy of the lattice, the job lasts as long as the slowest."""
+    return cells_per_rank * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def kernel_sha() -> str:
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
@@ -198,11 +215,8 @@ def run_gpu(args, rank: int, world: int):
     # around it inside each step (a second pass of the same length: the event
     # records add a few microseconds to a step, so they stay out of the headline)
     _, k1_ms, _, _, _ = timed_steps(sim, args.steps, args.warmup, timing=True)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n * args.steps * world / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = whole_job_mlups(n, args.steps, world, ms_max)
     s = BYTES[args.precision]
     abytes = algorithmic_bytes(counts, s)
     k1_avg = k1_ms / args.steps
