@@ -30,8 +30,6 @@ struct fsl_domain {
     size_t fbytes = 8;            // bytes per stored PDF
     cudaStream_t user = nullptr;  // caller's stream (may be the legacy default)
     cudaStream_t ls = nullptr;    // library stream (capturable)
-    cudaStream_t ls3 = nullptr;   // interface kernels, concurrent with the liquid kernel
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     int ifblocks = 304;           // grid of the list kernels (2 blocks per SM)
     int convblocks = 152;         // grid of the cooperative conversion kernel
@@ -229,10 +227,10 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
 
 void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st, cudaEvent_t el = nullptr, cudaEvent_t ei = nullptr) {
     switch (h->precision) {
-    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
-    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
-    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
-    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st, h->ls3, h->ev_fork, h->ev_join, el, ei); break;
+    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
+    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
+    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
+    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
     }
 }
 
@@ -464,16 +462,6 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     h->hcap = hc;
 
     cudaError_t e = cudaStreamCreateWithFlags(&h->ls, cudaStreamNonBlocking);
-    if (e == cudaSuccess) {
-        // the interface kernel is a short latency-bound chain: give its stream
-        // the highest priority so that its blocks are placed before the
-        // liquid kernel's
-        int lo = 0, hi = 0;
-        cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        e = cudaStreamCreateWithPriority(&h->ls3, cudaStreamNonBlocking, hi);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
@@ -924,9 +912,6 @@ fsl_status fsl_destroy(fsl_domain* h) {
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ls) cudaStreamDestroy(h->ls);
-    if (h->ls3) cudaStreamDestroy(h->ls3);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return FSL_OK;
 }
