@@ -111,9 +111,12 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
 /* Load the initial state of domain d (paper Sec. 2.2): cell types, fill
  * levels (interface cells), density and velocity; f = f_eq(rho, u), m = phi
  * rho.  Pointers are host memory (on_device = 0) or device memory on the
- * handle's GPU (on_device = 1).  Rejects (FSL_ERR_GEOMETRY) a liquid cell with
- * a gas neighbour.  Every domain must be initialised before the first step;
- * bubbles are found (flood fill, paper Sec. 2.3.2) with V* = V, p = p0. */
+ * handle's GPU (on_device = 1); the caller keeps them.  Host data pass through
+ * a device staging buffer owned by the handle, allocated on first use and
+ * grown when a call needs more (FSL_ERR_CUDA when that fails).  Rejects
+ * (FSL_ERR_GEOMETRY) a liquid cell with a gas neighbour.  Every domain must be
+ * initialised before the first step; bubbles are found (flood fill, paper Sec.
+ * 2.3.2) with V* = V, p = p0.  Synchronises. */
 fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, const double* fill,
                              const double* rho, const double* u, int32_t on_device);
 
@@ -138,8 +141,11 @@ fsl_status fsl_sync(fsl_domain* h);
  * the number of bubbles to *count.  Synchronises. */
 fsl_status fsl_bubbles(fsl_domain* h, int32_t d, fsl_bubble* out, int64_t cap, int64_t* count);
 
-/* Copy the fields selected by mask of domain d into dst[0..], host memory
- * (on_device = 0) or device memory (on_device = 1).  Synchronises. */
+/* Copy the fields selected by mask of domain d into dst[0..] (one pointer per
+ * selected field, in bit order; caller-owned), host memory (on_device = 0) or
+ * device memory (on_device = 1).  Host copies go through the handle's device
+ * staging buffer (grown when needed; FSL_ERR_CUDA when that fails).
+ * Synchronises. */
 fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst, int32_t on_device);
 
 /* Free the handle and its device memory. */
