@@ -204,8 +204,10 @@ fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts);
  * (8 MiB) compiled into the library, held by every GPU that loads it until the
  * process exits.  nx*ny*nz above 2^21 returns FSL_ERR_ARG.  The first call on
  * a device looks up the scratch's device address (cudaGetSymbolAddress with
- * that device current) and caches it; make that first call before any stream
- * capture.  All calls on a device share the scratch, and each call rewrites it
+ * that device current) and caches it for the life of the process (safe from
+ * several host threads); make that first call before any stream capture.  A
+ * cudaDeviceReset invalidates the cached address: do not call this entry
+ * point on a device after resetting it.  All calls on a device share the scratch, and each call rewrites it
  * from the start; calls whose kernels overlap on the GPU (different streams,
  * not ordered) race and give wrong labels. */
 fsl_status fsl_label_bubbles_static(const uint8_t* flags, int32_t nx, int32_t ny, int32_t nz, int64_t* labels,

@@ -67,6 +67,21 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The OpenMP build (-fopenmp) runs the per-cell loops whose iterations touch
+ * disjoint cells in parallel; its only reductions are integer counts and the
+ * fixed-point pool, so it gives the serial build's results bit for bit.  The
+ * serial build compiles these to nothing. */
+#ifdef _OPENMP
+#define FSL_ORA_PRAGMA(x) _Pragma(#x)
+#define FSL_ORA_PARALLEL_FOR FSL_ORA_PRAGMA(omp parallel for schedule(static))
+#define FSL_ORA_PARALLEL_FOR_SUM(a, b, c) FSL_ORA_PRAGMA(omp parallel for schedule(static) reduction(+ : a, b, c))
+#define FSL_ORA_ATOMIC_WRITE FSL_ORA_PRAGMA(omp atomic write)
+#else
+#define FSL_ORA_PARALLEL_FOR
+#define FSL_ORA_PARALLEL_FOR_SUM(a, b, c)
+#define FSL_ORA_ATOMIC_WRITE
+#endif
+
 enum { LIQ = 0, IFC = 1, GAS = 2, OBS = 3, LID = 4 };
 enum { MK_NONE = 0, MK_FILLED = 1, MK_EMPTIED = 2, MK_NEWG = 3, MK_NEWL = 4 };
 
@@ -542,6 +557,7 @@ static void step_once(ora_sim* s) {
 
     /* S1: stream with bounce-back (Eq. 7), mass exchange (Eq. 10),
      * reconstruction (Eq. 11), collision (Eq. 6), fill level and marks. */
+    FSL_ORA_PARALLEL_FOR
     for (int64_t i = 0; i < n; ++i) {
         uint8_t t = s->flag[i];
         if (t != LIQ && t != IFC) continue;
@@ -571,6 +587,7 @@ static void step_once(ora_sim* s) {
                 fin[a] = F[(size_t)ab * n + i] + (6.0 * weight(a)) * cuw;
             } else if (ty == GAS) {
                 if (t == LIQ) {
+                    FSL_ORA_ATOMIC_WRITE
                     s->status = -2;
                     fin[a] = F[(size_t)ab * n + i];
                 } else {
@@ -596,7 +613,10 @@ static void step_once(ora_sim* s) {
             mnew = s->m[i] + dm;
         }
         double rho = collide_rates(s->omp, s->omm, P->g, fin, fout);
-        if (!(rho == rho)) s->status = -4;
+        if (!(rho == rho)) {
+            FSL_ORA_ATOMIC_WRITE
+            s->status = -4;
+        }
         for (int a = 0; a < 19; ++a) FN[(size_t)a * n + i] = fout[a];
         s->mark[i] = MK_NONE;
         if (t == IFC) {
@@ -619,6 +639,7 @@ static void step_once(ora_sim* s) {
             }
         }
     }
+    FSL_ORA_PARALLEL_FOR
     for (int64_t i = 0; i < n; ++i) {
         uint8_t t = s->flag[i];
         if (t != LIQ && t != IFC) s->mark[i] = MK_NONE;
@@ -642,6 +663,7 @@ static void step_once(ora_sim* s) {
     /* S3: conversion phase B -- remaining emptied cells turn their liquid
      * neighbours into interface; new interface cells from gas are
      * initialised from their liquid/interface neighbours. */
+    FSL_ORA_PARALLEL_FOR
     for (int64_t i = 0; i < n; ++i) {
         if (s->flag[i] != LIQ) continue;
         /* the new interface cell joins the bubble of its first emptied
@@ -661,6 +683,7 @@ static void step_once(ora_sim* s) {
             s->rhoi[i] = r;
         }
     }
+    FSL_ORA_PARALLEL_FOR
     for (int64_t i = 0; i < n; ++i) {
         if (s->flag[i] != GAS || s->mark[i] != MK_NEWG) continue;
         double sr = 0.0, su[3] = {0.0, 0.0, 0.0};
@@ -691,6 +714,8 @@ static void step_once(ora_sim* s) {
     /* S4: excess mass of converted cells, shares for the receivers. */
     int64_t n_if = 0;
     int64_t conv = 0;
+    int64_t pooled = 0;   /* integer sums: the same in any order */
+    FSL_ORA_PARALLEL_FOR_SUM(n_if, conv, pooled)
     for (int64_t i = 0; i < n; ++i) {
         uint8_t t = s->flag[i], mk = s->mark[i];
         if (new_type(t, mk) == IFC) ++n_if;
@@ -703,14 +728,16 @@ static void step_once(ora_sim* s) {
             if (new_type(s->flag[z], s->mark[z]) == IFC) ++k;
         }
         if (k > 0) s->exs[i] = mex / (double)k;
-        else s->pool_fx += llrint(mex * 1099511627776.0);
+        else pooled += llrint(mex * 1099511627776.0);
     }
+    s->pool_fx += pooled;
     s->conversions = conv;
 
     /* S5: receivers pull the shares in direction order, add the pool share,
      * and refresh the fill level phi = m / rho (Eq. 9). */
     double share = 0.0;
     if (n_if > 0) share = ((double)s->pool_fx * ldexp(1.0, -40)) / (double)n_if;
+    FSL_ORA_PARALLEL_FOR
     for (int64_t i = 0; i < n; ++i) {
         if (new_type(s->flag[i], s->mark[i]) != IFC) continue;
         double sm = s->m[i];
@@ -721,6 +748,7 @@ static void step_once(ora_sim* s) {
         if (n_if > 0) sm = sm + share;
         s->exs[i] = sm;   /* staged: flags are still needed by other cells */
     }
+    FSL_ORA_PARALLEL_FOR
     for (int64_t i = 0; i < n; ++i) {
         uint8_t t = s->flag[i], mk = s->mark[i];
         int nt = new_type(t, mk);

@@ -14,18 +14,33 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "fsl_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11"]
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
+    return _build(LIB, [], force)
+
+
+def build_openmp(force: bool = False):
+    """The same source compiled with -fopenmp: per-cell loops in parallel over
+    the host cores, bit-identical results (integer reductions only).  None if
+    the compiler has no OpenMP support."""
+    try:
+        return _build(LIB_OMP, ["-fopenmp"], force)
+    except (subprocess.CalledProcessError, OSError):
+        return None
+
+
+def _build(lib_path: str, extra, force: bool) -> str:
+    if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "fsl_oracle.h"))):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+        tmp = lib_path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, *extra, "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 class Params(ctypes.Structure):
@@ -41,45 +56,50 @@ class Bubble(ctypes.Structure):
                 ("pad", ctypes.c_int32)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = ctypes.CDLL(build())
-        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-        L.ora_create.restype = vp
-        L.ora_create.argtypes = [ctypes.POINTER(Params)]
-        L.ora_destroy.argtypes = [vp]
-        L.ora_init.restype = ctypes.c_int
-        L.ora_init.argtypes = [vp, vp, vp, vp, vp]
-        L.ora_set_source.restype = ctypes.c_int
-        L.ora_set_source.argtypes = [vp, i64, dbl, dbl, i32]
-        L.ora_step.restype = ctypes.c_int
-        L.ora_step.argtypes = [vp, i64]
-        L.ora_status.restype = ctypes.c_int
-        L.ora_status.argtypes = [vp]
-        for name in ("ora_get_f", "ora_get_flags", "ora_get_phi", "ora_get_mass", "ora_get_ids"):
-            getattr(L, name).argtypes = [vp, vp]
-        L.ora_get_bubbles.restype = i64
-        L.ora_get_bubbles.argtypes = [vp, vp, i64]
-        L.ora_bubble_pressure.restype = dbl
-        L.ora_bubble_pressure.argtypes = [ctypes.POINTER(Bubble)]
-        L.ora_pool_fx.restype = i64
-        L.ora_pool_fx.argtypes = [vp]
-        L.ora_last_conversions.restype = i64
-        L.ora_last_conversions.argtypes = [vp]
-        L.ora_lattice.argtypes = [vp, vp, vp]
-        L.ora_feq.argtypes = [dbl, vp, vp]
-        L.ora_collide.restype = dbl
-        L.ora_collide.argtypes = [ctypes.POINTER(Params), vp, vp]
-        L.ora_label.argtypes = [vp, i32, i32, i32, vp]
-        L.ora_curvature.restype = dbl
-        L.ora_curvature.argtypes = [vp, i64]
-        L.ora_gradient.argtypes = [vp, i64, vp]
-        _lib = L
-    return _lib
+def lib(openmp: bool = False):
+    """The serial oracle, or (openmp=True) its OpenMP build; raises if that
+    build is unavailable."""
+    if openmp in _libs:
+        return _libs[openmp]
+    path = build_openmp() if openmp else build()
+    if path is None:
+        raise RuntimeError("the OpenMP build of the oracle is unavailable (no -fopenmp support)")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    L.ora_create.restype = vp
+    L.ora_create.argtypes = [ctypes.POINTER(Params)]
+    L.ora_destroy.argtypes = [vp]
+    L.ora_init.restype = ctypes.c_int
+    L.ora_init.argtypes = [vp, vp, vp, vp, vp]
+    L.ora_set_source.restype = ctypes.c_int
+    L.ora_set_source.argtypes = [vp, i64, dbl, dbl, i32]
+    L.ora_step.restype = ctypes.c_int
+    L.ora_step.argtypes = [vp, i64]
+    L.ora_status.restype = ctypes.c_int
+    L.ora_status.argtypes = [vp]
+    for name in ("ora_get_f", "ora_get_flags", "ora_get_phi", "ora_get_mass", "ora_get_ids"):
+        getattr(L, name).argtypes = [vp, vp]
+    L.ora_get_bubbles.restype = i64
+    L.ora_get_bubbles.argtypes = [vp, vp, i64]
+    L.ora_bubble_pressure.restype = dbl
+    L.ora_bubble_pressure.argtypes = [ctypes.POINTER(Bubble)]
+    L.ora_pool_fx.restype = i64
+    L.ora_pool_fx.argtypes = [vp]
+    L.ora_last_conversions.restype = i64
+    L.ora_last_conversions.argtypes = [vp]
+    L.ora_lattice.argtypes = [vp, vp, vp]
+    L.ora_feq.argtypes = [dbl, vp, vp]
+    L.ora_collide.restype = dbl
+    L.ora_collide.argtypes = [ctypes.POINTER(Params), vp, vp]
+    L.ora_label.argtypes = [vp, i32, i32, i32, vp]
+    L.ora_curvature.restype = dbl
+    L.ora_curvature.argtypes = [vp, i64]
+    L.ora_gradient.argtypes = [vp, i64, vp]
+    _libs[openmp] = L
+    return L
 
 
 def _ptr(a: np.ndarray):
@@ -107,18 +127,19 @@ BUBBLE_DTYPE = np.dtype([("id", np.int64), ("volume", np.float64), ("init_volume
 
 
 class Oracle:
-    """One lattice advanced by the oracle."""
+    """One lattice advanced by the oracle (openmp=True: the OpenMP build)."""
 
-    def __init__(self, **params):
+    def __init__(self, openmp: bool = False, **params):
+        self.L = lib(openmp)
         self.p = make_params(**params)
         self.n = self.p.nx * self.p.ny * self.p.nz
-        self._s = lib().ora_create(ctypes.byref(self.p))
+        self._s = self.L.ora_create(ctypes.byref(self.p))
         if not self._s:
             raise ValueError("bad oracle parameters")
 
     @classmethod
-    def from_scenario(cls, sc) -> "Oracle":
-        o = cls(**sc.params())
+    def from_scenario(cls, sc, openmp: bool = False) -> "Oracle":
+        o = cls(openmp=openmp, **sc.params())
         rc = o.init(sc.flags, sc.fill, sc.rho, sc.u)
         if rc != 0:
             raise ValueError(f"oracle rejected the geometry ({rc})")
@@ -128,7 +149,7 @@ class Oracle:
 
     def __del__(self):
         if getattr(self, "_s", None):
-            lib().ora_destroy(self._s)
+            self.L.ora_destroy(self._s)
             self._s = None
 
     def init(self, flags, fill, rho, u) -> int:
@@ -136,59 +157,59 @@ class Oracle:
         fi = np.ascontiguousarray(fill, dtype=np.float64).reshape(-1)
         rh = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
         uu = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
-        return lib().ora_init(self._s, _ptr(fl), _ptr(fi), _ptr(rh), _ptr(uu))
+        return self.L.ora_init(self._s, _ptr(fl), _ptr(fi), _ptr(rh), _ptr(uu))
 
     def set_source(self, seed_cell, extra0, rate, constp) -> int:
-        return lib().ora_set_source(self._s, int(seed_cell), float(extra0), float(rate), int(constp))
+        return self.L.ora_set_source(self._s, int(seed_cell), float(extra0), float(rate), int(constp))
 
     def step(self, nsteps: int = 1) -> int:
-        return lib().ora_step(self._s, int(nsteps))
+        return self.L.ora_step(self._s, int(nsteps))
 
     @property
     def status(self) -> int:
-        return lib().ora_status(self._s)
+        return self.L.ora_status(self._s)
 
     def f(self) -> np.ndarray:
         out = np.empty((19, self.n), dtype=np.float64)
-        lib().ora_get_f(self._s, _ptr(out))
+        self.L.ora_get_f(self._s, _ptr(out))
         return out
 
     def flags(self) -> np.ndarray:
         out = np.empty(self.n, dtype=np.uint8)
-        lib().ora_get_flags(self._s, _ptr(out))
+        self.L.ora_get_flags(self._s, _ptr(out))
         return out
 
     def phi(self) -> np.ndarray:
         out = np.empty(self.n, dtype=np.float64)
-        lib().ora_get_phi(self._s, _ptr(out))
+        self.L.ora_get_phi(self._s, _ptr(out))
         return out
 
     def mass(self) -> np.ndarray:
         out = np.empty(self.n, dtype=np.float64)
-        lib().ora_get_mass(self._s, _ptr(out))
+        self.L.ora_get_mass(self._s, _ptr(out))
         return out
 
     def ids(self) -> np.ndarray:
         out = np.empty(self.n, dtype=np.int64)
-        lib().ora_get_ids(self._s, _ptr(out))
+        self.L.ora_get_ids(self._s, _ptr(out))
         return out
 
     def pool_fx(self) -> int:
-        return int(lib().ora_pool_fx(self._s))
+        return int(self.L.ora_pool_fx(self._s))
 
     def conversions(self) -> int:
-        return int(lib().ora_last_conversions(self._s))
+        return int(self.L.ora_last_conversions(self._s))
 
     def curvature(self, i: int) -> float:
-        return float(lib().ora_curvature(self._s, int(i)))
+        return float(self.L.ora_curvature(self._s, int(i)))
 
     def gradient(self, i: int) -> np.ndarray:
         g = np.zeros(3)
-        lib().ora_gradient(self._s, int(i), _ptr(g))
+        self.L.ora_gradient(self._s, int(i), _ptr(g))
         return g
 
     def bubbles(self) -> np.ndarray:
-        L = lib()
+        L = self.L
         nb = L.ora_get_bubbles(self._s, None, 0)
         raw = (Bubble * max(nb, 1))()
         L.ora_get_bubbles(self._s, ctypes.cast(raw, ctypes.c_void_p), nb)

@@ -595,15 +595,18 @@ fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, con
     uint8_t* dfl = nullptr;
     double *dfi = nullptr, *drh = nullptr, *du = nullptr;
     if (!on_device) {
-        CK(h, cudaStreamSynchronize(h->ls));   // queued work first (the copies below are synchronous)
+        CK(h, cudaStreamSynchronize(h->ls));   // queued work may still read the staging buffer
         const size_t bytes[4] = {n, 8 * n, 8 * n, 24 * n};
         void* parts[4];
         CK(h, staging(h, bytes, 4, parts));
         dfl = (uint8_t*)parts[0]; dfi = (double*)parts[1]; drh = (double*)parts[2]; du = (double*)parts[3];
-        CK(h, cudaMemcpy(dfl, flags, n, cudaMemcpyHostToDevice));
-        CK(h, cudaMemcpy(dfi, fill, 8 * n, cudaMemcpyHostToDevice));
-        CK(h, cudaMemcpy(drh, rho, 8 * n, cudaMemcpyHostToDevice));
-        CK(h, cudaMemcpy(du, u, 24 * n, cudaMemcpyHostToDevice));
+        // on the library stream, so that the initialisation kernel below is
+        // ordered after the copies (the stream is synchronised before return,
+        // which also covers the caller's host buffers)
+        CK(h, cudaMemcpyAsync(dfl, flags, n, cudaMemcpyHostToDevice, h->ls));
+        CK(h, cudaMemcpyAsync(dfi, fill, 8 * n, cudaMemcpyHostToDevice, h->ls));
+        CK(h, cudaMemcpyAsync(drh, rho, 8 * n, cudaMemcpyHostToDevice, h->ls));
+        CK(h, cudaMemcpyAsync(du, u, 24 * n, cudaMemcpyHostToDevice, h->ls));
     } else {
         dfl = (uint8_t*)flags; dfi = (double*)fill; drh = (double*)rho; du = (double*)u;
     }

@@ -20,6 +20,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/fsl.h"
 
 #define FSL_STATIC_MAX_CELLS (1 << 21)
@@ -29,7 +32,10 @@ namespace {
 
 static __device__ __align__(256) int g_label_scratch[FSL_STATIC_MAX_CELLS];
 
-void* g_scratch_ptr[FSL_STATIC_MAX_DEVICES] = {nullptr};
+// device address of the scratch per device ordinal, looked up once per device
+// (under the mutex; later calls read the atomic slot without locking)
+std::atomic<void*> g_scratch_ptr[FSL_STATIC_MAX_DEVICES];
+std::mutex g_scratch_mutex;
 
 __host__ __device__ inline bool is_bubble_cell(uint8_t f) {
     const uint8_t t = (uint8_t)(f & 7);
@@ -94,13 +100,17 @@ extern "C" fsl_status fsl_label_bubbles_static(const uint8_t* flags, int32_t nx,
     if (n > FSL_STATIC_MAX_CELLS) return FSL_ERR_ARG;   // larger lattices need fsl_create
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= FSL_STATIC_MAX_DEVICES) return FSL_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
+    void* lab_ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!lab_ptr) {
         // first call on this device: look up the device address of the scratch
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_label_scratch) != cudaSuccess || !p) return FSL_ERR_CUDA;
-        g_scratch_ptr[dev] = p;
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        lab_ptr = g_scratch_ptr[dev].load(std::memory_order_relaxed);
+        if (!lab_ptr) {
+            if (cudaGetSymbolAddress(&lab_ptr, g_label_scratch) != cudaSuccess || !lab_ptr) return FSL_ERR_CUDA;
+            g_scratch_ptr[dev].store(lab_ptr, std::memory_order_release);
+        }
     }
-    int* lab = (int*)g_scratch_ptr[dev];
+    int* lab = (int*)lab_ptr;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int nb = (int)((n + 255) / 256);
     k_static_init<<<nb, 256, 0, s>>>(flags, (int)n, lab);

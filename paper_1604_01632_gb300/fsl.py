@@ -141,14 +141,37 @@ def _default_stream() -> int:
 STATIC_MAX_CELLS = 1 << 21
 
 
+def _check_device_tensor(t, name: str, dtype_name: str, n: int):
+    """A CUDA tensor on the current device, of the given dtype, contiguous and
+    holding at least n elements; ValueError otherwise (nothing is launched)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch CUDA tensor, not {type(t).__name__}")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must live on the current CUDA device (got {t.device})")
+    if t.dtype != getattr(torch, dtype_name):
+        raise ValueError(f"{name} must be {dtype_name} (got {t.dtype})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{name} holds {t.numel()} elements, the lattice has {n} cells")
+
+
 def label_bubbles_static(flags, nx: int, ny: int, nz: int, labels, stream: Optional[int] = None):
     """Allocation-free bubble labelling through fsl_label_bubbles_static.
 
     For callers that cannot allocate device memory.  `flags` (uint8) and
-    `labels` (int64) are caller-owned device tensors of nx*ny*nz elements; the
+    `labels` (int64) are caller-owned contiguous CUDA tensors on the current
+    device with at least nx*ny*nz elements (checked here before the call, so
+    that a host array or a short buffer never reaches the kernels); the
     library uses only its fixed 2^21-cell scratch.  Labels are the minimum
     linear index of each 18-connected gas/interface component, -1 elsewhere.
     Calls that overlap on the GPU share the scratch and race."""
+    if min(nx, ny, nz) <= 0:
+        raise ValueError("lattice dimensions must be positive")
+    n = int(nx) * int(ny) * int(nz)
+    _check_device_tensor(flags, "flags", "uint8", n)
+    _check_device_tensor(labels, "labels", "int64", n)
     L = load_library()
     st = L.fsl_label_bubbles_static(_ptr(flags), nx, ny, nz, _ptr(labels),
                                      ctypes.c_void_p(_default_stream() if stream is None else stream))

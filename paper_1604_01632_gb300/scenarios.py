@@ -356,11 +356,188 @@ def bubble_population(n_domains: int = 64, seed: int = 0, sides=(32, 48, 64, 96)
     return out
 
 
+def _rsa_grid(rng, box_lo, box_hi, radii, gap, max_attempts, periodic):
+    """Random sequential addition: sphere k (in the given order) draws uniform
+    centres until one keeps a liquid gap of `gap` to every sphere placed so
+    far, all draws together capped at max_attempts.  On a periodic axis the
+    centre ranges over [lo, hi) and distances take the minimum image; on a
+    bounded axis it ranges over [lo + r, hi - r].
+
+    Candidates are drawn in batches and the first acceptable one in draw order
+    is taken (the others count as drawn).  Two filters make a draw cheap: a
+    coarse grid of 2-cell voxels marks voxels lying entirely within
+    r_j + gap + r_min of a placed centre (no sphere of the list may be centred
+    there), and the exact test looks only at the spheres of the 27 buckets
+    around the candidate (bucket edge >= the largest centre distance of two
+    spheres that can conflict)."""
+    lo = np.asarray(box_lo, dtype=np.float64)
+    hi = np.asarray(box_hi, dtype=np.float64)
+    per = np.asarray(periodic, dtype=bool)
+    L = hi - lo
+    radii = np.asarray(radii, dtype=np.float64)
+    if radii.size == 0:
+        return np.zeros((0, 3)), np.zeros(0)
+    rmin = float(radii.min())
+    reach = 2.0 * float(radii.max()) + gap
+    nb = np.maximum(1, np.floor(L / reach).astype(np.int64))
+    h = L / nb
+    nbk = int(np.prod(nb))
+    members = np.full((nbk, 16), -1, dtype=np.int64)
+    fillc = np.zeros(nbk, dtype=np.int64)
+    pc = np.zeros((len(radii) + 1, 3))
+    pr = np.zeros(len(radii) + 1)
+    pc[-1] = 1e30                      # member slot -1: a sphere far away
+    offs = [np.arange(-1, 2) if nb[a] >= 3 else None for a in range(3)]
+    # coarse exclusion grid: voxel edge 2, voxel v covers [lo + 2 v, lo + 2 v + 2)
+    nv = np.maximum(1, np.ceil(L / 2.0).astype(np.int64))
+    excl = np.zeros(int(np.prod(nv)), dtype=bool)
+
+    def neighbour_buckets(bi):         # (k, 3) bucket coordinates -> (k, <= 27) bucket ids
+        ax = []
+        for a in range(3):
+            if offs[a] is None:
+                v = np.broadcast_to(np.arange(nb[a]), (bi.shape[0], nb[a]))
+            elif per[a]:
+                v = (bi[:, a:a + 1] + offs[a][None, :]) % nb[a]
+            else:
+                v = np.clip(bi[:, a:a + 1] + offs[a][None, :], 0, nb[a] - 1)
+            ax.append(v)
+        return (ax[0][:, :, None, None] + nb[0] * (ax[1][:, None, :, None] + nb[1] * ax[2][:, None, None, :])
+                ).reshape(bi.shape[0], -1)
+
+    def voxel_ids(p):                  # (k, 3) points -> (k,) coarse voxel ids
+        v = np.minimum(((p - lo) / 2.0).astype(np.int64), nv - 1)
+        return v[:, 0] + nv[0] * (v[:, 1] + nv[1] * v[:, 2])
+
+    def exclude(c, r):                 # mark voxels entirely within r + gap + rmin of c
+        R = r + gap + rmin
+        m = int(np.ceil(R / 2.0)) + 1
+        o = np.arange(-m, m + 1)
+        vc = np.floor((c - lo) / 2.0).astype(np.int64)
+        axes = []
+        for a in range(3):
+            v = vc[a] + o
+            ctr = lo[a] + 2.0 * v + 1.0 - c[a]          # voxel centre relative to c (before wrapping)
+            if per[a]:
+                v = np.mod(v, nv[a])
+                keep = np.ones(v.shape, dtype=bool)
+            else:
+                keep = (v >= 0) & (v < nv[a])
+            axes.append((v[keep], ctr[keep]))
+        (vx, cx_), (vy, cy_), (vz, cz_) = axes
+        d2 = cz_[:, None, None] ** 2 + cy_[None, :, None] ** 2 + cx_[None, None, :] ** 2
+        inside = np.sqrt(d2) + np.sqrt(3.0) <= R
+        ids = vx[None, None, :] + nv[0] * (vy[None, :, None] + nv[1] * vz[:, None, None])
+        excl[ids[inside]] = True
+
+    n = 0
+    attempts = 0
+    batch = 8
+    for r in radii:
+        clo = np.where(per, lo, lo + r)
+        chi = np.where(per, hi, hi - r)
+        if np.any(chi <= clo):
+            continue
+        placed = False
+        while attempts < max_attempts and not placed:
+            k = int(min(batch, max_attempts - attempts))
+            cand = clo + rng.uniform(0.0, 1.0, (k, 3)) * (chi - clo)
+            free = np.nonzero(~excl[voxel_ids(cand)])[0]
+            hit = -1
+            if free.size:
+                cf = cand[free]
+                bi = np.minimum(((cf - lo) / h).astype(np.int64), nb - 1)
+                idx = members[neighbour_buckets(bi)].reshape(free.size, -1)     # (kf, M)
+                d = cf[:, None, :] - pc[idx]
+                for a in range(3):
+                    if per[a]:
+                        d[:, :, a] -= L[a] * np.round(d[:, :, a] / L[a])
+                ok = np.all((d * d).sum(-1) >= (r + pr[idx] + gap) ** 2, axis=1)
+                w = np.nonzero(ok)[0]
+                if w.size:
+                    hit = int(free[w[0]])
+            if hit >= 0:
+                attempts += hit + 1
+                c = cand[hit]
+                pc[n] = c
+                pr[n] = r
+                bj = np.minimum(((c - lo) / h).astype(np.int64), nb - 1)
+                b = int(bj[0] + nb[0] * (bj[1] + nb[1] * bj[2]))
+                if fillc[b] == members.shape[1]:
+                    members = np.concatenate([members, np.full_like(members, -1)], 1)
+                members[b, fillc[b]] = n
+                fillc[b] += 1
+                exclude(c, r)
+                n += 1
+                placed = True
+                batch = max(8, batch // 2)
+            else:
+                attempts += k
+                batch = min(1 << 14, 2 * batch)
+        if attempts >= max_attempts:
+            break
+    return pc[:n].copy(), pr[:n].copy()
+
+
+def _stamp_spheres_banded(shape, centres, radii, sub: int = 4, chunk_cells: int = 1 << 22) -> np.ndarray:
+    """Liquid fraction of a box (every axis wrapping) holding non-overlapping gas
+    spheres: the fraction of sub^3 sample points of each cell outside every
+    sphere.  Cells whose centre lies more than the sample points' reach
+    (sqrt(3)/2 (1 - 1/sub)) inside a sphere are all gas, those as far outside
+    are untouched; only the band between is sub-sampled.  Spheres are handled
+    in chunks of equal bounding-box size, all with numpy array operations."""
+    nz, ny, nx = shape
+    fill = np.ones(nz * ny * nx)
+    offs = (np.arange(sub, dtype=np.float64) + 0.5) / sub - 0.5
+    reach = 0.5 * np.sqrt(3.0) * (1.0 - 1.0 / sub) + 1e-9
+    centres = np.asarray(centres, dtype=np.float64)
+    radii = np.asarray(radii, dtype=np.float64)
+    box = np.ceil(2.0 * radii + 3.0).astype(np.int64)
+    order = np.argsort(box, kind="stable")
+    for b in np.unique(box):
+        sel = order[box[order] == b]
+        per = max(1, chunk_cells // int(b) ** 3)
+        o = np.arange(b, dtype=np.float64)
+        for s0 in range(0, len(sel), per):
+            ids = sel[s0:s0 + per]
+            c = centres[ids]
+            r = radii[ids]
+            base = np.floor(c - r[:, None] - 1.0)                    # (M, 3) first cell of the box
+            X = base[:, 0:1] + o[None, :]                             # (M, b) cell corners
+            Y = base[:, 1:2] + o[None, :]
+            Z = base[:, 2:3] + o[None, :]
+            dx2 = (X + 0.5 - c[:, 0:1]) ** 2
+            dy2 = (Y + 0.5 - c[:, 1:2]) ** 2
+            dz2 = (Z + 0.5 - c[:, 2:3]) ** 2
+            dist = np.sqrt(dz2[:, :, None, None] + dy2[:, None, :, None] + dx2[:, None, None, :]) - r[:, None, None, None]
+            xi = np.mod(X.astype(np.int64), nx)
+            yi = np.mod(Y.astype(np.int64), ny)
+            zi = np.mod(Z.astype(np.int64), nz)
+            flat = xi[:, None, None, :] + nx * (yi[:, None, :, None] + ny * zi[:, :, None, None])
+            inside = dist < -reach
+            fill[flat[inside]] = 0.0
+            m, k, j, i = np.nonzero(np.abs(dist) <= reach)
+            if m.size == 0:
+                continue
+            ax = (X[m, i][:, None] + 0.5 + offs[None, :] - c[m, 0][:, None]) ** 2     # (NB, sub)
+            ay = (Y[m, j][:, None] + 0.5 + offs[None, :] - c[m, 1][:, None]) ** 2
+            az = (Z[m, k][:, None] + 0.5 + offs[None, :] - c[m, 2][:, None]) ** 2
+            d2 = az[:, :, None, None] + ay[:, None, :, None] + ax[:, None, None, :]
+            cnt = np.count_nonzero((d2 < (r[m] ** 2)[:, None, None, None]).reshape(m.size, -1), axis=1)
+            fb = flat[m, k, j, i]
+            fill[fb] = np.minimum(fill[fb], 1.0 - cnt / float(sub ** 3))
+    return fill.reshape(shape)
+
+
 def foam(n: int = 512, gas_fraction: float = 0.4, seed: int = 0, lid_speed: float = 0.05,
-         gravity: float = 1e-5, sigma: float = 3e-3, max_attempts: int = 200000, steps: int = 10000) -> Scenario:
+         gravity: float = 1e-5, sigma: float = 3e-3, max_attempts: Optional[int] = None, gap: float = 2.0,
+         steps: int = 10000) -> Scenario:
     """Dense bubble packing: lognormal radii (median 8, sigma_log 0.3, clipped to
-    [4, 16]) placed by random sequential addition toward `gas_fraction`; periodic
-    in x and y, no-slip bottom, lid moving at u_x = lid_speed on top."""
+    [4, 16]) drawn until their volume reaches `gas_fraction` of the box, placed
+    largest first by random sequential addition with a liquid gap of `gap`
+    cells between bubbles and to the walls (attempts capped, so a jammed
+    packing stops short of the target); periodic in x and y, no-slip bottom
+    wall at z = 0, lid at z = n - 1 moving at u_x = lid_speed."""
     rng = np.random.Generator(np.random.PCG64(seed))
     target = gas_fraction * n ** 3
     radii = []
@@ -370,30 +547,18 @@ def foam(n: int = 512, gas_fraction: float = 0.4, seed: int = 0, lid_speed: floa
         radii.append(r)
         vol += 4.0 / 3.0 * np.pi * r ** 3
     radii = np.sort(np.array(radii))[::-1]
-    centres, radii = _rsa(rng, (n, n, n - 4), radii, 2.0, max_attempts)
-    centres[:, 2] += 2.0
+    if max_attempts is None:
+        max_attempts = 100 * len(radii)
+    centres, radii = _rsa_grid(rng, (0.0, 0.0, 1.0 + gap), (float(n), float(n), n - 1.0 - gap), radii, gap,
+                               max_attempts, (True, True, False))
     shape = (n, n, n)
-    fill = np.ones(shape)
-    # per-sphere local stamping keeps this linear in the number of spheres
-    offs = (np.arange(4, dtype=np.float64) + 0.5) / 4 - 0.5
-    for c, r in zip(centres, radii):
-        lo = np.floor(c - r - 1).astype(int)
-        hi = np.ceil(c + r + 1).astype(int)
-        zi = np.arange(lo[2], hi[2]); yi = np.arange(lo[1], hi[1]); xi = np.arange(lo[0], hi[0])
-        zz, yy, xx = np.meshgrid(zi, yi, xi, indexing="ij")
-        cnt = np.zeros(zz.shape)
-        for oz in offs:
-            for oy in offs:
-                for ox in offs:
-                    d = np.sqrt((xx + 0.5 + ox - c[0]) ** 2 + (yy + 0.5 + oy - c[1]) ** 2 + (zz + 0.5 + oz - c[2]) ** 2)
-                    cnt += d < r
-        frac_gas = cnt / 64.0
-        sl = (np.mod(zz, n), np.mod(yy, n), np.mod(xx, n))
-        fill[sl] = np.minimum(fill[sl], 1.0 - frac_gas)
+    fill = _stamp_spheres_banded(shape, centres, radii)
     obs = np.zeros(shape, dtype=bool)
     obs[0] = True
     lid = np.zeros(shape, dtype=bool)
     lid[n - 1] = True
     flags = classify(fill, obstacle=obs, lid=lid)
-    return _finish(f"foam_{n}", flags, fill, collision=TRT, sigma=sigma, gravity=(0.0, 0.0, -gravity),
-                   lid=(lid_speed, 0.0, 0.0), steps=steps)
+    sc = _finish(f"foam_{n}", flags, fill, collision=TRT, sigma=sigma, gravity=(0.0, 0.0, -gravity),
+                 lid=(lid_speed, 0.0, 0.0), steps=steps)
+    sc.bubbles_placed = int(len(radii))
+    return sc
