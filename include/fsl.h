@@ -175,6 +175,22 @@ double fsl_stream_collide_ms(const fsl_domain* h);
  * profilers).  Results are identical. */
 fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
 
+/* Failure-path limits, for tests of the error reporting (0 restores a
+ * default):
+ *   ccl_max_iter   cap on the union / find loops of the labelling (default
+ *                  2^24); a pass that reaches it latches
+ *                  FSL_ERR_CCL_NOT_CONVERGED and leaves the bubble table of
+ *                  the labelled domains unreliable;
+ *   barrier_polls  polls a block of the conversion kernel makes at a grid
+ *                  barrier before it latches FSL_ERR_SYNC and returns (default
+ *                  2^22);
+ *   barrier_absent 1 makes every grid barrier wait for one block more than
+ *                  the grid holds, so that each wait runs out after
+ *                  barrier_polls polls (0: normal barriers).
+ * Waits for the handle's stream; the next fsl_step rebuilds its graphs.
+ * FSL_ERR_ARG for values out of range. */
+fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_polls, int32_t barrier_absent);
+
 /* Device time per phase of the steps timed since fsl_set_timing(h, 1), summed,
  * in milliseconds, when the handle runs without graphs (fsl_set_graphs(h, 0)):
  * out (array of 4): [0] stream-collide kernel (liquid and interface cells in

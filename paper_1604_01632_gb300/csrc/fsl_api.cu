@@ -2,6 +2,7 @@
 // step graphs, state exports.  Host code only; kernels live in fsl_core.cu
 // (precision-independent + FP64) and fsl_fast.cu (FP32 / FP16 / BF16 forms).
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -85,6 +86,9 @@ struct fsl_domain {
     cudaGraph_t timed_src[2] = {nullptr, nullptr};   // kept: its nodes name the event records
     int graph_kernels[3] = {0, 0, 0};
     long long launches = 0;
+    int ccl_cap = 1 << 24;        // cap on the labelling's union / find loops
+    int spins = 1 << 22;          // polls at a grid barrier before FSL_ERR_SYNC
+    int bar_extra = 0;            // 1: barriers wait for a block that does not exist (tests)
     bool timing = false;
     bool graphs = true;           // false: every kernel a separate launch (profilers)
     std::vector<cudaEvent_t> evpool;
@@ -177,6 +181,8 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.trig = h->trig;
     A.status = h->status;
     A.bar = h->bar;
+    A.spins = h->spins;
+    A.bar_extra = h->bar_extra;
     A.ndom = h->ndom;
     A.ilist = h->ilist[src];
     A.icount = h->icount[src];
@@ -221,7 +227,7 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     // find() walks strictly decreasing indices and every retry of unite()
     // follows a link made by another thread, so both loops end; the caps only
     // turn a corrupted label array into an error status
-    K.max_iter = 1 << 24;
+    K.max_iter = h->ccl_cap;
     return K;
 }
 
@@ -327,6 +333,8 @@ fsl_status latch(fsl_domain* h) {
                            : st == FSL_ERR_TABLE_FULL ? "bubble table full"
                            : st == FSL_ERR_SYNC ? "a grid barrier of the conversion kernel timed out"
                                                 : "device error";
+        // a barrier that timed out leaves its arrival count behind
+        if (st == FSL_ERR_SYNC) cudaMemset(h->bar, 0, 2 * sizeof(unsigned));
         return fail(h, (fsl_status)st, what);
     }
     return FSL_OK;
@@ -749,6 +757,24 @@ double fsl_stream_collide_ms(const fsl_domain* h) { return h ? h->k1_ms : 0.0; }
 fsl_status fsl_phase_ms(const fsl_domain* h, double* out) {
     if (!h || !out) return FSL_ERR_ARG;
     for (int k = 0; k < 4; ++k) out[k] = h->phase_ms[k];
+    return FSL_OK;
+}
+
+fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_polls, int32_t barrier_absent) {
+    if (!h) return FSL_ERR_ARG;
+    if (ccl_max_iter < 0 || ccl_max_iter > INT_MAX || barrier_polls < 0 || barrier_polls > INT_MAX ||
+        (barrier_absent != 0 && barrier_absent != 1))
+        return fail(h, FSL_ERR_ARG, "bad limit");
+    CK(h, cudaStreamSynchronize(h->ls));
+    h->ccl_cap = ccl_max_iter > 0 ? (int)ccl_max_iter : (1 << 24);
+    h->spins = barrier_polls > 0 ? (int)barrier_polls : (1 << 22);
+    h->bar_extra = barrier_absent;
+    // the step graphs hold the old values in their kernel parameters
+    for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < 3; ++j)
+            if (h->graph[k][j]) { cudaGraphExecDestroy(h->graph[k][j]); h->graph[k][j] = nullptr; }
+    for (int k = 0; k < 2; ++k)
+        if (h->timed_src[k]) { cudaGraphDestroy(h->timed_src[k]); h->timed_src[k] = nullptr; }
     return FSL_OK;
 }
 

@@ -144,6 +144,9 @@ struct StepArgs {
     int* stepno;                // device step counter
     long long* icnt;            // per-domain interface count at the end of the step
     unsigned* bar;              // grid barrier of the conversion kernel: count, generation
+    int spins;                  // polls a block waits at a grid barrier before it gives up
+    int bar_extra;              // arrivals a barrier waits for beyond the grid (0; 1 only to
+                                // test the timeout path: no block is then the last)
     Dom d0;                     // domain 0, read from the parameter space when ndom == 1
 };
 
@@ -1859,8 +1862,11 @@ __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
         int c = -1;
         long long term = 0;
         if (ty == GAS || ty == IFC) {
+            // the slot of the cell's root; -1 when a find gave up at its
+            // iteration cap (the pass has then latched ST_CCL and r may be an
+            // inner node whose aux entry was never written)
             const int r = K.lab[g];
-            c = K.aux[r];
+            c = (r >= 0 && K.lab[r] == r) ? K.aux[r] : -1;
             term = A.phif ? volume_term_f(ty, A.phif[g]) : volume_term(ty, A.phi[g]);
         }
         warp_add(K.nvfx, c, term);
@@ -1931,12 +1937,11 @@ __device__ inline void ccl_install_phase(const StepArgs& A, const CclArgs& K) {
 
 // Barrier over all blocks of a cooperative launch (all of them resident).  The
 // last block to arrive resets the count and advances the generation; the others
-// wait for the generation to move, at most FSL_BARRIER_SPINS polls, after which
-// they record ST_SYNC and report failure (the caller returns).  The arrival is
-// an acquire-release atomic and the release of the generation and its polls
-// are release / acquire at GPU scope, so every write before the barrier is
+// wait for the generation to move, at most A.spins polls, after which they
+// record ST_SYNC and report failure (the caller returns).  The arrival is an
+// acquire-release atomic and the release of the generation and its polls are
+// release / acquire at GPU scope, so every write before the barrier is
 // visible to every read after it.
-#define FSL_BARRIER_SPINS (1 << 22)
 __device__ inline bool grid_barrier(const StepArgs& A) {
     __shared__ int ok;
     __syncthreads();
@@ -1949,14 +1954,14 @@ __device__ inline bool grid_barrier(const StepArgs& A) {
         // arrive: release this block's writes (ordered before by the block
         // barrier), acquire those of the blocks that arrived before
         asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
-        if (old == gridDim.x - 1) {
+        if (old == gridDim.x - 1 + (unsigned)A.bar_extra) {
             asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(count) : "memory");
             asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(gen) : "memory");
         } else {
             int it = 0;
             do {
                 asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(gnow) : "l"(gen) : "memory");
-            } while (gnow == g0 && ++it < FSL_BARRIER_SPINS);
+            } while (gnow == g0 && ++it < A.spins);
             if (gnow == g0) {
                 set_status(A.status, ST_SYNC);
                 ok = 0;

@@ -29,7 +29,7 @@ FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.flo
 EXPORTS = ["fsl_create", "fsl_init_geometry", "fsl_set_bubble_source", "fsl_step", "fsl_sync", "fsl_bubbles",
            "fsl_fields", "fsl_destroy", "fsl_last_error", "fsl_kernel_launches", "fsl_set_timing",
            "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs",
-           "fsl_label_bubbles_static", "fsl_phase_ms"]
+           "fsl_label_bubbles_static", "fsl_phase_ms", "fsl_set_limits"]
 
 
 class FslError(RuntimeError):
@@ -98,6 +98,8 @@ def load_library():
     L.fsl_phase_ms.argtypes = [vp, vp]
     L.fsl_set_graphs.restype = i32
     L.fsl_set_graphs.argtypes = [vp, i32]
+    L.fsl_set_limits.restype = i32
+    L.fsl_set_limits.argtypes = [vp, i64, i64, i32]
     L.fsl_labelling_runs.restype = i64
     L.fsl_labelling_runs.argtypes = [vp]
     L.fsl_cell_counts.restype = i32
@@ -302,6 +304,11 @@ class Simulation:
 
     def set_timing(self, on: bool):
         self._check(self.L.fsl_set_timing(self._h, 1 if on else 0))
+
+    def set_limits(self, ccl_max_iter: int = 0, barrier_polls: int = 0, barrier_absent: bool = False):
+        """Failure-path limits for tests (0 = default): labelling iteration cap,
+        barrier polls, and a barrier that waits for a block that does not exist."""
+        self._check(self.L.fsl_set_limits(self._h, int(ccl_max_iter), int(barrier_polls), 1 if barrier_absent else 0))
 
     def set_graphs(self, on: bool):
         self._check(self.L.fsl_set_graphs(self._h, 1 if on else 0))
