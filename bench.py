@@ -1,18 +1,23 @@
-"""Benchmark of one FSLBM step (all sub-steps of the method) on GB300.
+"""Benchmark of the FSLBM step (every sub-step of the method) on one GB300.
 
-Workload (default): the gas-thread breakup lattice, 256x64x64 cells, periodic in
-x with no-slip walls elsewhere, gas cylinder of radius 8 (1 + 0.1 sin(2 pi x /
-64)), TRT (Lambda = 3/16, tau = 0.8), sigma = 5e-3, FP16-shifted PDF storage
-with FP32 collision; seeded synthetic geometry.
+Headline workload (default): the dense coalescing foam, 512^3 cells
+(134,217,728), periodic in x and y, no-slip bottom wall, lid moving at
+u_x = 0.05, gravity 1e-5, sigma = 3e-3, TRT (Lambda = 3/16, tau = 0.8);
+lognormal bubble radii (median 8, sigma_log 0.3, clipped to [4, 16]) placed by
+random sequential addition toward a gas fraction of 0.4 (seeded synthetic
+geometry; the achieved fraction is reported).  FP16-shifted PDF storage with
+FP32 collision, against FP32, BF16-shifted and FP64 storage of the same
+lattice, each with its mass drift over the run.
 
 One step = stream/bounce-back + mass exchange + reconstruction + collision,
 the conversion phases with excess-mass redistribution, the bubble-volume
 update, and the merge/split labelling when triggered.  Inputs are resident in
 HBM when the timed region starts; the L2 cache (129 MB) is flushed before every
-timed step (the working set of this lattice fits in L2) and only the steps are
-timed, with CUDA events on the stream.
+timed step and only the steps are timed, with CUDA events on the stream.  The
+first steps of a handle tune the stream-collide kernel's form (they are real
+steps); the timed steps come after them and after the warm-up.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16s]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f16s] [--workload foam512]
     python bench.py --impl reference      # the FP64 CPU oracle on the host cores
 
 Under torchrun every rank advances its own independent copy of the lattice
@@ -40,14 +45,22 @@ METRIC = "FSLBM MLUPS & HBM roofline fraction: FP16-store/batched vs plain FP32/
 UNIT = "MLUPS"
 BYTES = {"fp64": 8, "fp32": 4, "f16s": 2, "bf16s": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "f16s": "f32", "bf16s": "f32"}
-KERNEL = "k_stream (stream-collide: interface blocks + liquid blocks)"
+KERNEL = "stream-collide kernel (interface and liquid cells, one launch per step)"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1604_01632_gb300", "csrc", f) for f in
                   ("fsl_device.cuh", "fsl_fast.cu", "fsl_core.cu")]
+CPU_SAMPLE_N = 128        # the oracle's bounded sample: the same foam recipe at 128^3
 
 
 def workload(name: str):
     from paper_1604_01632_gb300 import scenarios as S
+    if name == "foam512":
+        sc = S.foam(n=512)
+        return sc, ("foam 512^3 TRT tau=0.8 sigma=3e-3 g=1e-5 lid u_x=0.05, lognormal radii (median 8, "
+                    "sigma_log 0.3, [4,16]) by RSA toward gas fraction 0.4")
+    if name.startswith("foam"):
+        n = int(name[4:])
+        return S.foam(n=n), f"foam {n}^3 (the 512^3 foam recipe at {n}^3)"
     if name == "gas_thread":
         return S.gas_thread(), "gas_thread 256x64x64 TRT sigma=5e-3 R=8(1+0.1 sin(2 pi x/64))"
     if name == "static_bubble":
@@ -55,7 +68,16 @@ def workload(name: str):
     if name == "gas_thread_large":
         return (S.gas_thread(nx=1024, ny=256, nz=256, radius=32.0, wavelength=256.0),
                 "gas_thread 1024x256x256 TRT sigma=5e-3 R=32(1+0.1 sin(2 pi x/256))")
+    if name == "orifice":
+        return S.orifice(), "orifice 128x128x256 TRT g=1e-5 sigma=2e-3 hole r=6"
     raise ValueError(name)
+
+
+def gas_fraction(sc) -> float:
+    """Gas volume (gas cells 1, interface cells 1 - fill) over the lattice."""
+    g = np.count_nonzero(sc.flags == 2)
+    i = sc.flags == 1
+    return float((g + np.sum(1.0 - sc.fill[i])) / sc.n)
 
 
 def algorithmic_bytes(counts, s: int) -> float:
@@ -157,180 +179,6 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu(args, rank: int, world: int):
-    import torch
-    from paper_1604_01632_gb300 import fsl
-
-    dev = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(dev)
-    sc, wl_desc = workload(args.workload)
-    n = sc.n
-    stream = torch.cuda.current_stream()
-
-    def make(precision):
-        sim = fsl.Simulation.from_scenarios([sc], precision=precision, stream=int(stream.cuda_stream))
-        if args.no_graphs:
-            sim.set_graphs(False)
-        return sim
-
-    flush = L2Flush(torch, args.flush)
-    meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-    peak = float(meas_peaks["hbm_gbs"]) if meas_peaks else 6800.0
-
-    def timed_steps(sim, K, W, timing=True):
-        sim.set_timing(timing)
-        for _ in range(W):
-            flush()
-            sim.step(1)
-        sim.sync()
-        sim.set_timing(timing)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        c0 = sim.cell_counts(0)   # (its export kernel is not a step kernel)
-        l0 = sim.launches
-        r0 = sim.labelling_runs
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        for k in range(K):
-            flush()
-            ev[k][0].record()
-            sim.step(1)
-            ev[k][1].record()
-        torch.cuda.synchronize()
-        sim.sync()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        k1 = sim.stream_collide_ms()
-        launches = sim.launches - l0
-        c1 = sim.cell_counts(0)
-        return ms, k1, launches, (np.asarray(c0) + np.asarray(c1)) / 2.0, sim.labelling_runs - r0
-
-    # headline: the requested precision, steps timed without instrumentation
-    sim = make(args.precision)
-    clk = Clocks(dev)
-    clk.start()
-    ms, _, launches, counts, lruns = timed_steps(sim, args.steps, args.warmup, timing=False)
-    clocks = clk.stop()
-    # the stream-collide pair of the same run, timed by CUDA events recorded
-    # around it inside each step (a second pass of the same length: the event
-    # records add a few microseconds to a step, so they stay out of the headline)
-    _, k1_ms, _, _, _ = timed_steps(sim, args.steps, args.warmup, timing=True)
-    ms_max = max_over_ranks(ms, world, "cuda")
-    value = whole_job_mlups(n, args.steps, world, ms_max)
-    s = BYTES[args.precision]
-    abytes = algorithmic_bytes(counts, s)
-    k1_avg = k1_ms / args.steps
-    achieved = abytes / (k1_avg * 1e-3) / 1e9
-    traffic = traffic_per_launch(args.precision, args.workload)
-    sim.close()
-
-    # per-phase device times from a separate direct-launch pass (diagnostic)
-    phases = None
-    if not args.no_variants:
-        ph = make(args.precision)
-        ph.set_graphs(False)
-        timed_steps(ph, 20, args.warmup)
-        phases = {k: round(v / 20 * 1e3, 2) for k, v in ph.phase_ms().items()}
-        ph.close()
-
-    def measure(sim, cells, prec, K):
-        """Uninstrumented step time, then the stream-collide pair by events."""
-        vms, _, _, vc, _ = timed_steps(sim, K, args.warmup, timing=False)
-        _, vk1, _, _, _ = timed_steps(sim, K, args.warmup, timing=True)
-        vb = algorithmic_bytes(vc, BYTES[prec])
-        return {"mlups": round(cells * K / (vms * 1e-3) / 1e6, 1), "ms_per_step": round(vms / K, 5),
-                "stream_collide_gbs": round(vb / (vk1 / K * 1e-3) / 1e9, 1),
-                "stream_collide_frac": round(vb / (vk1 / K * 1e-3) / 1e9 / peak, 3)}
-
-    variants = {}
-    if not args.no_variants:
-        for prec in ("fp32", "bf16s", "fp64"):
-            if prec == args.precision:
-                continue
-            v = make(prec)
-            variants[prec] = measure(v, n, prec, max(5, args.steps // 2))
-            v.close()
-
-    # the same path on larger lattices of the paper's shapes (one domain each)
-    at_scale = {}
-    if not args.no_scale and world == 1:
-        from paper_1604_01632_gb300 import scenarios as S
-        large = workload("gas_thread_large")
-        runs = (("gas_thread_large", large, args.precision),
-                ("gas_thread_large_fp32", large, "fp32"),
-                ("orifice", (S.orifice(), "orifice 128x128x256 TRT g=1e-5 sigma=2e-3 hole r=6"), args.precision))
-        for key, (sc2, desc), prec in runs:
-            if prec == args.precision and key.endswith("_fp32"):
-                continue
-            v = fsl.Simulation.from_scenarios([sc2], precision=prec, stream=int(stream.cuda_stream))
-            r = measure(v, sc2.n, prec, 10)
-            r.update({"workload": desc, "cells": sc2.n, "storage": prec})
-            at_scale[key] = r
-            v.close()
-
-    # batched bubble populations: 64 independent domains in one handle (one
-    # graph per step) against the same domains stepped as 64 separate handles
-    batched = None
-    if not args.no_batched and world == 1:
-        batched = run_batched(args, fsl, torch, stream, flush)
-
-    # end to end through the C ABI from pinned host buffers: upload the initial
-    # state, K steps, read back the fields and the bubble table
-    e2e = None
-    if not args.no_e2e:
-        def pinned(shape, dtype):
-            t = torch.empty(int(np.prod(shape)), dtype=getattr(torch, np.dtype(dtype).name), pin_memory=True)
-            return t.numpy().reshape(shape)
-        flags, fill = pinned(n, np.uint8), pinned(n, np.float64)
-        rho, u = pinned(n, np.float64), pinned(3 * n, np.float64)
-        np.copyto(flags, sc.flags.reshape(-1))
-        np.copyto(fill, sc.fill.reshape(-1))
-        np.copyto(rho, sc.rho.reshape(-1))
-        np.copyto(u, sc.u.reshape(-1))
-        res = {"flags": pinned(n, np.uint8), "fill": pinned(n, np.float64), "id": pinned(n, np.int64),
-               "rho": pinned(n, np.float64), "u": pinned(3 * n, np.float64)}
-        sim = fsl.Simulation([sc.params()], precision=args.precision, stream=int(stream.cuda_stream))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sim.init_geometry(0, flags, fill, rho, u)
-        sim.step(args.steps)
-        out = sim.fields(0, ("flags", "fill", "id", "rho", "u"), out=res)
-        bub = sim.bubbles(0)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        h2d = flags.nbytes + fill.nbytes + rho.nbytes + u.nbytes
-        d2h = sum(a.nbytes for a in out.values()) + bub.nbytes
-        e2e = {"value": round(n * args.steps * world / dt / 1e6, 1), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps)}
-        sim.close()
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(sc, steps=args.cpu_steps)
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": wl_desc, "cells": n, "storage": args.precision,
-                       "l2": flush.describe() + " before every timed step; steps timed by CUDA events",
-                       "parallelism": f"replicas x{world}",
-                       "labelling_runs_per_step": round(lruns / args.steps, 3),
-                       "cell_counts_liquid_interface_gas_obstacle": [int(c) for c in counts[:4]]},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "kernel": KERNEL, "algorithmic_bytes_per_launch": int(abytes),
-                         "avg_launch_ms": round(k1_avg, 5), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                         "timing": "CUDA events on the launching stream around the stream-collide kernel "
-                                   "(liquid and interface blocks), second timed pass of the same run"},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "variants": variants, "phase_us_per_step_direct_launch": phases, "batched": batched,
-            "at_scale": at_scale,
-        }
-        print(json.dumps(line))
-
-
 class L2Flush:
     """Empties the 129 MB L2 before a timed step: a 256 MB write, then (mode
     "write+read") a 256 MB read of a second buffer, so that the lines left in
@@ -352,6 +200,208 @@ class L2Flush:
         if self.mode == "write+read":
             return "flushed (256 MB write, then 256 MB read of another buffer: no dirty lines left)"
         return "flushed (256 MB write)"
+
+
+def tune(sim, limit: int = 16) -> dict:
+    """Run the autotuning steps (real steps) until the stream-collide form is
+    decided; returns the tuner's record and the number of steps it took."""
+    k = 0
+    while sim.tuning()["form"] < 0 and k < limit:
+        sim.step(1)
+        k += 1
+    sim.sync()
+    rec = sim.tuning()
+    rec["steps"] = k
+    return rec
+
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    from paper_1604_01632_gb300 import fsl
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    t0 = time.perf_counter()
+    sc, wl_desc = workload(args.workload)
+    gen_s = time.perf_counter() - t0
+    n = sc.n
+    stream = torch.cuda.current_stream()
+
+    def make(precision, scen=None):
+        sim = fsl.Simulation.from_scenarios([scen or sc], precision=precision, stream=int(stream.cuda_stream))
+        if args.no_graphs:
+            sim.set_graphs(False)
+        return sim
+
+    flush = L2Flush(torch, args.flush)
+    meas_peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = float(meas_peaks["hbm_gbs"]) if meas_peaks else 6800.0
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if meas_peaks else "fallback 6800 GB/s"
+
+    def timed_steps(sim, K, W, timing=True, barrier=False):
+        sim.set_timing(timing)
+        for _ in range(W):
+            flush()
+            sim.step(1)
+        sim.sync()
+        sim.set_timing(timing)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        c0 = sim.cell_counts(0)   # (its export kernel is not a step kernel)
+        l0 = sim.launches
+        r0 = sim.labelling_runs
+        if barrier and world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(K):
+            flush()
+            ev[k][0].record()
+            sim.step(1)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        sim.sync()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        k1 = sim.stream_collide_ms()
+        launches = sim.launches - l0
+        c1 = sim.cell_counts(0)
+        return ms, k1, launches, (np.asarray(c0) + np.asarray(c1)) / 2.0, sim.labelling_runs - r0
+
+    def measure(sim, cells, prec, K, W):
+        """Uninstrumented step time, then the stream-collide kernel by events,
+        and the liquid-mass drift over all steps the handle ran."""
+        m0 = sim.total_mass()
+        vms, _, _, vc, lr = timed_steps(sim, K, W, timing=False)
+        _, vk1, _, _, _ = timed_steps(sim, K, W, timing=True)
+        m1 = sim.total_mass()
+        vb = algorithmic_bytes(vc, BYTES[prec])
+        return {"mlups": round(cells * K / (vms * 1e-3) / 1e6, 1), "ms_per_step": round(vms / K, 5),
+                "stream_collide_ms": round(vk1 / K, 5),
+                "stream_collide_gbs": round(vb / (vk1 / K * 1e-3) / 1e9, 1),
+                "stream_collide_frac": round(vb / (vk1 / K * 1e-3) / 1e9 / peak, 3),
+                "labelling_runs_per_step": round(lr / K, 3),
+                "mass_drift_rel": float(f"{(m1 - m0) / m0:.3e}")}
+
+    # headline: the requested precision, tuned, then steps timed without instrumentation
+    sim = make(args.precision)
+    mass0 = sim.total_mass()
+    tuning = tune(sim)
+    clk = Clocks(dev)
+    clk.start()
+    ms, _, launches, counts, lruns = timed_steps(sim, args.steps, args.warmup, timing=False, barrier=True)
+    clocks = clk.stop()
+    # the stream-collide kernel of the same run, timed by CUDA events recorded
+    # around it inside each step (a second pass of the same length: the event
+    # records add a few microseconds to a step, so they stay out of the headline)
+    _, k1_ms, _, _, _ = timed_steps(sim, args.steps, args.warmup, timing=True)
+    mass1 = sim.total_mass()
+    steps_run = tuning["steps"] + 2 * (args.steps + args.warmup)
+    ms_max = max_over_ranks(ms, world, "cuda")
+    value = whole_job_mlups(n, args.steps, world, ms_max)
+    s = BYTES[args.precision]
+    abytes = algorithmic_bytes(counts, s)
+    k1_avg = k1_ms / args.steps
+    achieved = abytes / (k1_avg * 1e-3) / 1e9
+    traffic = traffic_per_launch(args.precision, args.workload)
+    nbub = len(sim.bubbles(0))
+    sim.close()
+
+    # the same lattice in the other storage forms (FP32 is the metric's plain baseline)
+    variants = {}
+    if not args.no_variants and world == 1:
+        for prec in ("fp32", "bf16s", "fp64"):
+            if prec == args.precision:
+                continue
+            v = make(prec)
+            rec = tune(v)
+            K = max(5, args.steps // 2) if prec != "fp64" else max(3, args.steps // 4)
+            r = measure(v, n, prec, K, 3)
+            r["tuned_form"] = rec["form_name"]
+            variants[prec] = r
+            v.close()
+            torch.cuda.empty_cache()
+
+    # secondary workloads: the 1 M-cell gas thread (latency-dominated) and a
+    # batch of 64 bubble-population domains in one handle
+    secondary = {}
+    if not args.no_secondary and world == 1:
+        gsc, gdesc = workload("gas_thread")
+        for prec in (args.precision, "fp32"):
+            v = make(prec, gsc)
+            rec = tune(v)
+            r = measure(v, gsc.n, prec, 20, 5)
+            r.update({"workload": gdesc, "cells": gsc.n, "tuned_form": rec["form_name"]})
+            secondary[f"gas_thread_{prec}"] = r
+            v.close()
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = run_batched(args, fsl, torch, stream, flush)
+
+    # end to end through the C ABI from pinned host buffers: upload the initial
+    # state, K steps, read back cell types, fill levels, bubble ids and the
+    # bubble table
+    e2e = None
+    if not args.no_e2e:
+        def pinned(shape, dtype):
+            t = torch.empty(int(np.prod(shape)), dtype=getattr(torch, np.dtype(dtype).name), pin_memory=True)
+            return t.numpy().reshape(shape)
+        flags, fill = pinned(n, np.uint8), pinned(n, np.float64)
+        rho, u = pinned(n, np.float64), pinned(3 * n, np.float64)
+        np.copyto(flags, sc.flags.reshape(-1))
+        np.copyto(fill, sc.fill.reshape(-1))
+        np.copyto(rho, sc.rho.reshape(-1))
+        np.copyto(u, sc.u.reshape(-1))
+        res = {"flags": pinned(n, np.uint8), "fill": pinned(n, np.float64), "id": pinned(n, np.int64)}
+        sim = fsl.Simulation([sc.params()], precision=args.precision, stream=int(stream.cuda_stream))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init_geometry(0, flags, fill, rho, u)
+        for seed, extra, rate, constp in sc.sources:
+            sim.set_source(0, seed, extra, rate, constp)
+        sim.step(args.steps)
+        out = sim.fields(0, ("flags", "fill", "id"), out=res)
+        bub = sim.bubbles(0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h2d = flags.nbytes + fill.nbytes + rho.nbytes + u.nbytes
+        d2h = sum(a.nbytes for a in out.values()) + bub.nbytes
+        e2e = {"value": round(n * args.steps * world / dt / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps),
+               "note": f"{args.steps} steps per upload and read-back (tuning steps included)"}
+        sim.close()
+        del flags, fill, rho, u, res
+
+    cpu = cpu_single = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu, cpu_single = cpu_baselines(args)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": wl_desc, "cells": n, "storage": args.precision,
+                       "gas_fraction": round(gas_fraction(sc), 4),
+                       "bubbles_placed": getattr(sc, "bubbles_placed", None), "bubbles_at_end": nbub,
+                       "input_generation_s": round(gen_s, 1),
+                       "l2": flush.describe() + " before every timed step (the lattice's working set also "
+                             "exceeds L2); steps timed by CUDA events",
+                       "parallelism": f"replicas x{world}",
+                       "labelling_runs_per_step": round(lruns / args.steps, 3),
+                       "cell_counts_liquid_interface_gas_obstacle_lid": [int(c) for c in counts[:5]],
+                       "stream_collide_tuning": tuning,
+                       "mass_drift_rel": float(f"{(mass1 - mass0) / mass0:.3e}"),
+                       "mass_drift_steps": steps_run},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "kernel": KERNEL, "algorithmic_bytes_per_launch": int(abytes),
+                         "avg_launch_ms": round(k1_avg, 5), "peak_source": peak_src,
+                         "timing": "CUDA events on the launching stream around the stream-collide kernel, "
+                                   "second timed pass of the same run"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "variants": variants, "secondary": secondary, "batched": batched,
+            "cpu_baseline_single_thread": cpu_single,
+        }
+        print(json.dumps(line))
 
 
 def run_batched(args, fsl, torch, stream, flush, steps: int = 20):
@@ -380,13 +430,18 @@ def run_batched(args, fsl, torch, stream, flush, steps: int = 20):
         return sum(a.elapsed_time(b) for a, b in ev)
 
     sim = fsl.Simulation.from_scenarios(doms, precision=args.precision, stream=int(stream.cuda_stream))
+    rec = tune(sim)
     r0 = sim.labelling_runs
     ms = timed(lambda: sim.step(1), sim.sync)
     out["batched_mlups"] = round(cells * steps / (ms * 1e-3) / 1e6, 1)
     out["batched_ms_per_step"] = round(ms / steps, 4)
     out["labelling_runs_per_step"] = round((sim.labelling_runs - r0) / (steps + 3), 3)
+    out["tuned_form"] = rec["form_name"]
+    out["tuning_ms_per_form"] = rec["ms_per_form"]
     sim.close()
     sims = [fsl.Simulation.from_scenarios([d], precision=args.precision, stream=int(stream.cuda_stream)) for d in doms]
+    for x in sims:
+        tune(x)
 
     def step_all():
         for x in sims:
@@ -404,37 +459,67 @@ def run_batched(args, fsl, torch, stream, flush, steps: int = 20):
     return out
 
 
-def cpu_baseline(sc, steps: int):
-    """The FP64 oracle as it stands, single-threaded on a host core, on a bounded
-    sample (`steps` steps of the same lattice)."""
+def cpu_sample():
+    """The oracle's bounded sample of the headline workload: the same foam
+    recipe (radii, placement, walls, lid, parameters) on a 128^3 lattice."""
+    from paper_1604_01632_gb300 import scenarios as S
+    return S.foam(n=CPU_SAMPLE_N)
+
+
+def cpu_baselines(args, steps_omp: int = 8, steps_single: int = 3):
+    """The FP64 oracle as it stands on the host cores: its OpenMP build on all
+    cores (os.cpu_count()) and the serial build on one core, on a bounded
+    sample of the headline workload."""
     from oracle import oracle
-    o = oracle.Oracle.from_scenario(sc)
-    t0 = time.perf_counter()
-    o.step(steps)
-    dt = time.perf_counter() - t0
-    return {"value": round(sc.n * steps / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of the full {sc.nx}x{sc.ny}x{sc.nz} lattice ({dt:.1f} s)"}
+    sc = cpu_sample()
+    cores = os.cpu_count() or 1
+    res = []
+    for openmp, steps in ((True, steps_omp), (False, steps_single)):
+        try:
+            o = oracle.Oracle.from_scenario(sc, openmp=openmp)
+        except RuntimeError:
+            res.append(None)
+            continue
+        o.step(1)
+        t0 = time.perf_counter()
+        o.step(steps)
+        dt = time.perf_counter() - t0
+        res.append({"value": round(sc.n * steps / dt / 1e6, 3), "unit": UNIT, "cores": cores if openmp else 1,
+                    "kind": "oracle",
+                    "sample": f"{steps} steps of the foam recipe at {CPU_SAMPLE_N}^3 ({sc.n} cells) after one "
+                              f"untimed step, {'OpenMP build, all host cores' if openmp else 'serial build'} "
+                              f"({dt:.1f} s)"})
+    return res[0] or res[1], res[1]
 
 
 def run_reference(args, rank: int):
     if rank != 0:
         return
-    sc, wl_desc = workload(args.workload)
     from oracle import oracle
-    o = oracle.Oracle.from_scenario(sc)
+    sc = cpu_sample()
+    cores = os.cpu_count() or 1
+    try:
+        o = oracle.Oracle.from_scenario(sc, openmp=True)
+        kind = "OpenMP build, all host cores"
+    except RuntimeError:
+        o = oracle.Oracle.from_scenario(sc)
+        kind, cores = "serial build (no OpenMP support)", 1
     steps = max(1, args.steps)
     o.step(max(0, args.warmup))
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
     value = sc.n * steps / dt / 1e6
+    _, wl_desc = ("", "foam 512^3 (headline workload); each reference step is one oracle step of the same foam "
+                      f"recipe at {CPU_SAMPLE_N}^3")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True,
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(dt / steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl_desc, "cells": sc.n, "storage": "fp64"},
-        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{steps} timed steps of the full lattice after {args.warmup} untimed"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} timed steps of the {CPU_SAMPLE_N}^3 foam after {args.warmup} untimed, "
+                                   f"{kind}"},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -442,18 +527,17 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fsl", choices=["fsl", "reference"])
     ap.add_argument("--precision", default="f16s", choices=list(BYTES))
-    ap.add_argument("--workload", default="gas_thread")
-    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--workload", default="foam512")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="direct kernel launches (for ncu)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-scale", action="store_true", help="skip the larger-lattice measurements")
     ap.add_argument("--flush", default="write+read", choices=["write", "write+read"],
                     help="L2 flush between timed steps")
     args = ap.parse_args()

@@ -148,6 +148,12 @@ fsl_status fsl_bubbles(fsl_domain* h, int32_t d, fsl_bubble* out, int64_t cap, i
  * Synchronises. */
 fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst, int32_t on_device);
 
+/* Liquid mass of domain d (paper Eq. 9 and the mass balance of Eq. 10):
+ * the density of the stored PDFs summed over liquid cells, plus the mass m of
+ * the interface cells, plus excess mass pooled and not yet shared out.  Summed
+ * in a fixed order (the same value for the same state).  Synchronises. */
+fsl_status fsl_total_mass(fsl_domain* h, int32_t d, double* mass);
+
 /* Free the handle and its device memory. */
 fsl_status fsl_destroy(fsl_domain* h);
 
@@ -190,6 +196,43 @@ fsl_status fsl_set_graphs(fsl_domain* h, int32_t on);
  * Waits for the handle's stream; the next fsl_step rebuilds its graphs.
  * FSL_ERR_ARG for values out of range. */
 fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_polls, int32_t barrier_absent);
+
+/* Form of the stream-collide kernel (the same results in every form; each
+ * cell runs the same arithmetic).  By default (form -1) the library tunes it:
+ * the first fsl_step calls of a handle run eight real steps that each time
+ * one candidate form (every form twice, direct launches, the call waits for
+ * each), then keep the fastest and record it in a process-wide cache keyed by
+ * precision, one or many domains, SM count, lattice size (log2 of the padded
+ * cells) and interface share (1/64 steps); a later handle of the same key
+ * takes the cached form without tuning.  Forms:
+ *   0  split: blocks [0, 2 x SMs) take the interface list in 32-cell chunks
+ *      (16 in FP64), the other blocks one liquid tile each;
+ *   1, 2, 3  persistent: a resident grid walks one sequence of work items in
+ *      which the interface chunks are spread evenly among liquid items of 1,
+ *      2 or 4 tiles (a tile is 512 cells in the 16-bit forms, 256 otherwise).
+ * -1 restarts the tuning.  Waits for the handle's stream; the next fsl_step
+ * rebuilds its graphs.  FSL_ERR_ARG for another value.  fsl_stream_form
+ * returns the form in use (the one tried next while tuning). */
+fsl_status fsl_set_stream_form(fsl_domain* h, int32_t form);
+int32_t fsl_stream_form(const fsl_domain* h);
+
+/* Autotuner record of the handle: ms_per_form (array of 4, may be NULL) the
+ * fastest stream-collide time measured per form (0 = not run); *form the
+ * chosen form (-1 while tuning); *source 0 = not decided, 1 = measured on
+ * this handle, 2 = from the process cache, 3 = set by the caller. */
+fsl_status fsl_tuning(const fsl_domain* h, double* ms_per_form, int32_t* form, int32_t* source);
+
+/* Empty the process-wide tuning cache. */
+fsl_status fsl_forget_tuning(void);
+
+/* Order of the interface list the stream-collide kernel walks: 1 = rebuilt
+ * after each step's conversion in increasing cell index (two passes over the
+ * cell types), 0 = in the order the conversion kernel appends it, -1 (default)
+ * = 1 where the two PDF arrays exceed twice the L2 cache.  The same results in
+ * every mode.  Waits for the handle's stream; FSL_ERR_ARG for another value.
+ * fsl_interface_order returns the mode in effect (0 or 1). */
+fsl_status fsl_set_interface_order(fsl_domain* h, int32_t mode);
+int32_t fsl_interface_order(const fsl_domain* h);
 
 /* Device time per phase of the steps timed since fsl_set_timing(h, 1), summed,
  * in milliseconds, when the handle runs without graphs (fsl_set_graphs(h, 0)):

@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <utility>
 #include <string>
 #include <vector>
@@ -23,6 +25,27 @@ namespace {
 
 const int kDefaultCapacityMin = 256;
 
+// Candidate sequence of the autotuner: every form twice, the faster of its two
+// timed steps counts.
+const int kTuneSeq[] = {SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4};
+const int kTuneSteps = (int)(sizeof(kTuneSeq) / sizeof(kTuneSeq[0]));
+
+// Process-wide cache of tuning decisions, keyed by the workload's shape:
+// storage precision, one or many domains, SM count, lattice size (log2 of the
+// padded cells) and the interface share (in 1/64 steps) at tuning time.
+struct TuneKey {
+    int prec, multi, sms, lsize, ifrac;
+    bool operator<(const TuneKey& o) const {
+        if (prec != o.prec) return prec < o.prec;
+        if (multi != o.multi) return multi < o.multi;
+        if (sms != o.sms) return sms < o.sms;
+        if (lsize != o.lsize) return lsize < o.lsize;
+        return ifrac < o.ifrac;
+    }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune_cache;
+
 }  // namespace
 
 struct fsl_domain {
@@ -33,6 +56,18 @@ struct fsl_domain {
     cudaStream_t ls = nullptr;    // library stream (capturable)
 
     int ifblocks = 304;           // grid of the list kernels (2 blocks per SM)
+    int form = SC_SPLIT;          // stream-collide kernel form in use
+    // autotuner: while `tuning`, each step runs the next candidate form with
+    // CUDA events around its stream-collide kernel (direct launches)
+    bool tuning = true;           // auto mode and not yet decided
+    int tune_next = 0;            // index into the candidate sequence
+    double tune_ms[SC_FORMS] = {0, 0, 0, 0};   // best measured time per form (0: not run)
+    int tune_source = 0;          // 0 none yet, 1 measured here, 2 taken from the process cache, 3 fixed by the caller
+    cudaEvent_t tev[2] = {nullptr, nullptr};
+    int order_mode = -1;          // interface list in cell order: 1 on, 0 off, -1 by lattice size
+    long long l2bytes = 0;        // L2 cache of the device
+    int* ocnt = nullptr;          // interface cells per conversion block (ordered rebuild)
+    int pgrid[SC_FORMS] = {0, 0, 0, 0};   // resident grid of each persistent form
     int convblocks = 152;         // grid of the cooperative conversion kernel
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
@@ -70,10 +105,15 @@ struct fsl_domain {
     long long* hvals = nullptr;
     long long hcap = 0;
     long long *nvfx = nullptr, *nvxfx = nullptr, *nvsfx = nullptr, *nncells = nullptr;
-    int *nconstp = nullptr, *croot = nullptr, *minc = nullptr, *nslot = nullptr;
+    int *nconstp = nullptr, *croot = nullptr, *minc = nullptr;
+    int *hused = nullptr, *nhused = nullptr, *nused = nullptr, *nfree = nullptr, *freelist = nullptr;
+    int *aff = nullptr, *afflist = nullptr, *naff = nullptr, *plist = nullptr, *np = nullptr;
+    int *newslots = nullptr, *nnew = nullptr;
     long long* vtot = nullptr;
     int* minidx = nullptr;
     long long* counts = nullptr;
+    double* mass_part = nullptr;  // per-block liquid-mass sums (fsl_total_mass)
+    long long max_dom_blocks = 1;
     long long* runs = nullptr;
 
     std::vector<bool> inited;
@@ -154,6 +194,16 @@ cudaError_t staging(fsl_domain* h, const size_t* bytes, int n, void** parts) {
     return cudaSuccess;
 }
 
+// Whether the conversion kernel rebuilds the interface list in cell order: by
+// default where the two PDF arrays of a step exceed twice the L2 cache (there
+// an interface cell's neighbour data would otherwise come from DRAM again for
+// every cell that reads it; the rebuild reads the cell types twice).
+int order_effective(const fsl_domain* h) {
+    if (h->order_mode >= 0) return h->order_mode;
+    const double pdf_bytes = 2.0 * 19.0 * (double)h->stride * (double)h->fbytes;
+    return h->l2bytes > 0 && pdf_bytes > 2.0 * (double)h->l2bytes ? 1 : 0;
+}
+
 StepArgs step_args(fsl_domain* h, int src) {
     StepArgs A;
     A.doms = h->d_doms;
@@ -181,6 +231,8 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.trig = h->trig;
     A.status = h->status;
     A.bar = h->bar;
+    A.order = order_effective(h);
+    A.ocnt = h->ocnt;
     A.spins = h->spins;
     A.bar_extra = h->bar_extra;
     A.ndom = h->ndom;
@@ -217,9 +269,19 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     K.croot = h->croot;
     K.vtot = h->vtot;
     K.minc = h->minc;
-    K.nslot = h->nslot;
+    K.hused = h->hused;
+    K.nhused = h->nhused;
+    K.nused = h->nused;
+    K.nfree = h->nfree;
+    K.freelist = h->freelist;
+    K.aff = h->aff;
+    K.afflist = h->afflist;
+    K.naff = h->naff;
+    K.plist = h->plist;
+    K.np = h->np;
+    K.newslots = h->newslots;
+    K.nnew = h->nnew;
     K.slot_dom = h->d_slot_dom;
-    K.nslots_total = h->nslots;
     K.runs = h->runs;
     K.vsfx = h->vsfx;
     K.constp = h->constp;
@@ -231,12 +293,24 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     return K;
 }
 
-void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st, cudaEvent_t el = nullptr, cudaEvent_t ei = nullptr) {
+void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st, cudaEvent_t el = nullptr, cudaEvent_t ei = nullptr,
+               int form = -1) {
+    if (form < 0) form = h->form;
+    const int pg = h->pgrid[form];
     switch (h->precision) {
-    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
-    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
-    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
-    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, st, nullptr, nullptr, nullptr, el, ei); break;
+    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
+    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
+    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
+    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
+    }
+}
+
+int stream_occupancy(int precision, int form, bool one) {
+    switch (precision) {
+    case FSL_P_FP64: return stream_blocks_per_sm<double>(form, one);
+    case FSL_P_FP32: return stream_blocks_per_sm<float>(form, one);
+    case FSL_P_F16S: return stream_blocks_per_sm<__half>(form, one);
+    default: return stream_blocks_per_sm<__nv_bfloat16>(form, one);
     }
 }
 
@@ -345,6 +419,20 @@ fsl_status ensure_initial(fsl_domain* h) {
     for (int d = 0; d < h->ndom; ++d)
         if (!h->inited[d]) return fail(h, FSL_ERR_ARG, "every domain must be initialised first");
     StepArgs A = step_args(h, h->cur);
+    // the initial pass hands out every slot afresh and rebuilds every table row
+    const size_t NS = (size_t)h->nslots;
+    CK(h, cudaMemsetAsync(h->nused, 0, 4 * (size_t)h->ndom, h->ls));
+    CK(h, cudaMemsetAsync(h->nfree, 0, 4 * (size_t)h->ndom, h->ls));
+    CK(h, cudaMemsetAsync(h->aff, 0, 4 * NS, h->ls));
+    CK(h, cudaMemsetAsync(h->naff, 0, sizeof(int), h->ls));
+    CK(h, cudaMemsetAsync(h->np, 0, sizeof(int), h->ls));
+    CK(h, cudaMemsetAsync(h->nnew, 0, sizeof(int), h->ls));
+    CK(h, cudaMemsetAsync(h->nhused, 0, sizeof(int), h->ls));
+    CK(h, cudaMemsetAsync(h->vfx, 0, 8 * NS, h->ls));
+    CK(h, cudaMemsetAsync(h->vxfx, 0, 8 * NS, h->ls));
+    CK(h, cudaMemsetAsync(h->vsfx, 0, 8 * NS, h->ls));
+    CK(h, cudaMemsetAsync(h->ncells, 0, 8 * NS, h->ls));
+    CK(h, cudaMemsetAsync(h->constp, 0, 4 * NS, h->ls));
     h->launches += launch_ccl(A, ccl_args(h, 1), h->nblocks, h->ls);
     CK(h, cudaMemsetAsync(h->icount[h->cur], 0, sizeof(int), h->ls));
     CK(h, cudaMemsetAsync(h->icnt, 0, 8 * (size_t)h->ndom, h->ls));
@@ -481,6 +569,11 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         const int per_sm = conv_blocks_per_sm(precision);
         if (per_sm < 1) e = cudaErrorInvalidConfiguration;
         h->convblocks = std::max(1, sms) * std::max(1, per_sm);
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        h->l2bytes = l2;
+        for (int f = SC_PERS1; f < SC_FORMS; ++f)
+            h->pgrid[f] = std::max(1, sms) * std::max(1, stream_occupancy(precision, f, n_domains == 1));
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
@@ -540,9 +633,23 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->croot, 4 * NS);
     AL(h->minc, 4 * NS);
     AL(h->vtot, 8 * NS);
-    AL(h->nslot, 4 * n_domains);
+    AL(h->ocnt, 4 * (size_t)h->convblocks);
+    AL(h->hused, 4 * (size_t)hc);
+    AL(h->nhused, sizeof(int));
+    AL(h->nused, 4 * n_domains);
+    AL(h->nfree, 4 * n_domains);
+    AL(h->freelist, 4 * NS);
+    AL(h->aff, 4 * NS);
+    AL(h->afflist, 4 * NS);
+    AL(h->naff, sizeof(int));
+    AL(h->plist, 4 * N);
+    AL(h->np, sizeof(int));
+    AL(h->newslots, 4 * NS);
+    AL(h->nnew, sizeof(int));
     AL(h->minidx, 4 * NS);
     AL(h->counts, 8 * 8);
+    for (const Dom& D : h->hdoms) h->max_dom_blocks = std::max(h->max_dom_blocks, ((long long)D.n + FSL_BLOCK - 1) / FSL_BLOCK);
+    AL(h->mass_part, 8 * (size_t)h->max_dom_blocks);
     AL(h->runs, 8);
 #undef AL
     if (e != cudaSuccess) {
@@ -586,6 +693,16 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->vsfx, 0, 8 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->ncells, 0, 8 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->constp, 0, 4 * NS);
+    // labelling: empty overlap hash, no marked bubble, no slot handed out
+    if (e == cudaSuccess) e = cudaMemset(h->hkeys, 0xff, 8 * (size_t)hc);
+    if (e == cudaSuccess) e = cudaMemset(h->hvals, 0, 8 * (size_t)hc);
+    if (e == cudaSuccess) e = cudaMemset(h->aff, 0, 4 * NS);
+    if (e == cudaSuccess) e = cudaMemset(h->naff, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->np, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->nnew, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->nhused, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->nused, 0, 4 * n_domains);
+    if (e == cudaSuccess) e = cudaMemset(h->nfree, 0, 4 * n_domains);
     if (e != cudaSuccess) {
         fsl_destroy(h);
         return FSL_ERR_CUDA;
@@ -667,6 +784,72 @@ fsl_status fsl_set_bubble_source(fsl_domain* h, int32_t d, int64_t seed_cell, do
     return FSL_OK;
 }
 
+static void drop_graphs(fsl_domain* h);
+
+namespace {
+
+TuneKey tune_key(fsl_domain* h, int icount) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int lsize = 0;
+    while ((1LL << (lsize + 1)) <= h->stride) ++lsize;
+    return TuneKey{h->precision, h->ndom > 1 ? 1 : 0, sms, lsize, (int)(64LL * icount / std::max(1LL, h->stride))};
+}
+
+// One autotuning step: the next candidate form, its stream-collide kernel
+// bracketed by events and timed (the call waits for it).  After the last
+// candidate the fastest form is kept and recorded in the process cache.
+fsl_status tune_step(fsl_domain* h) {
+    if (h->tune_next == 0) {
+        int ic = 0;
+        CK(h, cudaMemcpyAsync(&ic, h->icount[h->cur], sizeof(int), cudaMemcpyDeviceToHost, h->ls));
+        CK(h, cudaStreamSynchronize(h->ls));
+        const TuneKey key = tune_key(h, ic);
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->form = it->second;
+            h->tuning = false;
+            h->tune_source = 2;
+            return FSL_OK;   // no step taken: the caller runs it with the cached form
+        }
+    }
+    const int f = kTuneSeq[h->tune_next];
+    if (!h->tev[0]) {
+        CK(h, cudaEventCreate(&h->tev[0]));
+        CK(h, cudaEventCreate(&h->tev[1]));
+    }
+    StepArgs A = step_args(h, h->cur);
+    CK(h, cudaEventRecord(h->tev[0], h->ls));
+    launch_k1(h, A, h->ls, nullptr, nullptr, f);
+    CK(h, cudaEventRecord(h->tev[1], h->ls));
+    CK(h, launch_conv(h, A, h->ls));
+    h->launches += 2;
+    h->cur = 1 - h->cur;
+    CK(h, cudaEventSynchronize(h->tev[1]));
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]));
+    if (h->tune_ms[f] == 0.0 || ms < h->tune_ms[f]) h->tune_ms[f] = ms;
+    if (++h->tune_next == kTuneSteps) {
+        int best = SC_SPLIT;
+        for (int g = 0; g < SC_FORMS; ++g)
+            if (h->tune_ms[g] > 0.0 && h->tune_ms[g] < h->tune_ms[best]) best = g;
+        h->form = best;
+        h->tuning = false;
+        h->tune_source = 1;
+        int ic = 0;
+        CK(h, cudaMemcpyAsync(&ic, h->icount[h->cur], sizeof(int), cudaMemcpyDeviceToHost, h->ls));
+        CK(h, cudaStreamSynchronize(h->ls));
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[tune_key(h, ic)] = best;
+        drop_graphs(h);
+    }
+    return FSL_OK;
+}
+
+}  // namespace
+
 fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
     if (!h || nsteps < 0) return fail(h, FSL_ERR_ARG, "bad argument");
     fsl_status st = ensure_initial(h);
@@ -674,6 +857,20 @@ fsl_status fsl_step(fsl_domain* h, int64_t nsteps) {
     h->stepped = true;
     join_in(h);
     int64_t k = 0;
+    // autotuning steps first (each a real step of the simulation)
+    while (h->tuning && k < nsteps) {
+        const int before = h->cur;
+        st = tune_step(h);
+        if (st != FSL_OK) return st;
+        if (h->cur != before) ++k;   // a cache hit decides without a step
+    }
+    if (k == nsteps) {
+        CK(h, cudaGetLastError());
+        join_out(h);
+        return FSL_OK;
+    }
+    nsteps -= k;
+    k = 0;
     if (!h->graphs) {
         // direct launches
         for (; k < nsteps; ++k) {
@@ -760,6 +957,8 @@ fsl_status fsl_phase_ms(const fsl_domain* h, double* out) {
     return FSL_OK;
 }
 
+static void drop_graphs(fsl_domain* h);
+
 fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_polls, int32_t barrier_absent) {
     if (!h) return FSL_ERR_ARG;
     if (ccl_max_iter < 0 || ccl_max_iter > INT_MAX || barrier_polls < 0 || barrier_polls > INT_MAX ||
@@ -769,14 +968,62 @@ fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_p
     h->ccl_cap = ccl_max_iter > 0 ? (int)ccl_max_iter : (1 << 24);
     h->spins = barrier_polls > 0 ? (int)barrier_polls : (1 << 22);
     h->bar_extra = barrier_absent;
-    // the step graphs hold the old values in their kernel parameters
+    drop_graphs(h);   // the step graphs hold the old values in their kernel parameters
+    return FSL_OK;
+}
+
+static void drop_graphs(fsl_domain* h) {
     for (int k = 0; k < 2; ++k)
         for (int j = 0; j < 3; ++j)
             if (h->graph[k][j]) { cudaGraphExecDestroy(h->graph[k][j]); h->graph[k][j] = nullptr; }
     for (int k = 0; k < 2; ++k)
         if (h->timed_src[k]) { cudaGraphDestroy(h->timed_src[k]); h->timed_src[k] = nullptr; }
+}
+
+fsl_status fsl_set_stream_form(fsl_domain* h, int32_t form) {
+    if (!h || form < -1 || form >= SC_FORMS) return fail(h, FSL_ERR_ARG, "bad stream-collide form");
+    CK(h, cudaStreamSynchronize(h->ls));
+    if (form < 0) {
+        // autotune again from the next step on (the process cache is consulted first)
+        h->tuning = true;
+        h->tune_next = 0;
+        for (int f = 0; f < SC_FORMS; ++f) h->tune_ms[f] = 0.0;
+        h->tune_source = 0;
+    } else {
+        h->form = form;
+        h->tuning = false;
+        h->tune_source = 3;
+    }
+    drop_graphs(h);   // the step graphs hold the previous kernel
     return FSL_OK;
 }
+
+fsl_status fsl_tuning(const fsl_domain* h, double* ms_per_form, int32_t* form, int32_t* source) {
+    if (!h) return FSL_ERR_ARG;
+    if (ms_per_form)
+        for (int f = 0; f < SC_FORMS; ++f) ms_per_form[f] = h->tune_ms[f];
+    if (form) *form = h->tuning ? -1 : h->form;
+    if (source) *source = h->tune_source;
+    return FSL_OK;
+}
+
+fsl_status fsl_forget_tuning(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache.clear();
+    return FSL_OK;
+}
+
+int32_t fsl_stream_form(const fsl_domain* h) { return h ? h->form : -1; }
+
+fsl_status fsl_set_interface_order(fsl_domain* h, int32_t mode) {
+    if (!h || mode < -1 || mode > 1) return fail(h, FSL_ERR_ARG, "bad interface-order mode");
+    CK(h, cudaStreamSynchronize(h->ls));
+    h->order_mode = mode;
+    drop_graphs(h);
+    return FSL_OK;
+}
+
+int32_t fsl_interface_order(const fsl_domain* h) { return h ? order_effective(h) : -1; }
 
 fsl_status fsl_set_graphs(fsl_domain* h, int32_t on) {
     if (!h) return FSL_ERR_ARG;
@@ -926,6 +1173,34 @@ fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts) {
     return latch(h);
 }
 
+fsl_status fsl_total_mass(fsl_domain* h, int32_t d, double* mass) {
+    if (!h || d < 0 || d >= h->ndom || !mass) return fail(h, FSL_ERR_ARG, "bad argument");
+    fsl_status st = ensure_initial(h);
+    if (st != FSL_OK) return st;
+    join_in(h);
+    const Dom& D = h->hdoms[d];
+    const long long nb = ((long long)D.n + FSL_BLOCK - 1) / FSL_BLOCK;
+    switch (h->precision) {
+    case FSL_P_FP64: launch_mass_partials<double>(h->f[h->cur], h->flag, h->m, h->stride, D.off, D.n, h->mass_part, h->ls); break;
+    case FSL_P_FP32: launch_mass_partials<float>(h->f[h->cur], h->flag, h->m, h->stride, D.off, D.n, h->mass_part, h->ls); break;
+    case FSL_P_F16S: launch_mass_partials<__half>(h->f[h->cur], h->flag, h->m, h->stride, D.off, D.n, h->mass_part, h->ls); break;
+    default: launch_mass_partials<__nv_bfloat16>(h->f[h->cur], h->flag, h->m, h->stride, D.off, D.n, h->mass_part, h->ls); break;
+    }
+    h->launches += 1;
+    CK(h, cudaGetLastError());
+    std::vector<double> part((size_t)nb);
+    long long pool = 0;
+    CK(h, cudaMemcpyAsync(part.data(), h->mass_part, 8 * (size_t)nb, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaMemcpyAsync(&pool, h->pool + d, 8, cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaStreamSynchronize(h->ls));
+    double t = 0.0;
+    for (double v : part) t += v;
+    // excess mass pooled and not yet shared out (fixed point 2^-40)
+    *mass = t + (double)pool * 9.094947017729282379150390625e-13;
+    join_out(h);
+    return latch(h);
+}
+
 fsl_status fsl_destroy(fsl_domain* h) {
     if (!h) return FSL_ERR_ARG;
     if (h->ls) cudaStreamSynchronize(h->ls);
@@ -935,6 +1210,8 @@ fsl_status fsl_destroy(fsl_domain* h) {
     for (int k = 0; k < 2; ++k)
         if (h->timed_src[k]) cudaGraphDestroy(h->timed_src[k]);
     for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->tev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : h->phpool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     if (h->stage) cudaFree(h->stage);

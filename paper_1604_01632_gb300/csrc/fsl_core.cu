@@ -31,30 +31,12 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_build_ilist(StepArgs A) {
 
 // --------------------------------------------- connected-component labelling
 
-__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_init(StepArgs A, CclArgs K) {
-    if (!K.initial && *A.trig == 0) return;
-    ccl_init_phase(A, K);
-}
-__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_hook(StepArgs A, CclArgs K) {
-    if (!K.initial && *A.trig == 0) return;
-    ccl_hook_phase(A, K);
-}
-__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_compress(StepArgs A, CclArgs K) {
-    if (!K.initial && *A.trig == 0) return;
-    ccl_compress_phase(A, K);
-}
-__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_pairs(StepArgs A, CclArgs K) {
-    if (!K.initial && *A.trig == 0) return;
-    ccl_pairs_phase(A, K);
-}
-__global__ void k_ccl_table(StepArgs A, CclArgs K) {
-    if (K.initial || *A.trig == 0) return;
-    ccl_table_phase(A, K);
-}
-__global__ void k_ccl_install(StepArgs A, CclArgs K) {
-    if (!K.initial && *A.trig == 0) return;
-    ccl_install_phase(A, K);
-}
+// The labelling phases of the initial pass (every bubble), one kernel each.
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_init(StepArgs A, CclArgs K) { ccl_init_phase(A, K); }
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_hook(StepArgs A, CclArgs K) { ccl_hook_phase(A, K); }
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_compress(StepArgs A, CclArgs K) { ccl_compress_phase(A, K); }
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_pairs(StepArgs A, CclArgs K) { ccl_pairs_phase(A, K); }
+__global__ void __launch_bounds__(FSL_BLOCK) k_ccl_install(StepArgs A, CclArgs K) { ccl_install_phase(A, K); }
 
 // ------------------------------------------------------------------ exports
 
@@ -92,16 +74,15 @@ __global__ void k_export_cells(const uint8_t* flag, const double* phi, const dou
 
 void launch_build_ilist(const StepArgs& A, long long nb, cudaStream_t s) { k_build_ilist<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A); }
 
+// Initial labelling (K.initial = 1): the list phases run over a grid of one
+// thread per cell, which covers the participant list whatever its length.
 int launch_ccl(const StepArgs& A, const CclArgs& K, long long nb, cudaStream_t s) {
     k_ccl_init<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
     k_ccl_hook<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
     k_ccl_compress<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
     k_ccl_pairs<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
-    const unsigned tb = (unsigned)((K.hcap + 255) / 256);
-    k_ccl_table<<<tb > 0 ? tb : 1, 256, 0, s>>>(A, K);
-    const unsigned ib = (unsigned)((K.nslots_total + 255) / 256);
-    k_ccl_install<<<ib > 0 ? ib : 1, 256, 0, s>>>(A, K);
-    return 6;
+    k_ccl_install<<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A, K);
+    return 5;
 }
 
 void launch_export_minid(const int* id, long long off, int n, int* minidx, cudaStream_t s) {

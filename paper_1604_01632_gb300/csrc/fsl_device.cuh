@@ -144,6 +144,9 @@ struct StepArgs {
     int* stepno;                // device step counter
     long long* icnt;            // per-domain interface count at the end of the step
     unsigned* bar;              // grid barrier of the conversion kernel: count, generation
+    int order;                  // 1: the conversion kernel rebuilds the next interface list in
+                                // cell order (after phase D), 0: phase D appends it
+    int* ocnt;                  // interface cells per conversion block (ordered rebuild)
     int spins;                  // polls a block waits at a grid barrier before it gives up
     int bar_extra;              // arrivals a barrier waits for beyond the grid (0; 1 only to
                                 // test the timeout path: no block is then the last)
@@ -973,28 +976,30 @@ __device__ inline void ph_row(int r, int& dy, int& dz) {
     }
 }
 
-// Block `bid` of the `nbl` blocks of the interface part of the stream-collide
-// kernel.
+// Per-step counters, reset by one block of the stream-collide kernel (the
+// previous step's kernels are done with them; nothing in the stream-collide
+// kernel reads them).
+__device__ inline void step_counters(const StepArgs& A) {
+    for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
+        if (A.nif[d] > 0) A.pool[d] = 0;   // the pool was shared out last step
+        A.nif[d] = A.icnt[d];
+        A.trig[1 + d] = 0;
+    }
+    if (threadIdx.x == 0) {
+        *A.stepno += 1;
+        *A.gcount = 0;
+        *A.lcount = 0;
+        *A.trig = 0;
+    }
+}
+
+// One pass over the interface cells i0 .. i0 + N - 1 of the list (those below
+// cnt), by the whole block; ends with a block barrier.
 template <typename T, bool ONE>
-__device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int nbl, IfStage<T>& sh) {
+__device__ __forceinline__ void interface_chunk(const StepArgs& A, int i0, int cnt, IfStage<T>& sh) {
     using C = typename Form<T>::C;
     constexpr int N = IfCells<T>::n;
     constexpr int TPC = FSL_BLOCK / N;   // threads per cell
-    if (bid == 0) {
-        // per-step counters; the previous step's kernels are done with them
-        for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) {
-            if (A.nif[d] > 0) A.pool[d] = 0;   // the pool was shared out last step
-            A.nif[d] = A.icnt[d];
-            A.trig[1 + d] = 0;
-        }
-        if (threadIdx.x == 0) {
-            *A.stepno += 1;
-            *A.gcount = 0;
-            *A.lcount = 0;
-            *A.trig = 0;
-        }
-    }
-    const int cnt = *A.icount;
     const unsigned S = (unsigned)A.stride;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
@@ -1005,7 +1010,7 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
     else { phic = A.phif; phtc = A.phitf; }
     const int c = threadIdx.x / TPC;      // cell of this thread in the load and gradient phases
     const int q = threadIdx.x % TPC;
-    for (int i0 = bid * N; i0 < cnt; i0 += nbl * N) {
+    {
         // ---------------- load phase: every global load of the thread is
         // issued before the first shared-memory store, so that the phase costs
         // about two memory latencies (the list entry, then everything else)
@@ -1243,6 +1248,16 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
     }
 }
 
+// Block `bid` of the `nbl` blocks of the interface part of the split
+// stream-collide kernel: list chunks bid, bid + nbl, bid + 2 nbl, ...
+template <typename T, bool ONE>
+__device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int nbl, IfStage<T>& sh) {
+    constexpr int N = IfCells<T>::n;
+    if (bid == 0) step_counters(A);
+    const int cnt = *A.icount;
+    for (int i0 = bid * N; i0 < cnt; i0 += nbl * N) interface_chunk<T, ONE>(A, i0, cnt, sh);
+}
+
 // The stream-collide step (Eqs. 6, 7, 10, 11) as one kernel: blocks
 // [0, nif) take the interface cells from the list (they are launched first,
 // so they are placed first), the other blocks the liquid cells.
@@ -1258,6 +1273,50 @@ __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream(St
         liquid_single<T, ONE>(A, (long long)blockIdx.x - nif);
     }
 }
+
+// Persistent form of the stream-collide kernel: a grid of resident blocks
+// walks one sequence of work items in which the interface chunks (N list
+// cells each) are spread evenly among the liquid items (LT tiles each): with
+// nI chunks and nL liquid items, M = nI + nL, item w is chunk floor(w nI / M)
+// when floor((w + 1) nI / M) > floor(w nI / M), else liquid item
+// w - floor(w nI / M).  Block b takes items b, b + grid, b + 2 grid, ...  Every
+// block does both kinds of work (the interface cells' latency chains overlap
+// the liquid cells' streaming), and with the interface list in cell order the
+// items in flight at any time lie close together in the lattice.  Results are
+// those of the split form: every cell runs the same arithmetic.
+template <typename T, bool ONE, int LT>
+__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream_pers(StepArgs A) {
+    __shared__ IfStage<T> sh;
+    pdl_trigger();   // the conversion kernel may be placed as blocks finish
+    if (blockIdx.x == 0) step_counters(A);
+    constexpr int N = IfCells<T>::n;
+    constexpr long long TILE = Form<T>::shifted ? 2 * FSL_BLOCK : FSL_BLOCK;
+    const int cnt = *A.icount;
+    const long long nI = (cnt + N - 1) / N;
+    const long long ntile = (A.stride + TILE - 1) / TILE;
+    const long long nL = (ntile + LT - 1) / LT;
+    const long long M = nI + nL;
+    for (long long w = blockIdx.x; w < M; w += gridDim.x) {
+        const long long c0 = (w * nI) / M, c1 = ((w + 1) * nI) / M;
+        if (c1 > c0) {
+            interface_chunk<T, ONE>(A, (int)(c0 * N), cnt, sh);
+        } else {
+            const long long t0 = (w - c0) * LT;
+#pragma unroll 1
+            for (int k = 0; k < LT; ++k) {
+                const long long tile = t0 + k;
+                if (tile >= ntile) break;
+                if constexpr (Form<T>::shifted) liquid_pairs<T, ONE>(A, tile);
+                else liquid_single<T, ONE>(A, tile);
+            }
+        }
+    }
+}
+
+// Stream-collide kernel forms (the autotuner picks one per workload): the split
+// form (interface blocks first, then one block per liquid tile) and the
+// persistent form with 1, 2 or 4 tiles per liquid item.
+enum { SC_SPLIT = 0, SC_PERS1 = 1, SC_PERS2 = 2, SC_PERS4 = 3, SC_FORMS = 4 };
 
 // First neighbour of cell z (direction order) that is an interface cell
 // carrying mark `want`, or -1.
@@ -1481,13 +1540,146 @@ __device__ inline bool removal_is_local(unsigned fg) {
     return (targets & ~reach) == 0;
 }
 
+// ------------------------------------------- interface list in cell order
+// On lattices much larger than the L2 cache the next step's interface list is
+// rebuilt from the cell types after phase D, in increasing cell index, so that
+// the stream-collide work items in flight at any time lie close together and
+// share their neighbours' data in L2 (the list phase D appends is in the order
+// its warps finish).  Block b of the conversion kernel owns 16-cell groups
+// [G b / nb, G (b + 1) / nb), G = cells / 16 (the padded lattice is a multiple
+// of 256 cells, the type array 256-byte aligned).
+
+__device__ inline void order_range(const StepArgs& A, long long& lo, long long& hi) {
+    const long long G = A.stride / 16, nb = gridDim.x;
+    lo = G * blockIdx.x / nb;
+    hi = G * (blockIdx.x + 1) / nb;
+}
+
+// Bit k set when cell 16 j + k is an interface cell (one 16-byte load).
+__device__ inline unsigned ifc_mask16(const uint8_t* flag, long long j) {
+    const uint4 v = ((const uint4*)flag)[j];
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) m |= (unsigned)(((w[k >> 2] >> (8 * (k & 3))) & K_TYPE) == IFC) << k;
+    return m;
+}
+
+// Exclusive prefix sum of v over the block (a multiple of 32 threads, at most
+// 1024); *total receives the block's sum.  Every thread must call; ends with
+// a barrier.
+__device__ inline int block_exclusive_sum(int v, int* total) {
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) wsum[lane] = t;   // inclusive sums over the warps
+    }
+    __syncthreads();
+    const int before = w > 0 ? wsum[w - 1] : 0;
+    *total = wsum[nw - 1];
+    __syncthreads();                      // wsum is reused by the next call
+    return before + x - v;
+}
+
+// Pass 1: interface cells in each block's range.
+__device__ inline void order_count_phase(const StepArgs& A) {
+    long long lo, hi;
+    order_range(A, lo, hi);
+    int n = 0;
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) n += __popc(ifc_mask16(A.flag, j));
+    int tot;
+    block_exclusive_sum(n, &tot);
+    if (threadIdx.x == 0) A.ocnt[blockIdx.x] = tot;
+}
+
+// Pass 2: each block writes its interface cells in order after those of the
+// blocks before it; the last block stores the list length.
+__device__ inline void order_write_phase(const StepArgs& A) {
+    long long lo, hi;
+    order_range(A, lo, hi);
+    int part = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) part += A.ocnt[k];
+    int off;
+    block_exclusive_sum(part, &off);
+    for (long long j0 = lo; j0 < hi; j0 += blockDim.x) {
+        const long long j = j0 + threadIdx.x;
+        const unsigned m = j < hi ? ifc_mask16(A.flag, j) : 0u;
+        int tot;
+        int pos = off + block_exclusive_sum(__popc(m), &tot);
+        for (unsigned b = m; b; b &= b - 1) A.ilist_next[pos++] = (int)(16 * j + (__ffs(b) - 1));
+        off += tot;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *A.icount_next = off;
+}
+
+// Scratch of the connected-component labelling and bubble-table rebuild.  A
+// pass after initialisation labels only the cells of the bubbles that phase C
+// marked (a merge or split may involve them); the other bubbles keep their
+// slots and table rows.  Slots are recycled through a stack per domain.
+struct CclArgs {
+    int* lab;                    // union-find parent per cell (global index), -1 outside the pass
+    int* aux;                    // new slot of each root cell
+    unsigned long long* hkeys;   // (new slot << 32 | old slot) overlap keys, ~0 empty
+    long long* hvals;            // overlap volumes V_{c,b}, fixed point
+    long long hcap;              // power of two
+    int* hused;                  // hash positions taken in this pass (emptied again at install)
+    int* nhused;
+    long long* nvfx;             // new table rows (slot-indexed, reset when a slot is handed out)
+    long long* nvxfx;
+    long long* nvsfx;
+    long long* nncells;
+    int* nconstp;
+    int* croot;                  // root cell (global index) of each new slot
+    long long* vtot;             // per old slot: total volume over all new components
+    int* minc;                   // per old slot: lowest root among its components
+    int* nused;                  // per domain: slots handed out so far (high-water mark)
+    int* nfree;                  // per domain: slots on its free stack
+    int* freelist;               // slot-indexed: domain d's stack at [slot_off, slot_off + cap)
+    int* aff;                    // per slot: 1 while its bubble takes part in the pass, 2 when
+                                 // handed out again in it, 0 otherwise
+    int* afflist;                // slots marked 1 this step
+    int* naff;
+    int* plist;                  // cells taking part in the pass
+    int* np;
+    int* newslots;               // slots handed out in the pass
+    int* nnew;
+    const int* slot_dom;         // slot -> domain
+    long long* runs;             // labelling passes run after initialisation
+    long long* vsfx;             // bubble tables written by the install phase
+    int* constp;
+    int initial;                 // 1: first labelling after initialisation (every bubble, V* = V)
+    int max_iter;                // cap on union / find loops
+};
+
+// A merge or split may involve bubble b (slot) of domain d: b takes part in
+// this step's labelling pass, which runs for the domain.
+__device__ inline void mark_affected(const StepArgs& A, const CclArgs& K, int d, int b) {
+    if (b >= 0 && atomicExch(&K.aff[b], 1) == 0) K.afflist[atomicAdd(K.naff, 1)] = b;
+    atomicExch(&A.trig[1 + d], 1);
+    atomicExch(A.trig, 1);
+}
+
 // Phase C, over the marked list and the new-from-liquid list: excess mass of
 // converted cells (filled: m - rho, emptied: m) split equally among the
 // neighbours that are interface after conversion, else pooled; merge / split
 // triggers.  Taking the filled cells away one at a time in index order, each
 // removal must pass the local test with the lower-index filled cells already
 // gone and the higher-index ones still present, or the labelling runs.
-__device__ inline void convert_c_phase(const StepArgs& A) {
+__device__ inline void convert_c_phase(const StepArgs& A, const CclArgs& K) {
     const int nm = *A.mcount, nl = *A.lcount;
     const int total = nm + nl;
     const int step = *A.stepno;
@@ -1531,10 +1723,7 @@ __device__ inline void convert_c_phase(const StepArgs& A) {
                             if (ntz == GAS || ntz == IFC || later_filled)
                                 fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
                         }
-                if (!removal_is_local(fgm)) {
-                    atomicExch(&A.trig[1 + d], 1);
-                    atomicExch(A.trig, 1);
-                }
+                if (!removal_is_local(fgm)) mark_affected(A, K, d, A.id[g]);   // its bubble may split
             }
             A.cstep[g] = step;
             A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
@@ -1553,15 +1742,14 @@ __device__ inline void convert_c_phase(const StepArgs& A) {
             iz[a] = A.id[z];
         }
         bool merge = false;
-#pragma unroll
         for (int a = 1; a < 19; ++a) {
             const uint8_t ntz = new_type(ctype(fl[a]), mz[a]);
-            merge |= (ntz == GAS || ntz == IFC) && iz[a] != b;
+            if ((ntz == GAS || ntz == IFC) && iz[a] != b) {
+                merge = true;
+                mark_affected(A, K, d, iz[a]);   // every bubble the new cell touches
+            }
         }
-        if (merge) {
-            atomicExch(&A.trig[1 + d], 1);
-            atomicExch(A.trig, 1);
-        }
+        if (merge) mark_affected(A, K, d, b);
     }
 }
 
@@ -1664,7 +1852,7 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
         warp_add(A.vfx, dv != 0 ? key : -1, dv);
         warp_add(A.ncells, ckey, dc);
         warp_add(A.icnt, keep ? d : -1, 1);
-        list_append(A.ilist_next, A.icount_next, keep, (int)g);
+        if (!A.order) list_append(A.ilist_next, A.icount_next, keep, (int)g);
     }
     if (blockIdx.x == 0) {
         // reservoir drain of every domain whose seed cell is still gas or
@@ -1683,30 +1871,6 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
     }
 }
 
-// Scratch of the connected-component labelling and bubble-table rebuild.
-struct CclArgs {
-    int* lab;                    // union-find parent per cell (global index), -1 background
-    int* aux;                    // new slot of each root cell
-    unsigned long long* hkeys;   // (new slot << 32 | old slot) overlap keys, ~0 empty
-    long long* hvals;            // overlap volumes V_{c,b}, fixed point
-    long long hcap;              // power of two
-    long long* nvfx;             // new table (slot-indexed)
-    long long* nvxfx;
-    long long* nvsfx;
-    long long* nncells;
-    int* nconstp;
-    int* croot;                  // root cell (global index) of each new slot
-    long long* vtot;             // per old slot: total volume over all new components
-    int* minc;                   // per old slot: lowest root among its components
-    int* nslot;                  // per domain: slots in use
-    const int* slot_dom;         // slot -> domain
-    long long nslots_total;
-    long long* runs;             // labelling passes run after initialisation
-    long long* vsfx;             // bubble tables written by the install phase
-    int* constp;
-    int initial;                 // 1: first labelling after initialisation (V* = V)
-    int max_iter;                // cap on union / find loops
-};
 
 
 // --------------------------------------------- connected-component labelling
@@ -1722,7 +1886,10 @@ struct CclArgs {
 __device__ inline bool is_fg(uint8_t f) { return ctype(f) == GAS || ctype(f) == IFC; }
 
 // Root of a; halves the path on the way (each cell is pointed at its
-// grandparent, still one of its ancestors, so the trees keep their roots).
+// grandparent).  Only the hook phase uses it: there a cell's parent changes
+// only from itself (a root) to a smaller root, so every ancestor a thread has
+// read stays an ancestor and a halving store, however late, keeps the cell in
+// its tree.
 __device__ inline int find_root(int* L, int a, int cap, bool& ok) {
     for (int it = 0; it < cap; ++it) {
         const int p = L[a];
@@ -1735,8 +1902,23 @@ __device__ inline int find_root(int* L, int a, int cap, bool& ok) {
     return a;
 }
 
-// Lock-free union: always hook the larger root under the smaller one, so the
-// final root of every component is its minimum cell index.
+// Root of a without writing (parents have smaller indices, so the walk ends).
+// The compress phase uses this one: a halving store there could land after
+// the cell's own thread has stored the root, and leave an inner node behind.
+__device__ inline int find_root_ro(const int* L, int a, int cap, bool& ok) {
+    for (int it = 0; it < cap; ++it) {
+        const int p = L[a];
+        if (p == a) return a;
+        a = p;
+    }
+    ok = false;
+    return a;
+}
+
+// Lock-free union: hook the larger root under the smaller one by a
+// compare-and-swap that succeeds only while it is still a root (a non-root's
+// parent is never rewritten), so the final root of every component is its
+// minimum cell index.
 __device__ inline bool unite(int* L, int a, int b, int cap) {
     bool ok = true;
     for (int it = 0; it < cap && ok; ++it) {
@@ -1745,17 +1927,10 @@ __device__ inline bool unite(int* L, int a, int b, int cap) {
         if (!ok) return false;
         if (a == b) return true;
         if (a < b) { const int tt = a; a = b; b = tt; }
-        const int old = atomicMin(&L[a], b);
-        if (old == a) return true;
-        a = old;
+        if (atomicCAS(&L[a], a, b) == a) return true;
+        // a was hooked by another thread meanwhile: find both roots again
     }
     return false;
-}
-
-// Domain taking part in this labelling pass (every domain after
-// initialisation, else the domains whose step set the trigger).
-__device__ inline bool ccl_active(const StepArgs& A, const CclArgs& K, int d) {
-    return K.initial || A.trig[1 + d] != 0;
 }
 
 // First tile and tile count of domain d (read field by field).
@@ -1765,75 +1940,97 @@ __device__ inline long long dom_tile0(const StepArgs& A, int d) {
 __device__ inline long long dom_ntiles(const StepArgs& A, int d) {
     return ((long long)(A.ndom == 1 ? A.d0.n : A.doms[d].n) + FSL_BLOCK - 1) / FSL_BLOCK;
 }
-// The tiles of the domains taking part in a pass: after initialisation every
-// tile in order; otherwise the tiles of each triggered domain, spread over the
-// whole grid one domain after the other (on a typical step of a large batch a
-// few domains trigger, and the others are not visited at all).
-#define FSL_TILE_LOOP(A, K, tile)                                                                            \
-    for (int dd_ = 0, nd_ = (K).initial ? 1 : (A).ndom; dd_ < nd_; ++dd_)                                   \
-        if ((K).initial || (A).trig[1 + dd_] != 0)                                                           \
-            for (long long tile = ((K).initial ? 0 : dom_tile0(A, dd_)) + blockIdx.x,                        \
-                           tend_ = (K).initial ? (A).stride / FSL_BLOCK : dom_tile0(A, dd_) + dom_ntiles(A, dd_); \
-                 tile < tend_; tile += gridDim.x)
 
+// Grid-stride loop over a device-counted list: every lane of a warp runs the
+// same iterations (i >= n on the lanes past the end), so warp collectives may
+// be used in the body.
+#define FSL_LIST_LOOP(i, n)                                                                                  \
+    for (long long base_ = (long long)blockIdx.x * blockDim.x, i = base_ + threadIdx.x; base_ < (n);      \
+         base_ += (long long)gridDim.x * blockDim.x, i = base_ + threadIdx.x)
+
+// Phase 1: the cells taking part (every gas / interface cell in the initial
+// pass; afterwards those of the marked bubbles, found by a scan of the
+// triggered domains' tiles, one cell per thread of a 256-thread block) start
+// as their own roots and are listed; marked slots go onto their domain's free
+// stack.  A marked bubble's cells touch no gas or interface cell outside the
+// pass: two bubbles become adjacent only through a new interface cell from
+// liquid, and phase C marks every bubble around such a cell.
 __device__ inline void ccl_init_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, K, t) {
-        const long long g = t * FSL_BLOCK + threadIdx.x;
-        if (ccl_active(A, K, block_dom(A, g))) K.lab[g] = is_fg(A.flag[g]) ? (int)g : -1;
+    for (int dd = 0, nd = K.initial ? 1 : A.ndom; dd < nd; ++dd) {
+        if (!K.initial && A.trig[1 + dd] == 0) continue;
+        const long long t0 = K.initial ? 0 : dom_tile0(A, dd);
+        const long long t1 = K.initial ? A.stride / FSL_BLOCK : t0 + dom_ntiles(A, dd);
+        for (long long tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
+            const long long g = tile * FSL_BLOCK + threadIdx.x;
+            bool part = is_fg(A.flag[g]);
+            if (part && !K.initial) {
+                const int b = A.id[g];
+                part = b >= 0 && K.aff[b] == 1;
+            }
+            K.lab[g] = part ? (int)g : -1;
+            list_append(K.plist, K.np, part, (int)g);
+        }
     }
-    const long long nth = (long long)gridDim.x * blockDim.x;
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (long long h = i0; h < K.hcap; h += nth) {
-        K.hkeys[h] = ~0ull;
-        K.hvals[h] = 0;
+    if (K.initial) return;
+    const int na = *K.naff;
+    FSL_LIST_LOOP(i, na) {
+        if (i >= na) continue;
+        const int b = K.afflist[i];
+        const Dom& D = get_dom(A, K.slot_dom[b]);
+        K.freelist[D.slot_off + atomicAdd(&K.nfree[K.slot_dom[b]], 1)] = b;
+        K.vtot[b] = 0;
+        K.minc[b] = INT_MAX;
     }
-    for (long long sl = i0; sl < K.nslots_total; sl += nth) {
-        K.nvfx[sl] = 0; K.nvxfx[sl] = 0; K.nvsfx[sl] = 0; K.nncells[sl] = 0; K.nconstp[sl] = 0;
-        K.croot[sl] = -1;
-        K.vtot[sl] = 0;
-        K.minc[sl] = INT_MAX;
-    }
-    for (long long dd = i0; dd < A.ndom; dd += nth)
-        if (ccl_active(A, K, (int)dd)) K.nslot[dd] = 0;
 }
 
+// Phase 2: unions over the 18-neighbourhood (the nine directions 1, 3, ...,
+// 17 cover each neighbour pair once).
 __device__ inline void ccl_hook_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, K, t) {
-        const long long g = t * FSL_BLOCK + threadIdx.x;
-        const int d = block_dom(A, g);
-        if (!ccl_active(A, K, d) || !is_fg(A.flag[g])) continue;
-        const Dom& D = get_dom(A, d);
+    const int np = *K.np;
+    FSL_LIST_LOOP(i, np) {
+        if (i >= np) continue;
+        const long long g = K.plist[i];
+        const Dom& D = get_dom(A, block_dom(A, g));
         const Cell c = make_cell(D, g);
-        // the nine directions 1, 3, ..., 17 cover each neighbour pair once
         for (int a = 1; a < 19; a += 2) {
-            const long long h = c.at(cx(a), cy(a), cz(a));
-            if (is_fg(A.flag[h])) {
-                if (!unite(K.lab, (int)g, (int)h, K.max_iter)) {
-                    set_status(A.status, ST_CCL);
-                    break;
-                }
+            const long long h = c.at(rcx(a), rcy(a), rcz(a));
+            if (K.lab[h] >= 0 && !unite(K.lab, (int)g, (int)h, K.max_iter)) {
+                set_status(A.status, ST_CCL);
+                break;
             }
         }
     }
 }
 
-// Compress every cell onto its root; roots take a new bubble-table slot.
+// Phase 3: every cell onto its root; each root takes a slot (from its
+// domain's free stack, else a fresh one) and resets that slot's new row.
 __device__ inline void ccl_compress_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, K, t) {
-        const long long g = t * FSL_BLOCK + threadIdx.x;
-        const int d = block_dom(A, g);
-        if (!ccl_active(A, K, d) || !is_fg(A.flag[g])) continue;
+    const int np = *K.np;
+    FSL_LIST_LOOP(i, np) {
+        if (i >= np) continue;
+        const long long g = K.plist[i];
         bool ok = true;
-        const int r = find_root(K.lab, (int)g, K.max_iter, ok);
+        const int r = find_root_ro(K.lab, (int)g, K.max_iter, ok);
         if (!ok) { set_status(A.status, ST_CCL); continue; }
         K.lab[g] = r;
-        if (r == (int)g) {
-            const Dom& D = get_dom(A, d);
-            const int k = atomicAdd(&K.nslot[d], 1);
-            if (k >= D.slot_cap) { set_status(A.status, ST_TABLE_FULL); K.aux[g] = -1; continue; }
-            K.aux[g] = D.slot_off + k;
-            K.croot[D.slot_off + k] = r;
+        if (r != (int)g) continue;
+        const int d = block_dom(A, g);
+        const Dom& D = get_dom(A, d);
+        int sl = -1;
+        const int k = K.initial ? -1 : atomicSub(&K.nfree[d], 1) - 1;
+        if (k >= 0) {
+            sl = K.freelist[D.slot_off + k];
+        } else {
+            const int j = atomicAdd(&K.nused[d], 1);
+            if (j < D.slot_cap) sl = D.slot_off + j;
+            else set_status(A.status, ST_TABLE_FULL);
         }
+        K.aux[g] = sl;
+        if (sl < 0) continue;
+        K.aff[sl] = 2;
+        K.croot[sl] = r;
+        K.nvfx[sl] = 0; K.nvxfx[sl] = 0; K.nvsfx[sl] = 0; K.nncells[sl] = 0; K.nconstp[sl] = 0;
+        K.newslots[atomicAdd(K.nnew, 1)] = sl;
     }
 }
 
@@ -1843,6 +2040,7 @@ __device__ inline void hash_add(const CclArgs& K, unsigned long long key, long l
     for (long long probe = 0; probe < K.hcap; ++probe) {
         const unsigned long long prev = atomicCAS(&K.hkeys[pos], ~0ull, key);
         if (prev == ~0ull || prev == key) {
+            if (prev == ~0ull) K.hused[atomicAdd(K.nhused, 1)] = (int)pos;
             atomicAdd((unsigned long long*)&K.hvals[pos], (unsigned long long)v);
             return;
         }
@@ -1851,22 +2049,22 @@ __device__ inline void hash_add(const CclArgs& K, unsigned long long key, long l
     set_status(status, ST_TABLE_FULL);
 }
 
-// New volumes and cell counts per component, overlap volumes V_{c,b} of new
-// component c with old bubble b, new ids.
+// Phase 4: new volumes and cell counts per component, overlap volumes V_{c,b}
+// of new component c with old bubble b, new slots into the id field.
 __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
-    FSL_TILE_LOOP(A, K, t) {
-        const long long g = t * FSL_BLOCK + threadIdx.x;
-        const int d = block_dom(A, g);
-        if (!ccl_active(A, K, d)) continue;   // whole block: one domain
-        const uint8_t ty = ctype(A.flag[g]);
+    const int np = *K.np;
+    FSL_LIST_LOOP(i, np) {
+        const bool valid = i < np;
+        const long long g = valid ? K.plist[i] : 0;
         int c = -1;
         long long term = 0;
-        if (ty == GAS || ty == IFC) {
+        if (valid) {
             // the slot of the cell's root; -1 when a find gave up at its
             // iteration cap (the pass has then latched ST_CCL and r may be an
             // inner node whose aux entry was never written)
             const int r = K.lab[g];
             c = (r >= 0 && K.lab[r] == r) ? K.aux[r] : -1;
+            const uint8_t ty = ctype(A.flag[g]);
             term = A.phif ? volume_term_f(ty, A.phif[g]) : volume_term(ty, A.phi[g]);
         }
         warp_add(K.nvfx, c, term);
@@ -1878,7 +2076,7 @@ __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
             hash_add(K, key, term, A.status);
             atomicAdd((unsigned long long*)&K.vtot[b], (unsigned long long)term);
             atomicMin(&K.minc[b], K.lab[g]);
-            const Dom& D = get_dom(A, d);
+            const Dom& D = get_dom(A, block_dom(A, g));
             if (D.seed >= 0 && g - D.off == D.seed) {
                 const long long x = A.vxfx[b];
                 hash_add(K, key, x, A.status);
@@ -1890,14 +2088,15 @@ __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
     }
 }
 
-// V*_c = sum over b of V*_b V_{c,b} / V_b, V*_b copied when c holds all of b
-// (Secs. 2.3.1, 2.3.2); a component touching a constant-pressure bubble
-// stays constant-pressure.
+// Phase 5: V*_c = sum over b of V*_b V_{c,b} / V_b, V*_b copied when c holds
+// all of b (Secs. 2.3.1, 2.3.2); a component touching a constant-pressure
+// bubble stays constant-pressure.
 __device__ inline void ccl_table_phase(const StepArgs& A, const CclArgs& K) {
-    const long long nth = (long long)gridDim.x * blockDim.x;
-    for (long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x; h < K.hcap; h += nth) {
+    const int nh = *K.nhused;
+    FSL_LIST_LOOP(i, nh) {
+        if (i >= nh) continue;
+        const long long h = K.hused[i];
         const unsigned long long key = K.hkeys[h];
-        if (key == ~0ull) continue;
         const int c = (int)(key >> 32);
         const int b = (int)(key & 0xffffffffu);
         const long long vcb = K.hvals[h];
@@ -1915,24 +2114,41 @@ __device__ inline void ccl_table_phase(const StepArgs& A, const CclArgs& K) {
     }
 }
 
+// Phase 6: the new rows replace the old; slots of marked bubbles that were
+// not handed out again are emptied (they stay on the free stack); the hash
+// positions taken are emptied; the marks are cleared.
 __device__ inline void ccl_install_phase(const StepArgs& A, const CclArgs& K) {
     if (!K.initial && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)K.runs, 1ull);
-    const long long nth = (long long)gridDim.x * blockDim.x;
-    for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < K.nslots_total; sl += nth) {
-        const int d = K.slot_dom[sl];
-        if (!ccl_active(A, K, d)) continue;   // untouched domains keep their table
-        const Dom& D = get_dom(A, d);
-        const int k = (int)(sl - D.slot_off);
-        if (k < K.nslot[d]) {
-            A.vfx[sl] = K.nvfx[sl];
-            A.vxfx[sl] = K.nvxfx[sl];
-            K.vsfx[sl] = K.initial ? K.nvfx[sl] + K.nvxfx[sl] : K.nvsfx[sl];
-            A.ncells[sl] = K.nncells[sl];
-            K.constp[sl] = K.nconstp[sl];
-        } else {
-            A.vfx[sl] = 0; A.vxfx[sl] = 0; K.vsfx[sl] = 0; A.ncells[sl] = 0; K.constp[sl] = 0;
+    const int nn = *K.nnew;
+    FSL_LIST_LOOP(i, nn) {
+        if (i >= nn) continue;
+        const int sl = K.newslots[i];
+        A.vfx[sl] = K.nvfx[sl];
+        A.vxfx[sl] = K.nvxfx[sl];
+        K.vsfx[sl] = K.initial ? K.nvfx[sl] + K.nvxfx[sl] : K.nvsfx[sl];
+        A.ncells[sl] = K.nncells[sl];
+        K.constp[sl] = K.nconstp[sl];
+        K.aff[sl] = 0;
+    }
+    if (K.initial) return;
+    const int na = *K.naff;
+    FSL_LIST_LOOP(i, na) {
+        if (i >= na) continue;
+        const int b = K.afflist[i];
+        if (K.aff[b] == 1) {   // not handed out again (a reused slot reads 2, or 0 once rewritten)
+            A.vfx[b] = 0; A.vxfx[b] = 0; K.vsfx[b] = 0; A.ncells[b] = 0; K.constp[b] = 0;
+            K.aff[b] = 0;
         }
     }
+    const int nh = *K.nhused;
+    FSL_LIST_LOOP(i, nh) {
+        if (i >= nh) continue;
+        K.hkeys[K.hused[i]] = ~0ull;
+        K.hvals[K.hused[i]] = 0;
+    }
+    for (long long dd = (long long)blockIdx.x * blockDim.x + threadIdx.x; dd < A.ndom;
+         dd += (long long)gridDim.x * blockDim.x)
+        if (K.nfree[dd] < 0) K.nfree[dd] = 0;
 }
 
 // Barrier over all blocks of a cooperative launch (all of them resident).  The
@@ -1980,14 +2196,24 @@ __global__ void __launch_bounds__(FSL_CONV_THREADS, 3) k_convert(StepArgs A, Ccl
     pdl_wait();   // the stream-collide kernel has finished and its writes are visible
     if (blockIdx.x == 0) {
         for (int d = threadIdx.x; d < A.ndom; d += blockDim.x) A.icnt[d] = 0;
-        if (threadIdx.x == 0) *A.icount_next = 0;
+        if (threadIdx.x == 0) {
+            *A.icount_next = 0;
+            // list counters of this step's labelling (used after phase C at the earliest)
+            *K.naff = 0; *K.np = 0; *K.nnew = 0; *K.nhused = 0;
+        }
     }
     convert_ab_phase<T>(A);
     if (!grid_barrier(A)) return;
-    convert_c_phase(A);
+    convert_c_phase(A, K);
     if (!grid_barrier(A)) return;
     const bool relabel = *(volatile int*)A.trig != 0;   // final after phase C
     convert_d_phase(A);
+    if (A.order) {
+        if (!grid_barrier(A)) return;
+        order_count_phase(A);
+        if (!grid_barrier(A)) return;
+        order_write_phase(A);
+    }
     if (!relabel) return;
     if (!grid_barrier(A)) return;
     ccl_init_phase(A, K);
@@ -2071,32 +2297,92 @@ __global__ void k_export_pdf(const T* f, long long S, long long off, int n, doub
     }
 }
 
+// Liquid mass of one domain, deterministically: per block the sum, in a fixed
+// tree order, of rho (sum of the stored PDFs, Eq. 4) over liquid cells and of m
+// over interface cells; the host adds the block sums in block order.
+template <typename T>
+__global__ void __launch_bounds__(FSL_BLOCK) k_mass_partials(const T* f, const uint8_t* flag, const double* m,
+                                                             long long S, long long off, int n, double* part) {
+    const long long l = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;
+    double v = 0.0;
+    if (l < n) {
+        const long long g = off + l;
+        const uint8_t t = ctype(flag[g]);
+        if (t == LIQ) {
+            double r = (double)Form<T>::ld(f + g, 0);
+            for (int a = 1; a < 19; ++a) r += (double)Form<T>::ld(f + (long long)a * S + g, a);
+            v = r;
+        } else if (t == IFC) {
+            v = m[g];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __shared__ double ws[FSL_BLOCK / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < FSL_BLOCK / 32; ++w) t += ws[w];
+        part[blockIdx.x] = t;
+    }
+}
+
 // Launch helpers instantiated once per storage form.
-template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, cudaStream_t s,
-                                         cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,
-                                         cudaEvent_t ei);
+template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, int form, int pgrid,
+                                         cudaStream_t s, cudaEvent_t el, cudaEvent_t ei);
+template <typename T> int stream_blocks_per_sm(int form, bool one);
 template <typename T> cudaError_t launch_convert(const StepArgs& A, const CclArgs& K, int nblocks, cudaStream_t s);
 template <typename T> int convert_blocks_per_sm();
 template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
                                              const double* rho, const double* u, cudaStream_t s);
 template <typename T> void launch_export_pdf(const void* f, long long S, long long off, int n, double* pdf,
                                              double* rho, double* u, cudaStream_t s);
+template <typename T> void launch_mass_partials(const void* f, const uint8_t* flag, const double* m, long long S,
+                                                long long off, int n, double* part, cudaStream_t s);
 
 #define FSL_INSTANTIATE_FORM(T)                                                                              \
-    template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, cudaStream_t s,               \
-                                      cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, cudaEvent_t el,   \
-                                      cudaEvent_t ei) {                                                      \
-        /* one kernel: interface blocks first, then the liquid blocks; el / ei */                           \
-        /* (optional) both mark its end */                                                                   \
-        (void)s2; (void)fork; (void)join;                                                                    \
-        const int nif = FSL_IF_GRID * ifb / 2;                                                               \
-        const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                         \
-        if (A.ndom == 1)                                                                                     \
-            k_stream<T, true><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                          \
-        else                                                                                                 \
-            k_stream<T, false><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                         \
+    template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, int form, int pgrid,          \
+                                      cudaStream_t s, cudaEvent_t el, cudaEvent_t ei) {                      \
+        /* split form: interface blocks first, then one block per liquid tile; */                          \
+        /* persistent forms: pgrid resident blocks; el / ei (optional) both */                              \
+        /* mark the kernel's end */                                                                          \
+        const unsigned pg = (unsigned)(pgrid > 0 ? pgrid : 1);                                               \
+        if (form == SC_SPLIT) {                                                                              \
+            const int nif = FSL_IF_GRID * ifb / 2;                                                           \
+            const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                     \
+            if (A.ndom == 1)                                                                                 \
+                k_stream<T, true><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                      \
+            else                                                                                             \
+                k_stream<T, false><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                     \
+        } else if (A.ndom == 1) {                                                                            \
+            if (form == SC_PERS1) k_stream_pers<T, true, 1><<<pg, FSL_BLOCK, 0, s>>>(A);                    \
+            else if (form == SC_PERS2) k_stream_pers<T, true, 2><<<pg, FSL_BLOCK, 0, s>>>(A);               \
+            else k_stream_pers<T, true, 4><<<pg, FSL_BLOCK, 0, s>>>(A);                                      \
+        } else {                                                                                             \
+            if (form == SC_PERS1) k_stream_pers<T, false, 1><<<pg, FSL_BLOCK, 0, s>>>(A);                   \
+            else if (form == SC_PERS2) k_stream_pers<T, false, 2><<<pg, FSL_BLOCK, 0, s>>>(A);              \
+            else k_stream_pers<T, false, 4><<<pg, FSL_BLOCK, 0, s>>>(A);                                     \
+        }                                                                                                    \
         if (ei) cudaEventRecord(ei, s);                                                                      \
         if (el) cudaEventRecord(el, s);                                                                      \
+    }                                                                                                        \
+    template <> int stream_blocks_per_sm<T>(int form, bool one) {                                            \
+        int nb = 0;                                                                                          \
+        if (form == SC_SPLIT) nb = 1;                                                                        \
+        else if (one && form == SC_PERS1)                                                                    \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, true, 1>, FSL_BLOCK, 0);     \
+        else if (one && form == SC_PERS2)                                                                    \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, true, 2>, FSL_BLOCK, 0);     \
+        else if (one)                                                                                        \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, true, 4>, FSL_BLOCK, 0);     \
+        else if (form == SC_PERS1)                                                                           \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, false, 1>, FSL_BLOCK, 0);    \
+        else if (form == SC_PERS2)                                                                           \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, false, 2>, FSL_BLOCK, 0);    \
+        else                                                                                                 \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, false, 4>, FSL_BLOCK, 0);    \
+        return nb;                                                                                           \
     }                                                                                                        \
     template <> cudaError_t launch_convert<T>(const StepArgs& A, const CclArgs& K, int nb, cudaStream_t s) {\
         cudaLaunchConfig_t cfg = {};                                                                         \
@@ -2122,6 +2408,12 @@ template <typename T> void launch_export_pdf(const void* f, long long S, long lo
                                           cudaStream_t s) {                                                  \
         k_init_state<T><<<(unsigned)((n + FSL_BLOCK - 1) / FSL_BLOCK), FSL_BLOCK, 0, s>>>(A, d, fl, fill,   \
                                                                                           rho, u);           \
+    }                                                                                                        \
+    template <> void launch_mass_partials<T>(const void* f, const uint8_t* flag, const double* m,            \
+                                             long long S, long long off, int n, double* part,               \
+                                             cudaStream_t s) {                                              \
+        k_mass_partials<T><<<(unsigned)((n + FSL_BLOCK - 1) / FSL_BLOCK), FSL_BLOCK, 0, s>>>(                 \
+            (const T*)f, flag, m, S, off, n, part);                                                          \
     }                                                                                                        \
     template <> void launch_export_pdf<T>(const void* f, long long S, long long off, int n, double* pdf,     \
                                           double* rho, double* u, cudaStream_t s) {                          \

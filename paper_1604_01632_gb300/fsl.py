@@ -29,7 +29,9 @@ FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.flo
 EXPORTS = ["fsl_create", "fsl_init_geometry", "fsl_set_bubble_source", "fsl_step", "fsl_sync", "fsl_bubbles",
            "fsl_fields", "fsl_destroy", "fsl_last_error", "fsl_kernel_launches", "fsl_set_timing",
            "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs",
-           "fsl_label_bubbles_static", "fsl_phase_ms", "fsl_set_limits"]
+           "fsl_label_bubbles_static", "fsl_phase_ms", "fsl_set_limits",
+           "fsl_total_mass", "fsl_set_stream_form", "fsl_stream_form",
+           "fsl_set_interface_order", "fsl_interface_order", "fsl_tuning", "fsl_forget_tuning"]
 
 
 class FslError(RuntimeError):
@@ -98,6 +100,20 @@ def load_library():
     L.fsl_phase_ms.argtypes = [vp, vp]
     L.fsl_set_graphs.restype = i32
     L.fsl_set_graphs.argtypes = [vp, i32]
+    L.fsl_tuning.restype = i32
+    L.fsl_tuning.argtypes = [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.fsl_forget_tuning.restype = i32
+    L.fsl_forget_tuning.argtypes = []
+    L.fsl_set_interface_order.restype = i32
+    L.fsl_set_interface_order.argtypes = [vp, i32]
+    L.fsl_interface_order.restype = i32
+    L.fsl_interface_order.argtypes = [vp]
+    L.fsl_set_stream_form.restype = i32
+    L.fsl_set_stream_form.argtypes = [vp, i32]
+    L.fsl_stream_form.restype = i32
+    L.fsl_stream_form.argtypes = [vp]
+    L.fsl_total_mass.restype = i32
+    L.fsl_total_mass.argtypes = [vp, i32, ctypes.POINTER(dbl)]
     L.fsl_set_limits.restype = i32
     L.fsl_set_limits.argtypes = [vp, i64, i64, i32]
     L.fsl_labelling_runs.restype = i64
@@ -294,6 +310,12 @@ class Simulation:
         self._check(self.L.fsl_cell_counts(self._h, d, c))
         return np.array(list(c), dtype=np.int64)
 
+    def total_mass(self, d: int = 0) -> float:
+        """Liquid mass of domain d: rho over liquid cells + m over interface cells + pool."""
+        v = ctypes.c_double(0.0)
+        self._check(self.L.fsl_total_mass(self._h, d, ctypes.byref(v)))
+        return float(v.value)
+
     @property
     def launches(self) -> int:
         return int(self.L.fsl_kernel_launches(self._h))
@@ -309,6 +331,33 @@ class Simulation:
         """Failure-path limits for tests (0 = default): labelling iteration cap,
         barrier polls, and a barrier that waits for a block that does not exist."""
         self._check(self.L.fsl_set_limits(self._h, int(ccl_max_iter), int(barrier_polls), 1 if barrier_absent else 0))
+
+    def set_stream_form(self, form: int):
+        """Stream-collide kernel form: 0 split, 1/2/3 persistent with 1/2/4 tiles per liquid
+        item, -1 autotune again."""
+        self._check(self.L.fsl_set_stream_form(self._h, int(form)))
+
+    def tuning(self) -> dict:
+        """Autotuner record: per-form stream-collide ms, chosen form, source."""
+        ms = (ctypes.c_double * 4)()
+        form, src = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self.L.fsl_tuning(self._h, ms, ctypes.byref(form), ctypes.byref(src)))
+        names = ("split", "persistent_1tile", "persistent_2tiles", "persistent_4tiles")
+        return {"ms_per_form": dict(zip(names, [round(v, 5) for v in ms])),
+                "form": int(form.value), "form_name": names[form.value] if form.value >= 0 else None,
+                "source": ("none", "measured", "cache", "caller")[src.value]}
+
+    def set_interface_order(self, mode: int):
+        """Interface list order: 1 rebuilt in cell order each step, 0 appended, -1 by lattice size."""
+        self._check(self.L.fsl_set_interface_order(self._h, int(mode)))
+
+    @property
+    def interface_order(self) -> int:
+        return int(self.L.fsl_interface_order(self._h))
+
+    @property
+    def stream_form(self) -> int:
+        return int(self.L.fsl_stream_form(self._h))
 
     def set_graphs(self, on: bool):
         self._check(self.L.fsl_set_graphs(self._h, 1 if on else 0))

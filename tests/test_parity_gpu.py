@@ -296,3 +296,79 @@ def test_accuracy_report_reduced_forms(fsl, oracle_mod):
         assert rep["bubble_volume_rel_max"] < 2e-2
         assert abs(rep["mass_drift_vs_oracle"]) < 1e-2
         sim.close()
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-13), ("fp32", 1e-5), ("f16s", 1e-5)])
+def test_total_mass_against_oracle(fsl, oracle_mod, precision, rtol):
+    """fsl_total_mass (rho over liquid cells + m over interface cells + pool,
+    summed on the device in a fixed order) against the oracle's liquid mass on
+    moving bubbles with conversions, after 0 and 40 steps; the FP64 path
+    differs only by summation order, the FP32-collide forms by their rounding.
+    Summed twice, the value is the same bit for bit."""
+    sc = S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=1)
+    sim, o = _pair(fsl, oracle_mod, sc, precision)
+    for k in (0, 40):
+        if k:
+            sim.step(k)
+            o.step(k)
+        got, want = sim.total_mass(), o.total_mass()
+        assert got == sim.total_mass()
+        assert abs(got / want - 1.0) < rtol, (k, got, want)
+    sim.close()
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+def test_persistent_stream_forms_bitexact(fsl, oracle_mod, form):
+    """The persistent stream-collide forms (1, 2 or 4 tiles per liquid item,
+    interface chunks interleaved) give the oracle's state bit for bit: a batch
+    of moving-bubble domains with conversions, merges and splits, and a single
+    domain with a moving lid and gravity."""
+    scs = [S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=s)
+           for s in (0, 1)]
+    scs.append(S.static_bubble(n=16, radius=4.0))
+    sim = fsl.Simulation.from_scenarios(scs, precision="fp64")
+    sim.set_stream_form(form)
+    assert sim.stream_form == form
+    oras = [oracle_mod.Oracle.from_scenario(s) for s in scs]
+    prev = 0
+    for k in (1, 5, 30):
+        sim.step(k - prev)
+        for o in oras:
+            o.step(k - prev)
+        prev = k
+        for d, o in enumerate(oras):
+            compare_exact(gpu_state(sim, d), oracle_state(o), what=f"form {form} domain {d} step {k}")
+    sim.close()
+    sc = S.foam(n=40, gas_fraction=0.3, seed=1, max_attempts=20000)
+    sim = fsl.Simulation.from_scenarios([sc], precision="fp64")
+    sim.set_stream_form(form)
+    o = oracle_mod.Oracle.from_scenario(sc)
+    for k in (1, 10):
+        sim.step(k if k == 1 else 9)
+        o.step(k if k == 1 else 9)
+        compare_exact(gpu_state(sim), oracle_state(o), what=f"form {form} foam step {k}")
+    sim.close()
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_cell_ordered_interface_list_bitexact(fsl, oracle_mod, form):
+    """The interface list rebuilt in cell order after every conversion (two
+    passes over the cell types inside the conversion kernel) changes only the
+    order of the work: the oracle's state bit for bit, split and persistent
+    stream-collide forms."""
+    scs = [S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=s)
+           for s in (2, 3)]
+    sim = fsl.Simulation.from_scenarios(scs, precision="fp64")
+    sim.set_interface_order(1)
+    sim.set_stream_form(form)
+    assert sim.interface_order == 1
+    oras = [oracle_mod.Oracle.from_scenario(s) for s in scs]
+    prev = 0
+    for k in (1, 4, 25):
+        sim.step(k - prev)
+        for o in oras:
+            o.step(k - prev)
+        prev = k
+        for d, o in enumerate(oras):
+            compare_exact(gpu_state(sim, d), oracle_state(o), what=f"ordered list form {form} domain {d} step {k}")
+    sim.close()

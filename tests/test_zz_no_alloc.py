@@ -46,9 +46,12 @@ def test_static_labels_match_library_ids_twice(env):
 
 
 def test_static_labels_reject_oversized_lattice(env):
+    """A lattice above the fixed scratch (2^21 cells) is refused by the library
+    itself, with buffers large enough to pass the binding's own checks."""
     torch, fsl = env
-    flags = torch.zeros(8, dtype=torch.uint8, device="cuda")
-    out = torch.zeros(8, dtype=torch.int64, device="cuda")
+    n = 256 * 128 * 65                                      # 2^21 + 2^15 cells
+    flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(n, dtype=torch.int64, device="cuda")
     with pytest.raises(fsl.FslError) as e:
-        fsl.label_bubbles_static(flags, 256, 128, 65, out)   # 2^21 + 2^15 cells
+        fsl.label_bubbles_static(flags, 256, 128, 65, out)
     assert e.value.status == -1
