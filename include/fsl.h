@@ -70,7 +70,13 @@ typedef struct {
     int32_t bubble_capacity;  /* bubble-table slots for this domain; 0 = default */
     int32_t lonely_rule;      /* 1: an interface cell with no gas neighbour fills, one with no liquid
                                  neighbour empties (it no longer separates liquid from gas) */
-    int32_t reserved;         /* set to 0 */
+    int32_t split_trigger;    /* when a bubble that loses a cell to the liquid is relabelled (a split
+                                 is possible only then, paper Sec. 2.3.2): 0 = the removed cell's gas
+                                 and interface neighbours are not connected inside its 3x3x3 cube
+                                 (exact: never misses a split); 1 = the paper's trigger, two
+                                 interface neighbours of its bubble with anti-parallel normals
+                                 (n_i . n_j < -1/2), which relabels less often and can miss a
+                                 split the local test would catch */
 } fsl_params;
 
 /* One bubble (paper Sec. 2.3): id = minimum linear index of its gas and
@@ -199,9 +205,10 @@ fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_p
 
 /* Form of the stream-collide kernel (the same results in every form; each
  * cell runs the same arithmetic).  By default (form -1) the library tunes it:
- * the first fsl_step calls of a handle run eight real steps that each time
- * one candidate form (every form twice, direct launches, the call waits for
- * each), then keep the fastest and record it in a process-wide cache keyed by
+ * the first fsl_step calls of a handle run real steps that each time one
+ * candidate form (every form twice, the slab form only with the interface
+ * list in cell order: eight or ten steps; direct launches, the call waits
+ * for each), then keep the fastest and record it in a process-wide cache keyed by
  * precision, one or many domains, SM count, lattice size (log2 of the padded
  * cells) and interface share (1/64 steps); a later handle of the same key
  * takes the cached form without tuning.  Forms:
@@ -209,14 +216,18 @@ fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_p
  *      (16 in FP64), the other blocks one liquid tile each;
  *   1, 2, 3  persistent: a resident grid walks one sequence of work items in
  *      which the interface chunks are spread evenly among liquid items of 1,
- *      2 or 4 tiles (a tile is 512 cells in the 16-bit forms, 256 otherwise).
+ *      2 or 4 tiles (a tile is 512 cells in the 16-bit forms, 256 otherwise);
+ *   4  slab: each block of a resident grid owns a contiguous range of tiles
+ *      and processes their liquid cells and the interface cells among them,
+ *      interleaved (only with the interface list in cell order, see
+ *      fsl_set_interface_order; FSL_ERR_ARG otherwise).
  * -1 restarts the tuning.  Waits for the handle's stream; the next fsl_step
  * rebuilds its graphs.  FSL_ERR_ARG for another value.  fsl_stream_form
  * returns the form in use (the one tried next while tuning). */
 fsl_status fsl_set_stream_form(fsl_domain* h, int32_t form);
 int32_t fsl_stream_form(const fsl_domain* h);
 
-/* Autotuner record of the handle: ms_per_form (array of 4, may be NULL) the
+/* Autotuner record of the handle: ms_per_form (array of 5, may be NULL) the
  * fastest stream-collide time measured per form (0 = not run); *form the
  * chosen form (-1 while tuning); *source 0 = not decided, 1 = measured on
  * this handle, 2 = from the process cache, 3 = set by the caller. */

@@ -26,8 +26,10 @@ namespace {
 const int kDefaultCapacityMin = 256;
 
 // Candidate sequence of the autotuner: every form twice, the faster of its two
-// timed steps counts.
-const int kTuneSeq[] = {SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4};
+// timed steps counts (the slab form only where the interface list is kept in
+// cell order; it is skipped otherwise).
+const int kTuneSeq[] = {SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB,
+                        SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB};
 const int kTuneSteps = (int)(sizeof(kTuneSeq) / sizeof(kTuneSeq[0]));
 
 // Process-wide cache of tuning decisions, keyed by the workload's shape:
@@ -61,13 +63,13 @@ struct fsl_domain {
     // CUDA events around its stream-collide kernel (direct launches)
     bool tuning = true;           // auto mode and not yet decided
     int tune_next = 0;            // index into the candidate sequence
-    double tune_ms[SC_FORMS] = {0, 0, 0, 0};   // best measured time per form (0: not run)
+    double tune_ms[SC_FORMS] = {0, 0, 0, 0, 0};   // best measured time per form (0: not run)
     int tune_source = 0;          // 0 none yet, 1 measured here, 2 taken from the process cache, 3 fixed by the caller
     cudaEvent_t tev[2] = {nullptr, nullptr};
     int order_mode = -1;          // interface list in cell order: 1 on, 0 off, -1 by lattice size
     long long l2bytes = 0;        // L2 cache of the device
     int* ocnt = nullptr;          // interface cells per conversion block (ordered rebuild)
-    int pgrid[SC_FORMS] = {0, 0, 0, 0};   // resident grid of each persistent form
+    int pgrid[SC_FORMS] = {0, 0, 0, 0, 0};   // resident grid of each persistent form
     int convblocks = 152;         // grid of the cooperative conversion kernel
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
@@ -511,7 +513,8 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     for (int d = 0; d < n_domains; ++d) {
         const fsl_params& p = params[d];
         long long n = (long long)p.nx * p.ny * p.nz;
-        if (p.nx <= 0 || p.ny <= 0 || p.nz <= 0 || n >= (1LL << 31) || !(p.tau > 0.5)) {
+        if (p.nx <= 0 || p.ny <= 0 || p.nz <= 0 || n >= (1LL << 31) || !(p.tau > 0.5) || p.split_trigger < 0 ||
+            p.split_trigger > 1) {
             delete h;
             return FSL_ERR_ARG;
         }
@@ -540,6 +543,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         div_magic(p.ny, D.mgy, D.shy);
         D.has_force = (p.gravity[0] != 0.0 || p.gravity[1] != 0.0 || p.gravity[2] != 0.0) ? 1 : 0;
         D.lonely_rule = p.lonely_rule;
+        D.split_trigger = p.split_trigger;
         h->hdoms.push_back(D);
         long long padded = (n + FSL_BLOCK - 1) / FSL_BLOCK * FSL_BLOCK;
         for (long long b = 0; b < padded / FSL_BLOCK; ++b) h->blk_dom.push_back(d);
@@ -815,6 +819,7 @@ fsl_status tune_step(fsl_domain* h) {
             return FSL_OK;   // no step taken: the caller runs it with the cached form
         }
     }
+    while (h->tune_next < kTuneSteps && kTuneSeq[h->tune_next] == SC_SLAB && !order_effective(h)) ++h->tune_next;
     const int f = kTuneSeq[h->tune_next];
     if (!h->tev[0]) {
         CK(h, cudaEventCreate(&h->tev[0]));
@@ -831,7 +836,9 @@ fsl_status tune_step(fsl_domain* h) {
     float ms = 0.f;
     CK(h, cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]));
     if (h->tune_ms[f] == 0.0 || ms < h->tune_ms[f]) h->tune_ms[f] = ms;
-    if (++h->tune_next == kTuneSteps) {
+    ++h->tune_next;
+    while (h->tune_next < kTuneSteps && kTuneSeq[h->tune_next] == SC_SLAB && !order_effective(h)) ++h->tune_next;
+    if (h->tune_next == kTuneSteps) {
         int best = SC_SPLIT;
         for (int g = 0; g < SC_FORMS; ++g)
             if (h->tune_ms[g] > 0.0 && h->tune_ms[g] < h->tune_ms[best]) best = g;
@@ -982,6 +989,8 @@ static void drop_graphs(fsl_domain* h) {
 
 fsl_status fsl_set_stream_form(fsl_domain* h, int32_t form) {
     if (!h || form < -1 || form >= SC_FORMS) return fail(h, FSL_ERR_ARG, "bad stream-collide form");
+    if (form == SC_SLAB && !order_effective(h))
+        return fail(h, FSL_ERR_ARG, "the slab form needs the interface list in cell order");
     CK(h, cudaStreamSynchronize(h->ls));
     if (form < 0) {
         // autotune again from the next step on (the process cache is consulted first)
@@ -1019,6 +1028,7 @@ fsl_status fsl_set_interface_order(fsl_domain* h, int32_t mode) {
     if (!h || mode < -1 || mode > 1) return fail(h, FSL_ERR_ARG, "bad interface-order mode");
     CK(h, cudaStreamSynchronize(h->ls));
     h->order_mode = mode;
+    if (h->form == SC_SLAB && !order_effective(h)) h->form = SC_SPLIT;   // the slab form needs the order
     drop_graphs(h);
     return FSL_OK;
 }

@@ -59,6 +59,7 @@ struct Dom {
     int shx, shy;               // (shift -1: the divisor is 1)
     int has_force;              // gravity is not zero
     int lonely_rule;            // interface cells without gas / liquid neighbours fill / empty
+    int split_trigger;          // 0: exact local test, 1: anti-parallel normals (the paper's)
     // the same parameters rounded to FP32 once on the host: the FP32-collide
     // kernels read these, so that no thread converts from FP64 (the FP64 pipe
     // is a small fraction of the FP32 rate on this GPU)
@@ -484,9 +485,10 @@ struct Collide2 {
     float2 ux, uy, uz, drho, rho, nusq15, hp, hm, Fx, Fy, Fz, uF;
 };
 
-// One TRT pair (a, a+1) of two cells; w = w_a, cp/cm the forcing prefactors.
-template <int a, bool FORCE>
-__device__ __forceinline__ void trt_pair2(const float2* d, float2* o, const Collide2& K, float omp, float omm,
+// One TRT pair (a, a+1) of two cells; w = w_a, cp/cm the forcing prefactors;
+// out(a, value) receives each output as soon as it is formed.
+template <int a, bool FORCE, class Out>
+__device__ __forceinline__ void trt_pair2(const float2* d, Out&& out, const Collide2& K, float omp, float omm,
                                           float w, float cp, float cm) {
     constexpr int b = a + 1;
     const float2 cu = cdot2<a>(K.ux, K.uy, K.uz);
@@ -505,12 +507,14 @@ __device__ __forceinline__ void trt_pair2(const float2* d, float2* o, const Coll
         oa = p2add(oa, p2add(sp, sm));
         ob = p2add(ob, p2sub(sp, sm));
     }
-    o[a] = oa;
-    o[b] = ob;
+    out(a, oa);
+    out(b, ob);
 }
 
-template <bool FORCE>
-__device__ __forceinline__ void collide_dev2(const float2* d, float2* o, float omp, float omm, float gx, float gy,
+// The outputs go to out(a, value) in the order 0, 1, 2, ..., 18 (so that the
+// caller can store them without holding all nineteen).
+template <bool FORCE, class Out>
+__device__ __forceinline__ void collide_dev2(const float2* d, Out&& out, float omp, float omm, float gx, float gy,
                                              float gz) {
     Collide2 K;
     K.drho = p2add(p2add(p2add(p2add(d[0], d[1]), p2add(d[2], d[3])), p2add(p2add(d[4], d[5]), p2add(d[6], d[7]))),
@@ -542,17 +546,17 @@ __device__ __forceinline__ void collide_dev2(const float2* d, float2* o, float o
         const float2 t = p2fma(K.rho, K.nusq15, K.drho);
         float2 o0 = p2fma(p2(-omp), p2sub(d[0], p2mul(p2(w0), t)), d[0]);
         if constexpr (FORCE) o0 = p2fma(p2(cp * w0 * -3.f), K.uF, o0);
-        o[0] = o0;
+        out(0, o0);
     }
-    trt_pair2<1, FORCE>(d, o, K, omp, omm, w1, cp, cm);
-    trt_pair2<3, FORCE>(d, o, K, omp, omm, w1, cp, cm);
-    trt_pair2<5, FORCE>(d, o, K, omp, omm, w1, cp, cm);
-    trt_pair2<7, FORCE>(d, o, K, omp, omm, w2, cp, cm);
-    trt_pair2<9, FORCE>(d, o, K, omp, omm, w2, cp, cm);
-    trt_pair2<11, FORCE>(d, o, K, omp, omm, w2, cp, cm);
-    trt_pair2<13, FORCE>(d, o, K, omp, omm, w2, cp, cm);
-    trt_pair2<15, FORCE>(d, o, K, omp, omm, w2, cp, cm);
-    trt_pair2<17, FORCE>(d, o, K, omp, omm, w2, cp, cm);
+    trt_pair2<1, FORCE>(d, out, K, omp, omm, w1, cp, cm);
+    trt_pair2<3, FORCE>(d, out, K, omp, omm, w1, cp, cm);
+    trt_pair2<5, FORCE>(d, out, K, omp, omm, w1, cp, cm);
+    trt_pair2<7, FORCE>(d, out, K, omp, omm, w2, cp, cm);
+    trt_pair2<9, FORCE>(d, out, K, omp, omm, w2, cp, cm);
+    trt_pair2<11, FORCE>(d, out, K, omp, omm, w2, cp, cm);
+    trt_pair2<13, FORCE>(d, out, K, omp, omm, w2, cp, cm);
+    trt_pair2<15, FORCE>(d, out, K, omp, omm, w2, cp, cm);
+    trt_pair2<17, FORCE>(d, out, K, omp, omm, w2, cp, cm);
 }
 
 template <typename C>
@@ -795,22 +799,18 @@ __device__ __forceinline__ void liquid_pairs(const StepArgs& A, long long bid) {
             d[a] = make_float2(x0, x1);
         }
     }
-    float2 o[19];
+    // each output is stored as soon as it is formed: one 32-bit store per
+    // direction when both cells are liquid, else the liquid lane's 16 bits
+    auto out = [&](int a, float2 v) {
+        if (a == 0 && ((v0 && !(v.x == v.x)) || (v1 && !(v.y == v.y)))) set_status(A.status, ST_NAN);
+        if (v0 && v1) Form<T>::st_dev2(dst + (a * S + gi), v);
+        else if (v0) Form<T>::st_dev(dst + (a * S + gi), v.x);
+        else Form<T>::st_dev(dst + (a * S + gi + 1u), v.y);
+    };
     if (D.has_force)
-        collide_dev2<true>(d, o, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
+        collide_dev2<true>(d, out, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
     else
-        collide_dev2<false>(d, o, R.omp, R.omm, 0.f, 0.f, 0.f);
-    if ((v0 && !(o[0].x == o[0].x)) || (v1 && !(o[0].y == o[0].y))) set_status(A.status, ST_NAN);
-    if (v0 && v1) {
-#pragma unroll
-        for (int a = 0; a < 19; ++a) Form<T>::st_dev2(dst + (a * S + gi), o[a]);
-    } else if (v0) {
-#pragma unroll
-        for (int a = 0; a < 19; ++a) Form<T>::st_dev(dst + (a * S + gi), o[a].x);
-    } else {
-#pragma unroll
-        for (int a = 0; a < 19; ++a) Form<T>::st_dev(dst + (a * S + gi + 1u), o[a].y);
-    }
+        collide_dev2<false>(d, out, R.omp, R.omm, 0.f, 0.f, 0.f);
 }
 
 // Coordinates of one interface cell, for the 5x5x5 fill-level stencil of the
@@ -941,6 +941,9 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 #ifndef FSL_IF_GRID
 #define FSL_IF_GRID 2     // interface blocks per SM in the grid (ifb is two per SM)
 #endif
+#ifndef FSL_STREAM_MINB
+#define FSL_STREAM_MINB 3 // resident stream-collide blocks per SM the FP32-collide forms are compiled for
+#endif
 template <typename T> struct IfCells {   // cells per pass of a 256-thread block
     static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : 32;
 };
@@ -952,13 +955,14 @@ struct IfStage {
     C fs[N][19];       // own post-collision PDFs of the previous step
     C fy[N][19];       // PDF streaming in from the source cell
     C fin[N][19];      // PDFs after streaming and reconstruction
-    C ex[N][19];       // mass-exchange term of each link (Eq. 10)
+    C ex[N][19];       // mass-exchange term of each link (Eq. 10); until the gradient
+                       // phase, the fill level of the link's neighbour x + c_a
     C nrm[N][7][3];    // gradient at the cell, unit normals at the face neighbours
     C pv[N];           // bubble pressure (Eq. 13)
+    C px[N];           // fill level of the cell
     double m[N];       // mass
     int g[N];          // cell
-    uint8_t ty[N][19];
-    uint8_t tz[N][19];
+    uint8_t tz[N][19]; // type of the neighbour x + c_a (the source of direction opp(a))
 };
 
 __device__ inline int ph_index(int dx, int dy, int dz) { return (dx + 2) + 5 * (dy + 2) + 25 * (dz + 2); }
@@ -1044,28 +1048,31 @@ __device__ __forceinline__ void interface_chunk(const StepArgs& A, int i0, int c
                     }
                 }
             }
-            C fsv[ND], fyv[ND], fzv[ND], phz[ND];
-            uint8_t tyv[ND], tzv[ND];
+            // per direction a: the own PDF, the PDF streaming in from x - c_a,
+            // and type and fill level of x + c_a.  The source x - c_a of
+            // direction a is the neighbour x + c_b of b = opp(a), so the
+            // source's type and the PDF f_b(x + c_a) of the mass exchange are
+            // loads the thread of the opposite direction makes (each neighbour
+            // is read once)
+            C fsv[ND], fyv[ND], phz[ND];
+            uint8_t tzv[ND];
 #pragma unroll
             for (int k = 0; k < ND; ++k) {
                 const int a = q + TPC * k;
                 if (a < 19) {
                     fsv[k] = Form<T>::ld(src + ((unsigned)a * S + (unsigned)g), a);
                     if (a > 0) {
-                        const int ab = opp(a);
                         const int ax = rcx(a), ay = rcy(a), az = rcz(a);
                         const unsigned y = st.at(-ax, -ay, -az);
                         const unsigned z = st.at(ax, ay, az);
-                        tyv[k] = ctype(A.flag[y]);
                         fyv[k] = Form<T>::ld(src + ((unsigned)a * S + y), a);
                         tzv[k] = ctype(A.flag[z]);
-                        fzv[k] = Form<T>::ld(src + ((unsigned)ab * S + z), ab);
                         phz[k] = phic[z];
                     }
                 }
             }
-            const C phx = phic[g];
             if (q == TPC - 1) {
+                sh.px[c] = phic[g];
                 sh.m[c] = A.m[g];
                 sh.g[c] = (int)g;
                 const int bub = A.id[g];
@@ -1094,21 +1101,27 @@ __device__ __forceinline__ void interface_chunk(const StepArgs& A, int i0, int c
                 if (a < 19) {
                     sh.fs[c][a] = fsv[k];
                     if (a > 0) {
-                        sh.ty[c][a] = tyv[k];
                         sh.fy[c][a] = fyv[k];
                         sh.tz[c][a] = tzv[k];
-                        if (tzv[k] == LIQ || tzv[k] == IFC) {
-                            const C e = fzv[k] - fsv[k];
-                            sh.ex[c][a] = tzv[k] == IFC ? ((C)0.5 * (phx + phz[k])) * e : e;
-                        }
+                        sh.ex[c][a] = phz[k];
                     }
                 }
             }
         }
         __syncthreads();
-        // ---------------- gradient phase: point j (the cell, then its +x, -x,
-        // +y, -y, +z, -z neighbours) for j = q, q + TPC, ...
+        // ---------------- gradient phase: first the exchange term of each of
+        // the thread's directions a (Eq. 10) from f_b(x + c_a) - f_a(x), b =
+        // opp(a), weighted by the mean fill level when x + c_a is an interface
+        // cell; then point j (the cell, then its +x, -x, +y, -y, +z, -z
+        // neighbours) for j = q, q + TPC, ...
         if (i0 + c < cnt) {
+            for (int a = q > 0 ? q : TPC; a < 19; a += TPC) {
+                const uint8_t tz = sh.tz[c][a];
+                if (tz == LIQ || tz == IFC) {
+                    const C e = sh.fy[c][opp(a)] - sh.fs[c][a];
+                    sh.ex[c][a] = tz == IFC ? ((C)0.5 * (sh.px[c] + sh.ex[c][a])) * e : e;
+                }
+            }
             for (int j = q; j < 7; j += TPC) {
                 const int ox = j == 1 ? 1 : (j == 2 ? -1 : 0);
                 const int oy = j == 3 ? 1 : (j == 4 ? -1 : 0);
@@ -1168,7 +1181,7 @@ __device__ __forceinline__ void interface_chunk(const StepArgs& A, int i0, int c
                     } else {
                         const int ab = opp(a);
                         const C fsb = sh.fs[c][ab];
-                        const uint8_t ty = sh.ty[c][a];
+                        const uint8_t ty = sh.tz[c][ab];   // type of x - c_a = x + c_ab
                         if (ty == OBS) {
                             fin = fsb;
                         } else if (ty == LID) {
@@ -1262,7 +1275,7 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
 // [0, nif) take the interface cells from the list (they are launched first,
 // so they are placed first), the other blocks the liquid cells.
 template <typename T, bool ONE>
-__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream(StepArgs A, int nif) {
+__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : FSL_STREAM_MINB) k_stream(StepArgs A, int nif) {
     __shared__ IfStage<T> sh;
     pdl_trigger();   // the conversion kernel may be placed as blocks finish
     if ((int)blockIdx.x < nif) {
@@ -1285,7 +1298,7 @@ __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream(St
 // items in flight at any time lie close together in the lattice.  Results are
 // those of the split form: every cell runs the same arithmetic.
 template <typename T, bool ONE, int LT>
-__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream_pers(StepArgs A) {
+__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : FSL_STREAM_MINB) k_stream_pers(StepArgs A) {
     __shared__ IfStage<T> sh;
     pdl_trigger();   // the conversion kernel may be placed as blocks finish
     if (blockIdx.x == 0) step_counters(A);
@@ -1313,10 +1326,58 @@ __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : 3) k_stream_pe
     }
 }
 
+// First position in the (cell-ordered) interface list whose cell is >= cell.
+__device__ inline int list_lower_bound(const int* list, int n, long long cell) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)list[mid] < cell) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Slab form of the persistent stream-collide kernel (needs the interface list
+// in cell order): block b owns the contiguous tiles [T b / grid, T (b + 1) /
+// grid) and processes its liquid tiles and the interface cells that lie in
+// them (a list range found by binary search), the two interleaved in
+// proportion as in k_stream_pers.  A block works through one region of the
+// lattice, so the neighbour data of its interface cells is mostly data its
+// own liquid tiles and earlier chunks have just brought into its SM.
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : FSL_STREAM_MINB) k_stream_slab(StepArgs A) {
+    __shared__ IfStage<T> sh;
+    __shared__ int range[2];
+    pdl_trigger();   // the conversion kernel may be placed as blocks finish
+    if (blockIdx.x == 0) step_counters(A);
+    constexpr int N = IfCells<T>::n;
+    constexpr long long TILE = Form<T>::shifted ? 2 * FSL_BLOCK : FSL_BLOCK;
+    const int cnt = *A.icount;
+    const long long ntile = (A.stride + TILE - 1) / TILE;
+    const long long t0 = ntile * blockIdx.x / gridDim.x, t1 = ntile * (blockIdx.x + 1) / gridDim.x;
+    if (threadIdx.x < 2)
+        range[threadIdx.x] = list_lower_bound(A.ilist, cnt, (threadIdx.x == 0 ? t0 : t1) * TILE);
+    __syncthreads();
+    const int l0 = range[0], l1 = range[1];
+    const long long nI = (l1 - l0 + N - 1) / N;
+    const long long nL = t1 - t0;
+    const long long M = nI + nL;
+    for (long long w = 0; w < M; ++w) {
+        const long long c0 = (w * nI) / M, c1 = ((w + 1) * nI) / M;
+        if (c1 > c0) {
+            interface_chunk<T, ONE>(A, l0 + (int)(c0 * N), l1, sh);
+        } else {
+            const long long tile = t0 + (w - c0);
+            if constexpr (Form<T>::shifted) liquid_pairs<T, ONE>(A, tile);
+            else liquid_single<T, ONE>(A, tile);
+        }
+    }
+}
+
 // Stream-collide kernel forms (the autotuner picks one per workload): the split
-// form (interface blocks first, then one block per liquid tile) and the
-// persistent form with 1, 2 or 4 tiles per liquid item.
-enum { SC_SPLIT = 0, SC_PERS1 = 1, SC_PERS2 = 2, SC_PERS4 = 3, SC_FORMS = 4 };
+// form (interface blocks first, then one block per liquid tile), the
+// persistent form with 1, 2 or 4 tiles per liquid item, and the slab form.
+enum { SC_SPLIT = 0, SC_PERS1 = 1, SC_PERS2 = 2, SC_PERS4 = 3, SC_SLAB = 4, SC_FORMS = 5 };
 
 // First neighbour of cell z (direction order) that is an interface cell
 // carrying mark `want`, or -1.
@@ -1673,6 +1734,51 @@ __device__ inline void mark_affected(const StepArgs& A, const CclArgs& K, int d,
     atomicExch(A.trig, 1);
 }
 
+// Unit normal n = -g / |g| of the fill level at cell w (Parker-Youngs gradient
+// g over the 3x3x3 stencil of the stencil fill levels), 0 where g = 0.
+__device__ inline void unit_normal_at(const StepArgs& A, const Dom& D, long long w, float& nx, float& ny, float& nz) {
+    const Cell c = make_cell(D, w);
+    float v[27];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+        const long long z = c.at(k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1);
+        v[k] = A.phitf ? A.phitf[z] : (float)A.phit[z];
+    }
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) {
+            const float W = (a == 0 && b == 0) ? 4.f : ((a == 0 || b == 0) ? 2.f : 1.f);
+            gx += W * (v[2 + 3 * (a + 1) + 9 * (b + 1)] - v[0 + 3 * (a + 1) + 9 * (b + 1)]);
+            gy += W * (v[(a + 1) + 3 * 2 + 9 * (b + 1)] - v[(a + 1) + 0 + 9 * (b + 1)]);
+            gz += W * (v[(a + 1) + 3 * (b + 1) + 9 * 2] - v[(a + 1) + 3 * (b + 1) + 0]);
+        }
+    }
+    const float q = gx * gx + gy * gy + gz * gz;
+    const float il = q > 0.f ? -rsqrtf(q) : 0.f;
+    nx = gx * il; ny = gy * il; nz = gz * il;
+}
+
+// The paper's split trigger (Sec. 2.3.2, Fig. "anti-parallel normals"): the
+// cell g, which fills and becomes liquid, has two interface neighbours of its
+// own bubble b (after this step's conversion) whose unit normals point in
+// opposite directions (n_i . n_j < -1/2): a liquid film between two parts of
+// one bubble, which may have cut it in two.
+__device__ inline bool antiparallel_normals(const StepArgs& A, const Dom& D, const Cell& c, long long g, int b) {
+    float nxs[18], nys[18], nzs[18];
+    int k = 0;
+    for (int a = 1; a < 19; ++a) {
+        const long long w = c.at(rcx(a), rcy(a), rcz(a));
+        if (new_type(ctype(A.flag[w]), A.mark[w]) != IFC || A.id[w] != b) continue;
+        unit_normal_at(A, D, w, nxs[k], nys[k], nzs[k]);
+        for (int j = 0; j < k; ++j)
+            if (nxs[j] * nxs[k] + nys[j] * nys[k] + nzs[j] * nzs[k] < -0.5f) return true;
+        ++k;
+    }
+    return false;
+}
+
 // Phase C, over the marked list and the new-from-liquid list: excess mass of
 // converted cells (filled: m - rho, emptied: m) split equally among the
 // neighbours that are interface after conversion, else pooled; merge / split
@@ -1723,7 +1829,9 @@ __device__ inline void convert_c_phase(const StepArgs& A, const CclArgs& K) {
                             if (ntz == GAS || ntz == IFC || later_filled)
                                 fgm |= 1u << ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
                         }
-                if (!removal_is_local(fgm)) mark_affected(A, K, d, A.id[g]);   // its bubble may split
+                const bool may_split = D.split_trigger ? antiparallel_normals(A, D, c, g, A.id[g])
+                                                       : !removal_is_local(fgm);
+                if (may_split) mark_affected(A, K, d, A.id[g]);   // its bubble may split
             }
             A.cstep[g] = step;
             A.mark[g] = (mk == MK_FILLED) ? MK_CFILLED : MK_CEMPTIED;
@@ -2355,6 +2463,9 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
                 k_stream<T, true><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                      \
             else                                                                                             \
                 k_stream<T, false><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                     \
+        } else if (form == SC_SLAB) {                                                                        \
+            if (A.ndom == 1) k_stream_slab<T, true><<<pg, FSL_BLOCK, 0, s>>>(A);                             \
+            else k_stream_slab<T, false><<<pg, FSL_BLOCK, 0, s>>>(A);                                        \
         } else if (A.ndom == 1) {                                                                            \
             if (form == SC_PERS1) k_stream_pers<T, true, 1><<<pg, FSL_BLOCK, 0, s>>>(A);                    \
             else if (form == SC_PERS2) k_stream_pers<T, true, 2><<<pg, FSL_BLOCK, 0, s>>>(A);               \
@@ -2370,6 +2481,10 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
     template <> int stream_blocks_per_sm<T>(int form, bool one) {                                            \
         int nb = 0;                                                                                          \
         if (form == SC_SPLIT) nb = 1;                                                                        \
+        else if (form == SC_SLAB && one)                                                                     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_slab<T, true>, FSL_BLOCK, 0);        \
+        else if (form == SC_SLAB)                                                                            \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_slab<T, false>, FSL_BLOCK, 0);       \
         else if (one && form == SC_PERS1)                                                                    \
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, true, 1>, FSL_BLOCK, 0);     \
         else if (one && form == SC_PERS2)                                                                    \

@@ -45,7 +45,8 @@ class Params(ctypes.Structure):
                 ("collision", ctypes.c_int32), ("tau", ctypes.c_double), ("magic", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("eps", ctypes.c_double),
                 ("lid_velocity", ctypes.c_double * 3), ("normal_rule", ctypes.c_int32),
-                ("bubble_capacity", ctypes.c_int32), ("lonely_rule", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("bubble_capacity", ctypes.c_int32), ("lonely_rule", ctypes.c_int32),
+                ("split_trigger", ctypes.c_int32)]
 
 
 class BubbleRec(ctypes.Structure):
@@ -125,7 +126,8 @@ def load_library():
 
 
 def make_params(nx, ny, nz, collision=0, tau=0.8, magic=3.0 / 16.0, sigma=0.0, gravity=(0.0, 0.0, 0.0),
-                eps=1e-3, lid=(0.0, 0.0, 0.0), normal_rule=1, lonely_rule=1, bubble_capacity=0) -> Params:
+                eps=1e-3, lid=(0.0, 0.0, 0.0), normal_rule=1, lonely_rule=1, bubble_capacity=0,
+                split_trigger=0) -> Params:
     p = Params()
     p.nx, p.ny, p.nz = nx, ny, nz
     p.collision, p.tau, p.magic, p.sigma = collision, tau, magic, sigma
@@ -136,7 +138,7 @@ def make_params(nx, ny, nz, collision=0, tau=0.8, magic=3.0 / 16.0, sigma=0.0, g
     p.normal_rule = normal_rule
     p.lonely_rule = lonely_rule
     p.bubble_capacity = bubble_capacity
-    p.reserved = 0
+    p.split_trigger = split_trigger
     return p
 
 
@@ -201,9 +203,9 @@ class Simulation:
     """One handle of the library: one or more independent lattices on one GPU."""
 
     def __init__(self, params: Sequence[dict], precision: str = "fp64", stream: Optional[int] = None,
-                 bubble_capacity: int = 0):
+                 bubble_capacity: int = 0, split_trigger: int = 0):
         self.L = load_library()
-        plist = [make_params(**p, bubble_capacity=bubble_capacity) for p in params]
+        plist = [make_params(**p, bubble_capacity=bubble_capacity, split_trigger=split_trigger) for p in params]
         self.dims = [(p.nx, p.ny, p.nz) for p in plist]
         arr = (Params * len(plist))(*plist)
         self.stream = _default_stream() if stream is None else stream
@@ -334,15 +336,15 @@ class Simulation:
 
     def set_stream_form(self, form: int):
         """Stream-collide kernel form: 0 split, 1/2/3 persistent with 1/2/4 tiles per liquid
-        item, -1 autotune again."""
+        item, 4 slab (interface list in cell order only), -1 autotune again."""
         self._check(self.L.fsl_set_stream_form(self._h, int(form)))
 
     def tuning(self) -> dict:
         """Autotuner record: per-form stream-collide ms, chosen form, source."""
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 5)()
         form, src = ctypes.c_int32(0), ctypes.c_int32(0)
         self._check(self.L.fsl_tuning(self._h, ms, ctypes.byref(form), ctypes.byref(src)))
-        names = ("split", "persistent_1tile", "persistent_2tiles", "persistent_4tiles")
+        names = ("split", "persistent_1tile", "persistent_2tiles", "persistent_4tiles", "slab")
         return {"ms_per_form": dict(zip(names, [round(v, 5) for v in ms])),
                 "form": int(form.value), "form_name": names[form.value] if form.value >= 0 else None,
                 "source": ("none", "measured", "cache", "caller")[src.value]}

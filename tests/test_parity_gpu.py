@@ -350,12 +350,12 @@ def test_persistent_stream_forms_bitexact(fsl, oracle_mod, form):
     sim.close()
 
 
-@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("form", [0, 1, 4])
 def test_cell_ordered_interface_list_bitexact(fsl, oracle_mod, form):
     """The interface list rebuilt in cell order after every conversion (two
     passes over the cell types inside the conversion kernel) changes only the
-    order of the work: the oracle's state bit for bit, split and persistent
-    stream-collide forms."""
+    order of the work: the oracle's state bit for bit, split, persistent and
+    slab stream-collide forms."""
     scs = [S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=s)
            for s in (2, 3)]
     sim = fsl.Simulation.from_scenarios(scs, precision="fp64")
@@ -372,3 +372,40 @@ def test_cell_ordered_interface_list_bitexact(fsl, oracle_mod, form):
         for d, o in enumerate(oras):
             compare_exact(gpu_state(sim, d), oracle_state(o), what=f"ordered list form {form} domain {d} step {k}")
     sim.close()
+
+
+def _paper_trigger_cases():
+    scs = [S.gas_thread(nx=48, ny=20, nz=20, radius=3.0, amp=0.25, wavelength=24, sigma=0.05, steps=0)]
+    scs += [S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=s)
+            for s in (0, 1, 2)]
+    scs += S.bubble_population(n_domains=2, seed=5, sides=(32, 48))
+    return scs
+
+
+def test_paper_split_trigger_against_exact_trigger_and_oracle(fsl, oracle_mod):
+    """The paper's split trigger (anti-parallel normals around a cell that
+    fills, Sec. 2.3.2) against the exact local test and the oracle (which
+    labels every step), on the thread breakup, moving bubbles with merges and
+    splits, and two bubble-population domains: over 120 steps the two
+    triggers give the same cell types, bubble ids and bubble tables, equal to
+    the oracle's.  The number of labelling passes of each is printed (the
+    two criteria fire on different steps)."""
+    scs = _paper_trigger_cases()
+    exact = fsl.Simulation.from_scenarios(scs, precision="fp64")
+    paper = fsl.Simulation.from_scenarios(scs, precision="fp64", split_trigger=1)
+    oras = [oracle_mod.Oracle.from_scenario(s) for s in scs]
+    prev = 0
+    for k in (10, 40, 80, 90, 100, 120):
+        for sim in (exact, paper):
+            sim.step(k - prev)
+        for o in oras:
+            o.step(k - prev)
+        prev = k
+        for d, o in enumerate(oras):
+            r = oracle_state(o)
+            compare_exact(gpu_state(exact, d), r, what=f"exact trigger domain {d} step {k}")
+            compare_exact(gpu_state(paper, d), r, what=f"paper trigger domain {d} step {k}")
+    print(f"labelling passes over {prev} steps: exact trigger {exact.labelling_runs}, "
+          f"paper trigger {paper.labelling_runs}")
+    exact.close()
+    paper.close()
