@@ -206,9 +206,9 @@ fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_p
 /* Form of the stream-collide kernel (the same results in every form; each
  * cell runs the same arithmetic).  By default (form -1) the library tunes it:
  * the first fsl_step calls of a handle run real steps that each time one
- * candidate form (every form twice, the slab form only with the interface
- * list in cell order: eight or ten steps; direct launches, the call waits
- * for each), then keep the fastest and record it in a process-wide cache keyed by
+ * candidate form (every usable form twice: the slab form only with the
+ * interface list in cell order, the tile-fused forms not in FP64; direct
+ * launches, the call waits for each), then keep the fastest and record it in a process-wide cache keyed by
  * precision, one or many domains, SM count, lattice size (log2 of the padded
  * cells) and interface share (1/64 steps); a later handle of the same key
  * takes the cached form without tuning.  Forms:
@@ -220,14 +220,19 @@ fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_p
  *   4  slab: each block of a resident grid owns a contiguous range of tiles
  *      and processes their liquid cells and the interface cells among them,
  *      interleaved (only with the interface list in cell order, see
- *      fsl_set_interface_order; FSL_ERR_ARG otherwise).
+ *      fsl_set_interface_order; FSL_ERR_ARG otherwise);
+ *   5  two kernels: the liquid cells (a tile per block), then the interface
+ *      cells one per thread with every direction unrolled;
+ *   6, 7  tile-fused: each block takes 2 or 4 tiles, streams and collides
+ *      their liquid cells, then their interface cells one per thread (FP32
+ *      and 16-bit storage only; FSL_ERR_ARG for FP64).
  * -1 restarts the tuning.  Waits for the handle's stream; the next fsl_step
  * rebuilds its graphs.  FSL_ERR_ARG for another value.  fsl_stream_form
  * returns the form in use (the one tried next while tuning). */
 fsl_status fsl_set_stream_form(fsl_domain* h, int32_t form);
 int32_t fsl_stream_form(const fsl_domain* h);
 
-/* Autotuner record of the handle: ms_per_form (array of 5, may be NULL) the
+/* Autotuner record of the handle: ms_per_form (array of 8, may be NULL) the
  * fastest stream-collide time measured per form (0 = not run); *form the
  * chosen form (-1 while tuning); *source 0 = not decided, 1 = measured on
  * this handle, 2 = from the process cache, 3 = set by the caller. */

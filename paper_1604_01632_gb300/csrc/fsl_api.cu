@@ -28,8 +28,8 @@ const int kDefaultCapacityMin = 256;
 // Candidate sequence of the autotuner: every form twice, the faster of its two
 // timed steps counts (the slab form only where the interface list is kept in
 // cell order; it is skipped otherwise).
-const int kTuneSeq[] = {SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB,
-                        SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB};
+const int kTuneSeq[] = {SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB, SC_TWO, SC_TILE2, SC_TILE4,
+                        SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB, SC_TWO, SC_TILE2, SC_TILE4};
 const int kTuneSteps = (int)(sizeof(kTuneSeq) / sizeof(kTuneSeq[0]));
 
 // Process-wide cache of tuning decisions, keyed by the workload's shape:
@@ -63,13 +63,13 @@ struct fsl_domain {
     // CUDA events around its stream-collide kernel (direct launches)
     bool tuning = true;           // auto mode and not yet decided
     int tune_next = 0;            // index into the candidate sequence
-    double tune_ms[SC_FORMS] = {0, 0, 0, 0, 0};   // best measured time per form (0: not run)
+    double tune_ms[SC_FORMS] = {};   // best measured time per form (0: not run)
     int tune_source = 0;          // 0 none yet, 1 measured here, 2 taken from the process cache, 3 fixed by the caller
     cudaEvent_t tev[2] = {nullptr, nullptr};
     int order_mode = -1;          // interface list in cell order: 1 on, 0 off, -1 by lattice size
     long long l2bytes = 0;        // L2 cache of the device
     int* ocnt = nullptr;          // interface cells per conversion block (ordered rebuild)
-    int pgrid[SC_FORMS] = {0, 0, 0, 0, 0};   // resident grid of each persistent form
+    int pgrid[SC_FORMS] = {};     // resident grid of each persistent form
     int convblocks = 152;         // grid of the cooperative conversion kernel
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<fsl_params> params;
@@ -792,6 +792,15 @@ static void drop_graphs(fsl_domain* h);
 
 namespace {
 
+// The slab form needs the interface list in cell order; the tile-fused forms
+// exist for the FP32-collide storage forms only (the FP64 cell needs more
+// registers than two blocks per SM leave it).
+bool form_usable(const fsl_domain* h, int f) {
+    if (f == SC_SLAB) return order_effective(h) != 0;
+    if (f == SC_TILE2 || f == SC_TILE4) return h->precision != FSL_P_FP64;
+    return f >= 0 && f < SC_FORMS;
+}
+
 TuneKey tune_key(fsl_domain* h, int icount) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -819,7 +828,7 @@ fsl_status tune_step(fsl_domain* h) {
             return FSL_OK;   // no step taken: the caller runs it with the cached form
         }
     }
-    while (h->tune_next < kTuneSteps && kTuneSeq[h->tune_next] == SC_SLAB && !order_effective(h)) ++h->tune_next;
+    while (h->tune_next < kTuneSteps && !form_usable(h, kTuneSeq[h->tune_next])) ++h->tune_next;
     const int f = kTuneSeq[h->tune_next];
     if (!h->tev[0]) {
         CK(h, cudaEventCreate(&h->tev[0]));
@@ -837,7 +846,7 @@ fsl_status tune_step(fsl_domain* h) {
     CK(h, cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]));
     if (h->tune_ms[f] == 0.0 || ms < h->tune_ms[f]) h->tune_ms[f] = ms;
     ++h->tune_next;
-    while (h->tune_next < kTuneSteps && kTuneSeq[h->tune_next] == SC_SLAB && !order_effective(h)) ++h->tune_next;
+    while (h->tune_next < kTuneSteps && !form_usable(h, kTuneSeq[h->tune_next])) ++h->tune_next;
     if (h->tune_next == kTuneSteps) {
         int best = SC_SPLIT;
         for (int g = 0; g < SC_FORMS; ++g)
@@ -989,8 +998,9 @@ static void drop_graphs(fsl_domain* h) {
 
 fsl_status fsl_set_stream_form(fsl_domain* h, int32_t form) {
     if (!h || form < -1 || form >= SC_FORMS) return fail(h, FSL_ERR_ARG, "bad stream-collide form");
-    if (form == SC_SLAB && !order_effective(h))
-        return fail(h, FSL_ERR_ARG, "the slab form needs the interface list in cell order");
+    if (form >= 0 && !form_usable(h, form))
+        return fail(h, FSL_ERR_ARG, form == SC_SLAB ? "the slab form needs the interface list in cell order"
+                                                    : "the tile-fused forms need FP32 or 16-bit storage");
     CK(h, cudaStreamSynchronize(h->ls));
     if (form < 0) {
         // autotune again from the next step on (the process cache is consulted first)

@@ -944,8 +944,11 @@ __device__ inline C collide_out(int a, const C* fin, const CollidePrep<C>& P, C 
 #ifndef FSL_STREAM_MINB
 #define FSL_STREAM_MINB 3 // resident stream-collide blocks per SM the FP32-collide forms are compiled for
 #endif
+#ifndef FSL_IF_CELLS
+#define FSL_IF_CELLS 32   // interface cells per pass of the FP32-collide forms (256 / threads per cell)
+#endif
 template <typename T> struct IfCells {   // cells per pass of a 256-thread block
-    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : 32;
+    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 16 : FSL_IF_CELLS;
 };
 template <typename T>
 struct IfStage {
@@ -1271,6 +1274,320 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
     for (int i0 = bid * N; i0 < cnt; i0 += nbl * N) interface_chunk<T, ONE>(A, i0, cnt, sh);
 }
 
+// ------------------------------------------- interface cells, one per thread
+// The 81 fill levels the curvature needs (Eq. 15 through the divergence of the
+// Parker-Youngs normals at the six face neighbours): every offset within +-1
+// on all axes (27), and those with one axis at +-2 and the other two within
+// +-1 (54).  Compact index of such an offset:
+__host__ __device__ constexpr int st81(int dx, int dy, int dz) {
+    return (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
+               ? (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
+           : (dx == 2 || dx == -2) ? 27 + (dx > 0 ? 9 : 0) + (dy + 1) + 3 * (dz + 1)
+           : (dy == 2 || dy == -2) ? 45 + (dy > 0 ? 9 : 0) + (dx + 1) + 3 * (dz + 1)
+                                   : 63 + (dz > 0 ? 9 : 0) + (dx + 1) + 3 * (dy + 1);
+}
+__host__ __device__ constexpr bool in81(int dx, int dy, int dz) {
+    return ((dx == 2 || dx == -2) ? 1 : 0) + ((dy == 2 || dy == -2) ? 1 : 0) + ((dz == 2 || dz == -2) ? 1 : 0) <= 1;
+}
+
+// Threads (cells) per block of the one-thread-per-cell interface kernel; the
+// block's stencil staging is 81 values per thread in shared memory.
+template <typename T> struct IfThreads {
+    static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 64 : 128;
+};
+
+// Parker-Youngs gradient at offset (ox, oy, oz) of the staged stencil, the
+// weighted central differences summed in the order of the two-level loop the
+// other interface path (and the oracle) use.
+template <typename C, int IB, int ox, int oy, int oz>
+__device__ __forceinline__ void pyg(const C* stc, int t, C& gx, C& gy, C& gz) {
+    gx = (C)0; gy = (C)0; gz = (C)0;
+#pragma unroll
+    for (int b = -1; b <= 1; ++b) {
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) {
+            const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
+            gx = gx + W * (stc[st81(ox + 1, oy + a, oz + b) * IB + t] - stc[st81(ox - 1, oy + a, oz + b) * IB + t]);
+            gy = gy + W * (stc[st81(ox + a, oy + 1, oz + b) * IB + t] - stc[st81(ox + a, oy - 1, oz + b) * IB + t]);
+            gz = gz + W * (stc[st81(ox + a, oy + b, oz + 1) * IB + t] - stc[st81(ox + a, oy + b, oz - 1) * IB + t]);
+        }
+    }
+}
+// Unit normal -g/|g| at a face neighbour (0 where g = 0).
+template <typename C, int IB, int ox, int oy, int oz>
+__device__ __forceinline__ void pyn(const C* stc, int t, C& nx, C& ny, C& nz) {
+    pyg<C, IB, ox, oy, oz>(stc, t, nx, ny, nz);
+    const C qq = nx * nx + ny * ny + nz * nz;
+    if (qq > (C)0) {
+        const C len = sqrt(qq);
+        nx = -(nx / len); ny = -(ny / len); nz = -(nz / len);
+    } else {
+        nx = (C)0; ny = (C)0; nz = (C)0;
+    }
+}
+
+// One interface cell g by one thread, every direction unrolled: the same
+// steps and the same arithmetic, operation by operation, as the shared
+// interface pass (stream with bounce-back, Eq. 7; mass exchange over the 18
+// links in direction order, Eq. 10; reconstruction from the bubble's gas
+// density 3 (p_V + 2 sigma kappa), Eqs. 8, 11-15; collision, Eq. 6; filled /
+// emptied marks).  stc: the block's stencil staging, [81][IB].  Returns
+// whether the cell was marked.
+template <typename T, bool ONE, int IB>
+__device__ __forceinline__ bool iface_one(const StepArgs& A, long long g, typename Form<T>::C* stc) {
+    using C = typename Form<T>::C;
+    const int t = threadIdx.x;
+    const Dom& D = dom_at<ONE>(A, g);
+    const Par<C> R = par_of<C>(D);
+    const Stencil st = make_stencil(D, g);
+    const unsigned S = (unsigned)A.stride;
+    const T* __restrict__ src = (const T*)A.fsrc;
+    T* __restrict__ dst = (T*)A.fdst;
+    const C* __restrict__ phic;
+    const C* __restrict__ phtc;
+    if constexpr (sizeof(C) == 8) { phic = A.phi; phtc = A.phit; }
+    else { phic = A.phif; phtc = A.phitf; }
+    // the stencil fill levels into the staging; those of the cell and of its
+    // 18 neighbours follow below from the types and fill levels loaded there
+#pragma unroll
+    for (int dz = -2; dz <= 2; ++dz)
+#pragma unroll
+        for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int nz = (dx != 0) + (dy != 0) + (dz != 0);
+                const bool d3q19 = nz <= 2 && dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+                if (in81(dx, dy, dz) && !d3q19) stc[st81(dx, dy, dz) * IB + t] = phtc[st.at(dx, dy, dz)];
+            }
+    // (no load of the next group is moved above these stores: the two groups
+    // in flight together would not fit the registers)
+    asm volatile("" ::: "memory");
+    // own PDFs, and per direction a the source x - c_a: its type, the PDF
+    // streaming in and its fill level
+    // (the 18 source types packed 3 bits each: ty(a) = (tym >> 3a) & 7)
+    C fs[19], fy[19], phy[19];
+    unsigned long long tym = 0;
+    fs[0] = Form<T>::ld(src + (unsigned)g, 0);
+#pragma unroll
+    for (int a = 1; a < 19; ++a) {
+        fs[a] = Form<T>::ld(src + ((unsigned)a * S + (unsigned)g), a);
+        const unsigned y = st.at(-cx(a), -cy(a), -cz(a));
+        tym |= (unsigned long long)ctype(A.flag[y]) << (3 * a);
+        fy[a] = Form<T>::ld(src + ((unsigned)a * S + y), a);
+        phy[a] = phic[y];
+    }
+    auto ty = [&](int a) { return (uint8_t)((tym >> (3 * a)) & 7u); };
+    // the stencil value of a cell is a function of its type and fill level
+    // (walls and liquid 1, gas 0, interface the fill level clamped to [0, 1]),
+    // the same expression that keeps the stored copy
+    auto stv = [&](uint8_t ty_, C ph) -> C {
+        if (ty_ == IFC) {
+            if constexpr (sizeof(C) == 8) return ph < 0.0 ? 0.0 : (ph > 1.0 ? 1.0 : ph);
+            else return fminf(fmaxf(ph, 0.f), 1.f);
+        }
+        return ty_ == GAS ? (C)0 : (C)1;
+    };
+#pragma unroll
+    for (int a = 1; a < 19; ++a) stc[st81(-cx(a), -cy(a), -cz(a)) * IB + t] = stv(ty(a), phy[a]);
+    const C phx = phic[g];
+    stc[st81(0, 0, 0) * IB + t] = stv(IFC, phx);
+    const double m0 = A.m[g];
+    const int bub = A.id[g];
+    C pv;
+    if constexpr (sizeof(C) == 8)
+        pv = bub >= 0 ? bubble_pressure(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : 1.0 / 3.0;
+    else
+        pv = bub >= 0 ? bubble_pressure_f(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : (float)(1.0 / 3.0);
+    // mass exchange (Eq. 10): link a reaches x + c_a = x - c_b, b = opp(a), whose
+    // type, PDF f_b streaming in and fill level are the loads of direction b
+    C dm = (C)0;
+    bool has_gas = false, has_liq = false;
+#pragma unroll
+    for (int a = 1; a < 19; ++a) {
+        const int b = opp(a);
+        const uint8_t tz = ty(b);
+        if (tz == LIQ || tz == IFC) {
+            const C e = fy[b] - fs[a];
+            dm = dm + (tz == IFC ? ((C)0.5 * (phx + phy[b])) * e : e);
+        }
+        has_gas |= tz == GAS;
+        has_liq |= tz == LIQ;
+    }
+    // gradient at the cell and unit normals at the face neighbours; curvature
+    C gx, gy, gz, n1x, n1y, n1z, n2x, n2y, n2z;
+    pyg<C, IB, 0, 0, 0>(stc, t, gx, gy, gz);
+    pyn<C, IB, 1, 0, 0>(stc, t, n1x, n1y, n1z);
+    pyn<C, IB, -1, 0, 0>(stc, t, n2x, n2y, n2z);
+    const C dX = n1x - n2x;
+    pyn<C, IB, 0, 1, 0>(stc, t, n1x, n1y, n1z);
+    pyn<C, IB, 0, -1, 0>(stc, t, n2x, n2y, n2z);
+    const C dY = n1y - n2y;
+    pyn<C, IB, 0, 0, 1>(stc, t, n1x, n1y, n1z);
+    pyn<C, IB, 0, 0, -1>(stc, t, n2x, n2y, n2z);
+    const C dZ = n1z - n2z;
+    const C kappa = (C)0.25 * ((dX + dY) + dZ);
+    // gas velocity: that of the cell's own post-collision PDFs
+    C rs, jsx, jsy, jsz;
+    moments<C>(fs, rs, jsx, jsy, jsz);
+    const C ugx = jsx / rs, ugy = jsy / rs, ugz = jsz / rs;
+    const C usg = ugx * ugx + ugy * ugy + ugz * ugz;
+    const C rg = (C)3 * (pv + R.sigma2 * kappa);
+    // stream with bounce-back and reconstruction
+    C fin[19];
+    fin[0] = fs[0];
+#pragma unroll
+    for (int a = 1; a < 19; ++a) {
+        const C fsb = fs[opp(a)];
+        const uint8_t tya = ty(a);
+        if (tya == OBS) {
+            fin[a] = fsb;
+        } else if (tya == LID) {
+            const C cuw = ((C)cx(a) * R.lid[0] + (C)cy(a) * R.lid[1]) + (C)cz(a) * R.lid[2];
+            fin[a] = fsb + ((C)6 * weightc<C>(a)) * cuw;
+        } else {
+            C fp, fm;
+            feq_pair<C>(a, rg, ugx, ugy, ugz, usg, fp, fm);
+            const C fga = (a & 1) ? fp + fm : fp - fm;
+            const C fgb = (a & 1) ? fp - fm : fp + fm;
+            if (tya == GAS) {
+                fin[a] = (fga + fgb) - fsb;
+            } else {
+                fin[a] = fy[a];
+                if (D.normal_rule && ((C)cx(a) * gx + (C)cy(a) * gy) + (C)cz(a) * gz > (C)0) fin[a] = (fga + fgb) - fsb;
+            }
+        }
+    }
+    // collision (Eq. 6) and the outputs
+    C rho;
+    if (D.has_force) {
+        const CollidePrep<C> P = collide_prep<C, true>(fin, R.g[0], R.g[1], R.g[2]);
+        rho = P.rho;
+#pragma unroll
+        for (int a = 0; a < 19; ++a)
+            Form<T>::st(dst + ((unsigned)a * S + (unsigned)g), a, collide_out<C, true>(a, fin, P, R.omp, R.omm));
+    } else {
+        const CollidePrep<C> P = collide_prep<C, false>(fin, (C)0, (C)0, (C)0);
+        rho = P.rho;
+#pragma unroll
+        for (int a = 0; a < 19; ++a)
+            Form<T>::st(dst + ((unsigned)a * S + (unsigned)g), a, collide_out<C, false>(a, fin, P, R.omp, R.omm));
+    }
+    if (!(rho == rho)) set_status(A.status, ST_NAN);
+    // the cell mass accumulates in FP64 for every form; fill / empty marks
+    const double mnew = m0 + (double)dm;
+    A.m[g] = mnew;
+    A.rhoi[g] = (double)rho;
+    bool filled, emptied;
+    if constexpr (sizeof(C) == 8) {
+        filled = mnew > (1.0 + D.eps) * rho;
+        emptied = mnew < (-D.eps) * rho;
+    } else {
+        const float mf = (float)mnew;
+        filled = mf > (1.f + D.feps) * rho;
+        emptied = mf < (-D.feps) * rho;
+    }
+    uint8_t mk = MK_NONE;
+    if (filled) mk = MK_FILLED;
+    else if (emptied) mk = MK_EMPTIED;
+    else if (D.lonely_rule) {
+        if (!has_gas) mk = MK_FILLED;
+        else if (!has_liq) mk = MK_EMPTIED;
+    }
+    A.mark[g] = mk;
+    return mk != MK_NONE;
+}
+
+// The interface cells of the list, one per thread, by a resident grid (block
+// b takes list entries b IB .. b IB + IB - 1, then those a grid further).
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(IfThreads<T>::n, sizeof(T) == 8 ? 4 : 4) k_iface(StepArgs A) {
+    using C = typename Form<T>::C;
+    constexpr int IB = IfThreads<T>::n;
+    __shared__ C stc[81 * IB];
+    pdl_trigger();   // the conversion kernel may be placed as blocks finish
+    if (blockIdx.x == 0) step_counters(A);
+    const int cnt = *A.icount;
+    for (long long base = (long long)blockIdx.x * IB; base < cnt; base += (long long)gridDim.x * IB) {
+        const long long i = base + threadIdx.x;
+        bool mk = false;
+        long long g = 0;
+        if (i < cnt) {
+            g = A.ilist[i];
+            mk = iface_one<T, ONE, IB>(A, g, stc);
+        }
+        list_append(A.mlist, A.mcount, mk, (int)g);
+    }
+}
+
+__device__ inline unsigned ifc_mask16(const uint8_t* flag, long long j);
+
+// Tile-fused form: block b takes the TPB tiles of super-tile b.  It streams
+// and collides their liquid cells, lists their interface cells in shared
+// memory (ballot compaction), then processes those one per thread.  The
+// interface cells' neighbour data is what the block has just read, and both
+// kinds of stores to a 32-byte sector meet in L2 before it is written back.
+// Dynamic shared memory: the stencil staging, 81 values per thread.
+template <typename T, bool ONE, int TPB>
+__global__ void __launch_bounds__(FSL_BLOCK, 2) k_stream_tile(StepArgs A) {
+    using C = typename Form<T>::C;
+    constexpr long long TILE = Form<T>::shifted ? 2 * FSL_BLOCK : FSL_BLOCK;
+    constexpr int SUPER = (int)(TPB * TILE);
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    C* stc = (C*)tile_smem;
+    __shared__ int il[SUPER];
+    __shared__ int nil;
+    pdl_trigger();   // the conversion kernel may be placed as blocks finish
+    if (blockIdx.x == 0) step_counters(A);
+    if (threadIdx.x == 0) nil = 0;
+    __syncthreads();
+    const long long c0 = (long long)blockIdx.x * SUPER;
+#pragma unroll 1
+    for (int k = 0; k < TPB; ++k) {
+        const long long tile = (long long)blockIdx.x * TPB + k;
+        if (tile * TILE >= A.stride) break;
+        if constexpr (Form<T>::shifted) liquid_pairs<T, ONE>(A, tile);
+        else liquid_single<T, ONE>(A, tile);
+    }
+    // the super-tile's interface cells (a 16-byte load of types per thread)
+    const unsigned lane = threadIdx.x & 31u;
+    for (long long j = c0 / 16 + threadIdx.x; j < (c0 + SUPER) / 16; j += FSL_BLOCK) {
+        const unsigned m = j * 16 < A.stride ? ifc_mask16(A.flag, j) : 0u;
+        const int n = __popc(m);
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (unsigned)o) incl += y;
+        }
+        int base = 0;
+        if (lane == 31) base = atomicAdd(&nil, incl);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        int pos = base + incl - n;
+        for (unsigned b = m; b; b &= b - 1) il[pos++] = (int)(16 * j + (__ffs(b) - 1));
+    }
+    __syncthreads();
+    const int ni = nil;
+    for (int i0 = 0; i0 < ni; i0 += FSL_BLOCK) {
+        const int i = i0 + threadIdx.x;
+        bool mk = false;
+        long long g = 0;
+        if (i < ni) {
+            g = il[i];
+            mk = iface_one<T, ONE, FSL_BLOCK>(A, g, stc);
+        }
+        list_append(A.mlist, A.mcount, mk, (int)g);
+    }
+}
+// dynamic shared memory of the tile-fused form
+template <typename T> constexpr int tile_smem_bytes() { return 81 * FSL_BLOCK * (int)sizeof(typename Form<T>::C); }
+
+// The liquid cells only (a tile per block), for the two-kernel form.
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(FSL_BLOCK, 3) k_liquid(StepArgs A) {
+    if constexpr (Form<T>::shifted) liquid_pairs<T, ONE>(A, (long long)blockIdx.x);
+    else liquid_single<T, ONE>(A, (long long)blockIdx.x);
+}
+
 // The stream-collide step (Eqs. 6, 7, 10, 11) as one kernel: blocks
 // [0, nif) take the interface cells from the list (they are launched first,
 // so they are placed first), the other blocks the liquid cells.
@@ -1376,8 +1693,11 @@ __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : FSL_STREAM_MIN
 
 // Stream-collide kernel forms (the autotuner picks one per workload): the split
 // form (interface blocks first, then one block per liquid tile), the
-// persistent form with 1, 2 or 4 tiles per liquid item, and the slab form.
-enum { SC_SPLIT = 0, SC_PERS1 = 1, SC_PERS2 = 2, SC_PERS4 = 3, SC_SLAB = 4, SC_FORMS = 5 };
+// persistent form with 1, 2 or 4 tiles per liquid item, the slab form, the
+// two-kernel form (liquid kernel, then one thread per interface cell), and
+// the tile-fused form with 2 or 4 tiles per block.
+enum { SC_SPLIT = 0, SC_PERS1 = 1, SC_PERS2 = 2, SC_PERS4 = 3, SC_SLAB = 4, SC_TWO = 5, SC_TILE2 = 6, SC_TILE4 = 7,
+       SC_FORMS = 8 };
 
 // First neighbour of cell z (direction order) that is an interface cell
 // carrying mark `want`, or -1.
@@ -2463,6 +2783,27 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
                 k_stream<T, true><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                      \
             else                                                                                             \
                 k_stream<T, false><<<(unsigned)(nif + nliq), FSL_BLOCK, 0, s>>>(A, nif);                     \
+        } else if (form == SC_TILE2 || form == SC_TILE4) {                                                  \
+            const long long tile = Form<T>::shifted ? 2LL * FSL_BLOCK : (long long)FSL_BLOCK;                \
+            const int tpb = form == SC_TILE2 ? 2 : 4;                                                       \
+            const unsigned nsup = (unsigned)((A.stride + tpb * tile - 1) / (tpb * tile));                    \
+            const int sm = tile_smem_bytes<T>();                                                             \
+            if (A.ndom == 1) {                                                                               \
+                if (tpb == 2) k_stream_tile<T, true, 2><<<nsup, FSL_BLOCK, sm, s>>>(A);                      \
+                else k_stream_tile<T, true, 4><<<nsup, FSL_BLOCK, sm, s>>>(A);                               \
+            } else {                                                                                         \
+                if (tpb == 2) k_stream_tile<T, false, 2><<<nsup, FSL_BLOCK, sm, s>>>(A);                     \
+                else k_stream_tile<T, false, 4><<<nsup, FSL_BLOCK, sm, s>>>(A);                              \
+            }                                                                                                \
+        } else if (form == SC_TWO) {                                                                         \
+            const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                     \
+            if (A.ndom == 1) {                                                                               \
+                k_liquid<T, true><<<(unsigned)nliq, FSL_BLOCK, 0, s>>>(A);                                   \
+                k_iface<T, true><<<pg, IfThreads<T>::n, 0, s>>>(A);                                          \
+            } else {                                                                                         \
+                k_liquid<T, false><<<(unsigned)nliq, FSL_BLOCK, 0, s>>>(A);                                  \
+                k_iface<T, false><<<pg, IfThreads<T>::n, 0, s>>>(A);                                         \
+            }                                                                                                \
         } else if (form == SC_SLAB) {                                                                        \
             if (A.ndom == 1) k_stream_slab<T, true><<<pg, FSL_BLOCK, 0, s>>>(A);                             \
             else k_stream_slab<T, false><<<pg, FSL_BLOCK, 0, s>>>(A);                                        \
@@ -2481,6 +2822,20 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
     template <> int stream_blocks_per_sm<T>(int form, bool one) {                                            \
         int nb = 0;                                                                                          \
         if (form == SC_SPLIT) nb = 1;                                                                        \
+        else if (form == SC_TILE2 || form == SC_TILE4) {                                                     \
+            /* the staging exceeds the default 48 KB: allow it, then ask */                                  \
+            const int sm = tile_smem_bytes<T>();                                                             \
+            cudaFuncSetAttribute(k_stream_tile<T, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
+            cudaFuncSetAttribute(k_stream_tile<T, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
+            cudaFuncSetAttribute(k_stream_tile<T, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
+            cudaFuncSetAttribute(k_stream_tile<T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
+            if (one) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, true, 2>, FSL_BLOCK, sm); \
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, false, 2>, FSL_BLOCK, sm); \
+        }                                                                                                    \
+        else if (form == SC_TWO && one)                                                                      \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iface<T, true>, IfThreads<T>::n, 0);        \
+        else if (form == SC_TWO)                                                                             \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iface<T, false>, IfThreads<T>::n, 0);       \
         else if (form == SC_SLAB && one)                                                                     \
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_slab<T, true>, FSL_BLOCK, 0);        \
         else if (form == SC_SLAB)                                                                            \
