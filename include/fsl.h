@@ -225,14 +225,17 @@ fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_p
  *      cells one per thread with every direction unrolled;
  *   6, 7  tile-fused: each block takes 2 or 4 tiles, streams and collides
  *      their liquid cells, then their interface cells one per thread (FP32
- *      and 16-bit storage only; FSL_ERR_ARG for FP64).
+ *      and 16-bit storage only; FSL_ERR_ARG for FP64);
+ *   8  the two kernels of form 5 side by side: the interface kernel on a
+ *      second stream of the handle with half its resident blocks per SM,
+ *      the liquid kernel beside it, joined before the conversion.
  * -1 restarts the tuning.  Waits for the handle's stream; the next fsl_step
  * rebuilds its graphs.  FSL_ERR_ARG for another value.  fsl_stream_form
  * returns the form in use (the one tried next while tuning). */
 fsl_status fsl_set_stream_form(fsl_domain* h, int32_t form);
 int32_t fsl_stream_form(const fsl_domain* h);
 
-/* Autotuner record of the handle: ms_per_form (array of 8, may be NULL) the
+/* Autotuner record of the handle: ms_per_form (array of 9, may be NULL) the
  * fastest stream-collide time measured per form (0 = not run); *form the
  * chosen form (-1 while tuning); *source 0 = not decided, 1 = measured on
  * this handle, 2 = from the process cache, 3 = set by the caller. */

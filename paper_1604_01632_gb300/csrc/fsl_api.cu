@@ -28,8 +28,8 @@ const int kDefaultCapacityMin = 256;
 // Candidate sequence of the autotuner: every form twice, the faster of its two
 // timed steps counts (the slab form only where the interface list is kept in
 // cell order; it is skipped otherwise).
-const int kTuneSeq[] = {SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB, SC_TWO, SC_TILE2, SC_TILE4,
-                        SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB, SC_TWO, SC_TILE2, SC_TILE4};
+const int kTuneSeq[] = {SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB, SC_TWO, SC_TILE2, SC_TILE4, SC_TWOC,
+                        SC_SPLIT, SC_PERS1, SC_PERS2, SC_PERS4, SC_SLAB, SC_TWO, SC_TILE2, SC_TILE4, SC_TWOC};
 const int kTuneSteps = (int)(sizeof(kTuneSeq) / sizeof(kTuneSeq[0]));
 
 // Process-wide cache of tuning decisions, keyed by the workload's shape:
@@ -56,6 +56,8 @@ struct fsl_domain {
     size_t fbytes = 8;            // bytes per stored PDF
     cudaStream_t user = nullptr;  // caller's stream (may be the legacy default)
     cudaStream_t ls = nullptr;    // library stream (capturable)
+    cudaStream_t ls2 = nullptr;   // second stream of the two-stream stream-collide form
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     int ifblocks = 304;           // grid of the list kernels (2 blocks per SM)
     int form = SC_SPLIT;          // stream-collide kernel form in use
@@ -299,11 +301,13 @@ void launch_k1(fsl_domain* h, const StepArgs& A, cudaStream_t st, cudaEvent_t el
                int form = -1) {
     if (form < 0) form = h->form;
     const int pg = h->pgrid[form];
+    cudaStream_t s2 = h->ls2;
+    cudaEvent_t fk = h->ev_fork, jn = h->ev_join;
     switch (h->precision) {
-    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
-    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
-    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
-    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei); break;
+    case FSL_P_FP64: launch_stream<double>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei, s2, fk, jn); break;
+    case FSL_P_FP32: launch_stream<float>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei, s2, fk, jn); break;
+    case FSL_P_F16S: launch_stream<__half>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei, s2, fk, jn); break;
+    default: launch_stream<__nv_bfloat16>(A, h->nblocks, h->ifblocks, form, pg, st, el, ei, s2, fk, jn); break;
     }
 }
 
@@ -316,13 +320,16 @@ int stream_occupancy(int precision, int form, bool one) {
     }
 }
 
-cudaError_t launch_conv(fsl_domain* h, const StepArgs& A, cudaStream_t st) {
+// form: the stream-collide form the conversion kernel follows (after the
+// two-stream form it depends on a join, not programmatically on one kernel)
+cudaError_t launch_conv(fsl_domain* h, const StepArgs& A, cudaStream_t st, int form = -1) {
     const CclArgs K = ccl_args(h, 0);
+    const bool pdl = (form < 0 ? h->form : form) != SC_TWOC;
     switch (h->precision) {
-    case FSL_P_FP64: return launch_convert<double>(A, K, h->convblocks, st);
-    case FSL_P_FP32: return launch_convert<float>(A, K, h->convblocks, st);
-    case FSL_P_F16S: return launch_convert<__half>(A, K, h->convblocks, st);
-    default: return launch_convert<__nv_bfloat16>(A, K, h->convblocks, st);
+    case FSL_P_FP64: return launch_convert<double>(A, K, h->convblocks, st, pdl);
+    case FSL_P_FP32: return launch_convert<float>(A, K, h->convblocks, st, pdl);
+    case FSL_P_F16S: return launch_convert<__half>(A, K, h->convblocks, st, pdl);
+    default: return launch_convert<__nv_bfloat16>(A, K, h->convblocks, st, pdl);
     }
 }
 
@@ -374,7 +381,7 @@ int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e
     if (e1) { record(e1); last_node(1); }
     launch_conv(h, A, h->ls);
     if (phases) cudaEventRecord(next_phase_event(h), h->ls);
-    return 2;
+    return (h->form == SC_TWO || h->form == SC_TWOC) ? 3 : 2;
 }
 
 std::pair<cudaEvent_t, cudaEvent_t> next_events(fsl_domain* h) {
@@ -578,7 +585,12 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         h->l2bytes = l2;
         for (int f = SC_PERS1; f < SC_FORMS; ++f)
             h->pgrid[f] = std::max(1, sms) * std::max(1, stream_occupancy(precision, f, n_domains == 1));
+        // beside the liquid kernel the interface kernel keeps half its blocks per SM
+        h->pgrid[SC_TWOC] = std::max(1, sms) * std::max(1, stream_occupancy(precision, SC_TWOC, n_domains == 1) / 2);
     }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ls2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
     const size_t N = (size_t)h->stride, NS = (size_t)h->nslots;
@@ -838,8 +850,8 @@ fsl_status tune_step(fsl_domain* h) {
     CK(h, cudaEventRecord(h->tev[0], h->ls));
     launch_k1(h, A, h->ls, nullptr, nullptr, f);
     CK(h, cudaEventRecord(h->tev[1], h->ls));
-    CK(h, launch_conv(h, A, h->ls));
-    h->launches += 2;
+    CK(h, launch_conv(h, A, h->ls, f));
+    h->launches += (f == SC_TWO || f == SC_TWOC) ? 3 : 2;
     h->cur = 1 - h->cur;
     CK(h, cudaEventSynchronize(h->tev[1]));
     float ms = 0.f;
@@ -1238,6 +1250,9 @@ fsl_status fsl_destroy(fsl_domain* h) {
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ls) cudaStreamDestroy(h->ls);
+    if (h->ls2) cudaStreamDestroy(h->ls2);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return FSL_OK;
 }

@@ -1694,10 +1694,11 @@ __global__ void __launch_bounds__(FSL_BLOCK, sizeof(T) == 8 ? 2 : FSL_STREAM_MIN
 // Stream-collide kernel forms (the autotuner picks one per workload): the split
 // form (interface blocks first, then one block per liquid tile), the
 // persistent form with 1, 2 or 4 tiles per liquid item, the slab form, the
-// two-kernel form (liquid kernel, then one thread per interface cell), and
-// the tile-fused form with 2 or 4 tiles per block.
+// two-kernel form (liquid kernel, then one thread per interface cell), the
+// tile-fused form with 2 or 4 tiles per block, and the two kernels run side by
+// side on two streams.
 enum { SC_SPLIT = 0, SC_PERS1 = 1, SC_PERS2 = 2, SC_PERS4 = 3, SC_SLAB = 4, SC_TWO = 5, SC_TILE2 = 6, SC_TILE4 = 7,
-       SC_FORMS = 8 };
+       SC_TWOC = 8, SC_FORMS = 9 };
 
 // First neighbour of cell z (direction order) that is an interface cell
 // carrying mark `want`, or -1.
@@ -2758,9 +2759,11 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_mass_partials(const T* f, const u
 
 // Launch helpers instantiated once per storage form.
 template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, int form, int pgrid,
-                                         cudaStream_t s, cudaEvent_t el, cudaEvent_t ei);
+                                         cudaStream_t s, cudaEvent_t el, cudaEvent_t ei, cudaStream_t s2,
+                                         cudaEvent_t efork, cudaEvent_t ejoin);
 template <typename T> int stream_blocks_per_sm(int form, bool one);
-template <typename T> cudaError_t launch_convert(const StepArgs& A, const CclArgs& K, int nblocks, cudaStream_t s);
+template <typename T> cudaError_t launch_convert(const StepArgs& A, const CclArgs& K, int nblocks, cudaStream_t s,
+                                                 bool pdl);
 template <typename T> int convert_blocks_per_sm();
 template <typename T> void launch_init_state(const StepArgs& A, int d, int n, const uint8_t* fl, const double* fill,
                                              const double* rho, const double* u, cudaStream_t s);
@@ -2771,7 +2774,8 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
 
 #define FSL_INSTANTIATE_FORM(T)                                                                              \
     template <> void launch_stream<T>(const StepArgs& A, long long nb, int ifb, int form, int pgrid,          \
-                                      cudaStream_t s, cudaEvent_t el, cudaEvent_t ei) {                      \
+                                      cudaStream_t s, cudaEvent_t el, cudaEvent_t ei, cudaStream_t s2,       \
+                                      cudaEvent_t efork, cudaEvent_t ejoin) {                                \
         /* split form: interface blocks first, then one block per liquid tile; */                          \
         /* persistent forms: pgrid resident blocks; el / ei (optional) both */                              \
         /* mark the kernel's end */                                                                          \
@@ -2795,6 +2799,17 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
                 if (tpb == 2) k_stream_tile<T, false, 2><<<nsup, FSL_BLOCK, sm, s>>>(A);                     \
                 else k_stream_tile<T, false, 4><<<nsup, FSL_BLOCK, sm, s>>>(A);                              \
             }                                                                                                \
+        } else if (form == SC_TWOC) {                                                                        \
+            /* the interface kernel on a second stream, beside the liquid kernel */                          \
+            const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                     \
+            cudaEventRecord(efork, s);                                                                       \
+            cudaStreamWaitEvent(s2, efork, 0);                                                               \
+            if (A.ndom == 1) k_iface<T, true><<<pg, IfThreads<T>::n, 0, s2>>>(A);                            \
+            else k_iface<T, false><<<pg, IfThreads<T>::n, 0, s2>>>(A);                                       \
+            cudaEventRecord(ejoin, s2);                                                                      \
+            if (A.ndom == 1) k_liquid<T, true><<<(unsigned)nliq, FSL_BLOCK, 0, s>>>(A);                      \
+            else k_liquid<T, false><<<(unsigned)nliq, FSL_BLOCK, 0, s>>>(A);                                 \
+            cudaStreamWaitEvent(s, ejoin, 0);                                                                \
         } else if (form == SC_TWO) {                                                                         \
             const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                     \
             if (A.ndom == 1) {                                                                               \
@@ -2832,6 +2847,10 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
             if (one) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, true, 2>, FSL_BLOCK, sm); \
             else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, false, 2>, FSL_BLOCK, sm); \
         }                                                                                                    \
+        else if (form == SC_TWOC && one)                                                                     \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iface<T, true>, IfThreads<T>::n, 0);        \
+        else if (form == SC_TWOC)                                                                            \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iface<T, false>, IfThreads<T>::n, 0);       \
         else if (form == SC_TWO && one)                                                                      \
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iface<T, true>, IfThreads<T>::n, 0);        \
         else if (form == SC_TWO)                                                                             \
@@ -2854,7 +2873,8 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_pers<T, false, 4>, FSL_BLOCK, 0);    \
         return nb;                                                                                           \
     }                                                                                                        \
-    template <> cudaError_t launch_convert<T>(const StepArgs& A, const CclArgs& K, int nb, cudaStream_t s) {\
+    template <> cudaError_t launch_convert<T>(const StepArgs& A, const CclArgs& K, int nb, cudaStream_t s,  \
+                                              bool pdl) {                                                    \
         cudaLaunchConfig_t cfg = {};                                                                         \
         cfg.gridDim = dim3((unsigned)nb);                                                                    \
         cfg.blockDim = dim3(FSL_CONV_THREADS);                                                               \
@@ -2865,7 +2885,7 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
         at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;                                       \
         at[1].val.programmaticStreamSerializationAllowed = 1;                                                \
         cfg.attrs = at;                                                                                      \
-        cfg.numAttrs = 2;                                                                                    \
+        cfg.numAttrs = pdl ? 2 : 1;   /* after a join of two streams: a plain dependency */               \
         return cudaLaunchKernelEx(&cfg, k_convert<T>, A, K);                                                 \
     }                                                                                                        \
     template <> int convert_blocks_per_sm<T>() {                                                             \

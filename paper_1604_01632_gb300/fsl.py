@@ -338,16 +338,16 @@ class Simulation:
         """Stream-collide kernel form: 0 split, 1/2/3 persistent with 1/2/4 tiles per liquid
         item, 4 slab (interface list in cell order only), 5 two kernels (liquid, then one
         thread per interface cell), 6/7 tile-fused with 2/4 tiles per block (not FP64),
-        -1 autotune again."""
+        8 the two kernels side by side on two streams, -1 autotune again."""
         self._check(self.L.fsl_set_stream_form(self._h, int(form)))
 
     def tuning(self) -> dict:
         """Autotuner record: per-form stream-collide ms, chosen form, source."""
-        ms = (ctypes.c_double * 8)()
+        ms = (ctypes.c_double * 9)()
         form, src = ctypes.c_int32(0), ctypes.c_int32(0)
         self._check(self.L.fsl_tuning(self._h, ms, ctypes.byref(form), ctypes.byref(src)))
         names = ("split", "persistent_1tile", "persistent_2tiles", "persistent_4tiles", "slab", "two_kernel",
-                 "tile_fused_2", "tile_fused_4")
+                 "tile_fused_2", "tile_fused_4", "two_kernel_concurrent")
         return {"ms_per_form": dict(zip(names, [round(v, 5) for v in ms])),
                 "form": int(form.value), "form_name": names[form.value] if form.value >= 0 else None,
                 "source": ("none", "measured", "cache", "caller")[src.value]}

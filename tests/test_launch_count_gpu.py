@@ -1,6 +1,7 @@
 """The library's launch count (the bench reports it as the kernels of the
-timed steps): exactly two kernels per step, the stream-collide kernel and the
-cooperative conversion kernel, with and without CUDA graphs."""
+timed steps): per step the stream-collide kernel (two kernels in the
+two-kernel forms: liquid cells, then interface cells) and the cooperative
+conversion kernel, with and without CUDA graphs, in every stream-collide form."""
 import pytest
 
 from paper_1604_01632_gb300 import scenarios as S
@@ -18,14 +19,19 @@ def fsl():
     return F
 
 
+@pytest.mark.parametrize("form", list(range(9)))
 @pytest.mark.parametrize("graphs", [True, False])
-def test_two_kernels_per_step(fsl, graphs):
+def test_kernels_per_step(fsl, graphs, form):
     sim = fsl.Simulation.from_scenarios([S.static_bubble(n=16, radius=4.0)], precision="f16s")
     sim.set_graphs(graphs)
+    if form == 4:
+        sim.set_interface_order(1)
+    sim.set_stream_form(form)
     sim.step(1)   # the first step also runs the initial labelling and list
     sim.sync()
     l0 = sim.launches
     sim.step(5)
     sim.sync()
-    assert sim.launches - l0 == 10
+    per_step = 3 if form in (5, 8) else 2
+    assert sim.launches - l0 == 5 * per_step
     sim.close()

@@ -317,11 +317,12 @@ def test_total_mass_against_oracle(fsl, oracle_mod, precision, rtol):
     sim.close()
 
 
-@pytest.mark.parametrize("form", [1, 2, 3, 5])
+@pytest.mark.parametrize("form", [1, 2, 3, 5, 8])
 def test_persistent_stream_forms_bitexact(fsl, oracle_mod, form):
     """The persistent stream-collide forms (1, 2 or 4 tiles per liquid item,
-    interface chunks interleaved) and the two-kernel form (liquid kernel, then
-    one thread per interface cell) give the oracle's state bit for bit: a batch
+    interface chunks interleaved) and the two-kernel forms (liquid kernel and
+    one thread per interface cell, one after the other or side by side on two
+    streams) give the oracle's state bit for bit: a batch
     of moving-bubble domains with conversions, merges and splits, and a single
     domain with a moving lid and gravity."""
     scs = [S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=s)
