@@ -202,7 +202,7 @@ class L2Flush:
         return "flushed (256 MB write)"
 
 
-def tune(sim, limit: int = 16) -> dict:
+def tune(sim, limit: int = 64) -> dict:
     """Run the autotuning steps (real steps) until the stream-collide form is
     decided; returns the tuner's record and the number of steps it took."""
     k = 0
@@ -231,6 +231,8 @@ def run_gpu(args, rank: int, world: int):
         sim = fsl.Simulation.from_scenarios([scen or sc], precision=precision, stream=int(stream.cuda_stream))
         if args.no_graphs:
             sim.set_graphs(False)
+        if args.stream_form >= 0:
+            sim.set_stream_form(args.stream_form)
         return sim
 
     flush = L2Flush(torch, args.flush)
@@ -538,6 +540,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="direct kernel launches (for ncu)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--stream-form", type=int, default=-1,
+                    help="fix the stream-collide form (0-8) instead of tuning it (for ncu)")
     ap.add_argument("--flush", default="write+read", choices=["write", "write+read"],
                     help="L2 flush between timed steps")
     args = ap.parse_args()

@@ -562,3 +562,51 @@ def foam(n: int = 512, gas_fraction: float = 0.4, seed: int = 0, lid_speed: floa
                  lid=(lid_speed, 0.0, 0.0), steps=steps)
     sc.bubbles_placed = int(len(radii))
     return sc
+
+
+# the thread-rupture case of the paper (Sec. 3.1): its physical quantities
+RUPTURE_DX = 1.25e-5       # m, lattice spacing
+RUPTURE_NU = 1e-6          # m^2/s, kinematic viscosity of the liquid
+RUPTURE_RHO = 1000.0       # kg/m^3, liquid density
+RUPTURE_SIGMAS = (0.072, 0.018)   # N/m, the two surface tensions
+RUPTURE_FRAMES_MS = {0.072: (22, 38, 46, 68, 324), 0.018: (22, 65, 76, 90, 324)}
+RUPTURE_PIECES = {0.072: 5, 0.018: 6}
+
+
+def rupture_units(sigma_si: float, dt: float = 5e-7, tau: Optional[float] = 0.8, nu_si: float = RUPTURE_NU,
+                  dx: float = RUPTURE_DX, rho_si: float = RUPTURE_RHO) -> dict:
+    """Lattice parameters of the thread-rupture case for an assumed time step
+    dt (the paper gives dx, nu, rho and sigma but no time step):
+    sigma_lb = sigma dt^2 / (rho dx^3).  With tau=None the viscosity is the
+    paper's, tau = 3 nu dt / dx^2 + 1/2 (0.5096 at dt = 5e-7 s); otherwise tau
+    is taken as given and the viscosity it implies, nu = (tau - 1/2) dx^2 /
+    (3 dt), is reported."""
+    if tau is None:
+        nu_lb = nu_si * dt / dx ** 2
+        tau = 3.0 * nu_lb + 0.5
+    nu_lb = (tau - 0.5) / 3.0
+    return {"dt": dt, "tau": tau, "nu_lb": nu_lb, "nu_si": nu_lb * dx ** 2 / dt,
+            "sigma_lb": sigma_si * dt ** 2 / (rho_si * dx ** 3)}
+
+
+def thread_rupture(sigma_si: float = 0.072, dt: float = 5e-7, tau: Optional[float] = 0.8, nx: int = 360,
+                   ny: int = 40, nz: int = 40, gas=(336, 8, 8), collision: int = TRT) -> Scenario:
+    """Rupture of a thin gas thread (paper Sec. 3.1): a 360 x 40 x 40 domain of
+    liquid at rest holding a centred rectangular gas block of 336 x 8 x 8 cells.
+    No-slip walls close all six faces (a one-cell obstacle shell inside the
+    box); no gravity.  The block's faces lie on cell faces, so fill levels are
+    0 or 1 and the closed interface layer is the liquid cells touching gas.
+    tau and sigma in lattice units follow from the paper's dx, rho, sigma and
+    the assumed dt (rupture_units)."""
+    p = rupture_units(sigma_si, dt, tau)
+    shape = (nz, ny, nx)
+    gx, gy, gz = gas
+    x0, y0, z0 = (nx - gx) // 2, (ny - gy) // 2, (nz - gz) // 2
+    fill = np.ones(shape)
+    fill[z0:z0 + gz, y0:y0 + gy, x0:x0 + gx] = 0.0
+    obs = _wall_shell(shape, axes=(0, 1, 2))
+    flags = classify(fill, obstacle=obs)
+    sc = _finish(f"thread_rupture_{nx}x{ny}x{nz}_sigma{sigma_si:g}", flags, fill, collision=collision,
+                 tau=p["tau"], sigma=p["sigma_lb"], steps=int(round(324e-3 / dt)))
+    sc.units = p
+    return sc

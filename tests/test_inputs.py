@@ -95,3 +95,25 @@ def test_generators_are_deterministic_in_the_seed():
     c = S.random_bubbles(24, 20, 16, n_bubbles=6, r_min=2.5, r_max=4.5, u_max=0.06, sigma=5e-3, seed=4)
     assert np.array_equal(a.flags, b.flags) and np.array_equal(a.fill, b.fill) and np.array_equal(a.u, b.u)
     assert not np.array_equal(a.flags, c.flags)
+
+
+def test_thread_rupture_recipe():
+    """Paper Sec. 3.1: 360 x 40 x 40 with a centred 336 x 8 x 8 gas block, walls on
+    all faces; the lattice units follow from dx, rho, sigma and the assumed dt."""
+    sc = S.thread_rupture(0.072)
+    assert (sc.nx, sc.ny, sc.nz) == (360, 40, 40)
+    f = sc.flags
+    assert (f == S.GAS).sum() == 336 * 8 * 8
+    gas = np.argwhere(f == S.GAS)
+    assert gas.min(0).tolist() == [16, 16, 12] and gas.max(0).tolist() == [23, 23, 347]
+    for ax in range(3):
+        assert (np.take(f, 0, axis=ax) == S.OBSTACLE).all() and (np.take(f, -1, axis=ax) == S.OBSTACLE).all()
+    assert _liquid_touches_gas(f) == 0
+    assert (sc.fill[f == S.INTERFACE] == 1.0).all()
+    # sigma dt^2 / (rho dx^3) and tau = 3 nu dt / dx^2 + 1/2 by hand for dt = 5e-7 s
+    u = S.rupture_units(0.072, tau=None)
+    assert u["sigma_lb"] == pytest.approx(0.072 * 2.5e-13 / (1000.0 * 1.953125e-15), rel=1e-12)
+    assert u["tau"] == pytest.approx(0.5 + 3.0 * 1e-6 * 5e-7 / 1.5625e-10, rel=1e-12)
+    assert sc.tau == 0.8 and sc.units["nu_si"] == pytest.approx(0.1 * 1.5625e-10 / 5e-7, rel=1e-12)
+    assert S.thread_rupture(0.018).sigma == pytest.approx(sc.sigma / 4.0, rel=1e-12)
+    assert sc.steps == 648000
