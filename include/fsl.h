@@ -229,6 +229,11 @@ fsl_status fsl_set_limits(fsl_domain* h, int64_t ccl_max_iter, int64_t barrier_p
  *   8  the two kernels of form 5 side by side: the interface kernel on a
  *      second stream of the handle with half its resident blocks per SM,
  *      the liquid kernel beside it, joined before the conversion.
+ * Forms 5-8 first run a normals pass (one kernel over the lattice) that
+ * stores the unit normal of every interface cell and face neighbour of one
+ * and each interface cell's reconstruction directions; their interface cells
+ * read the curvature's normals from it.  Kernels per step: 4 in forms 5 and
+ * 8, 3 in forms 6 and 7, 2 otherwise (the conversion kernel included).
  * -1 restarts the tuning.  Waits for the handle's stream; the next fsl_step
  * rebuilds its graphs.  FSL_ERR_ARG for another value.  fsl_stream_form
  * returns the form in use (the one tried next while tuning). */

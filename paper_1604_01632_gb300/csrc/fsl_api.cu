@@ -91,6 +91,8 @@ struct fsl_domain {
     uint8_t *flag = nullptr, *mark = nullptr;
     double *m = nullptr, *phi = nullptr, *phit = nullptr, *rhoi = nullptr, *exs = nullptr;
     float *phif = nullptr, *phitf = nullptr;   // FP32 copies (FP32-collide forms only)
+    void* nrm = nullptr;           // normals pass: 3 planes of the arithmetic type
+    unsigned* nmask = nullptr;     // normals pass: reconstruction directions per interface cell
     int* id = nullptr;
     long long *vfx = nullptr, *vxfx = nullptr, *vsfx = nullptr, *ncells = nullptr;
     int* constp = nullptr;
@@ -202,6 +204,15 @@ cudaError_t staging(fsl_domain* h, const size_t* bytes, int n, void** parts) {
 // default where the two PDF arrays of a step exceed twice the L2 cache (there
 // an interface cell's neighbour data would otherwise come from DRAM again for
 // every cell that reads it; the rebuild reads the cell types twice).
+// Kernels one step launches with stream-collide form f: the conversion kernel,
+// plus the normals pass in the forms that take interface cells one per thread,
+// plus one or two stream-collide kernels.
+int kernels_per_step(int f) {
+    if (f == SC_TWO || f == SC_TWOC) return 4;
+    if (f == SC_TILE2 || f == SC_TILE4) return 3;
+    return 2;
+}
+
 int order_effective(const fsl_domain* h) {
     if (h->order_mode >= 0) return h->order_mode;
     const double pdf_bytes = 2.0 * 19.0 * (double)h->stride * (double)h->fbytes;
@@ -222,6 +233,8 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.phit = h->phit;
     A.phif = h->phif;
     A.phitf = h->phitf;
+    A.nrm = h->nrm;
+    A.nmask = h->nmask;
     A.rhoi = h->rhoi;
     A.exs = h->exs;
     A.id = h->id;
@@ -381,7 +394,7 @@ int enqueue_main(fsl_domain* h, const StepArgs& A, cudaEvent_t e0, cudaEvent_t e
     if (e1) { record(e1); last_node(1); }
     launch_conv(h, A, h->ls);
     if (phases) cudaEventRecord(next_phase_event(h), h->ls);
-    return (h->form == SC_TWO || h->form == SC_TWOC) ? 3 : 2;
+    return kernels_per_step(h->form);
 }
 
 std::pair<cudaEvent_t, cudaEvent_t> next_events(fsl_domain* h) {
@@ -609,6 +622,8 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
         AL(h->phif, 4 * N);
         AL(h->phitf, 4 * N);
     }
+    AL(h->nrm, 3 * N * (precision == FSL_P_FP64 ? 8 : 4));
+    AL(h->nmask, 4 * N);
     AL(h->rhoi, 8 * N);
     AL(h->exs, 8 * N);
     AL(h->id, 4 * N);
@@ -685,6 +700,8 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->phit, 0, 8 * N);
     if (e == cudaSuccess && h->phif) e = cudaMemset(h->phif, 0, 4 * N);
     if (e == cudaSuccess && h->phitf) e = cudaMemset(h->phitf, 0, 4 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->nrm, 0, 3 * N * (precision == FSL_P_FP64 ? 8 : 4));
+    if (e == cudaSuccess) e = cudaMemset(h->nmask, 0, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->rhoi, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->exs, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->f[0], 0, 19 * N * h->fbytes);
@@ -851,7 +868,7 @@ fsl_status tune_step(fsl_domain* h) {
     launch_k1(h, A, h->ls, nullptr, nullptr, f);
     CK(h, cudaEventRecord(h->tev[1], h->ls));
     CK(h, launch_conv(h, A, h->ls, f));
-    h->launches += (f == SC_TWO || f == SC_TWOC) ? 3 : 2;
+    h->launches += kernels_per_step(f);
     h->cur = 1 - h->cur;
     CK(h, cudaEventSynchronize(h->tev[1]));
     float ms = 0.f;

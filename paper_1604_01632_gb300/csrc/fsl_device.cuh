@@ -151,6 +151,10 @@ struct StepArgs {
     int spins;                  // polls a block waits at a grid barrier before it gives up
     int bar_extra;              // arrivals a barrier waits for beyond the grid (0; 1 only to
                                 // test the timeout path: no block is then the last)
+    void* nrm;                  // normals pass: unit normals of the cells that need one,
+                                // three planes of the arithmetic type (x, y, z), stride apart
+    unsigned* nmask;            // normals pass: per interface cell, bit a set when the
+                                // reconstruction's normal test holds for direction a
     Dom d0;                     // domain 0, read from the parameter space when ndom == 1
 };
 
@@ -292,6 +296,13 @@ template <> struct Form<__half> {
     __device__ static inline void st_dev2(__half* p, float2 v) { *(__half2*)p = __floats2half2_rn(v.x, v.y); }
     __device__ static inline float2 ld_dev2(const __half* p) { return __half22float2(*(const __half2*)p); }
     __device__ static inline void st_dev(__half* p, float v) { *p = __float2half_rn(v); }
+    // the pair rounded once; stored whole, or only its low / high half
+    __device__ static inline void st_dev2m(__half* p, float2 v, bool both, bool lo, bool hi) {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        if (both) *(__half2*)p = h;
+        if (lo) p[0] = __low2half(h);
+        if (hi) p[1] = __high2half(h);
+    }
     __device__ static inline float ld(const __half* p, int a) { return weightc<float>(a) + __half2float(*p); }
     __device__ static inline void st(__half* p, int a, float v) { *p = __float2half_rn(v - weightc<float>(a)); }
 };
@@ -302,6 +313,12 @@ template <> struct Form<__nv_bfloat16> {
     __device__ static inline void st_dev2(__nv_bfloat16* p, float2 v) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(v.x, v.y); }
     __device__ static inline float2 ld_dev2(const __nv_bfloat16* p) { return __bfloat1622float2(*(const __nv_bfloat162*)p); }
     __device__ static inline void st_dev(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static inline void st_dev2m(__nv_bfloat16* p, float2 v, bool both, bool lo, bool hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        if (both) *(__nv_bfloat162*)p = h;
+        if (lo) p[0] = __low2bfloat16(h);
+        if (hi) p[1] = __high2bfloat16(h);
+    }
     __device__ static inline float ld(const __nv_bfloat16* p, int a) {
         return weightc<float>(a) + __bfloat162float(*p);
     }
@@ -759,37 +776,47 @@ __device__ __forceinline__ void liquid_pairs(const StepArgs& A, long long bid) {
     if (!v0 && !v1) return;
     const Dom& D = dom_at<ONE>(A, g0);
     const Par<float> R = par_of<float>(D);
-    const Pull P0 = make_pull(D, g0), P1 = make_pull(D, g0 + 1);
     const unsigned S = (unsigned)A.stride, gi = (unsigned)g0;
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
     float2 d[19];
     if (!((f0 | f1) & K_WALL) && !(D.nx & 1)) {
-        // even nx: the two cells share their row, so for the links along
-        // x = const the two sources are neighbours at an even offset: one
-        // aligned 32-bit load
+        // even nx: x0 is even and both cells lie in one row, so the y / z
+        // offsets of a link are common to the pair and only its x offsets
+        // differ: cell 0 pulls x - 1 from the row's end when x0 = 0, cell 1
+        // pulls x + 1 from the row's start when x0 + 1 = nx - 1.  Links along
+        // x = const read both sources with one aligned 32-bit load.
+        int x, y, z;
+        local_xyz(D, (int)(g0 - D.off), x, y, z);
+        const int sy = D.nx, sz = D.nx * D.ny;
+        const int oy[3] = {y == 0 ? (D.ny - 1) * sy : -sy, 0, y == D.ny - 1 ? -(D.ny - 1) * sy : sy};
+        const int oz[3] = {z == 0 ? (D.nz - 1) * sz : -sz, 0, z == D.nz - 1 ? -(D.nz - 1) * sz : sz};
+        const int xm0 = x == 0 ? D.nx - 1 : -1;                 // cell 0, source x - 1
+        const int xp1 = x + 2 == D.nx ? 2 - D.nx : 2;           // cell 1, source x + 1 (from cell 0)
 #pragma unroll
         for (int a = 0; a < 19; ++a) {
-            const unsigned y0 = gi + (unsigned)(P0.ox[1 - cx(a)] + P0.oy[1 - cy(a)] + P0.oz[1 - cz(a)]);
+            const unsigned r = gi + (unsigned)(oy[1 - cy(a)] + oz[1 - cz(a)]);
             if (cx(a) == 0) {
-                d[a] = Form<T>::ld_dev2(src + (a * S + y0));
-            } else {
-                const unsigned y1 = gi + 1u + (unsigned)(P1.ox[1 - cx(a)] + P1.oy[1 - cy(a)] + P1.oz[1 - cz(a)]);
-                d[a] = make_float2(Form<T>::ld_dev(src + (a * S + y0)), Form<T>::ld_dev(src + (a * S + y1)));
+                d[a] = Form<T>::ld_dev2(src + (a * S + r));
+            } else if (cx(a) > 0) {   // sources x - 1: cell 0's per x0, cell 1's is cell 0's column
+                d[a] = make_float2(Form<T>::ld_dev(src + (a * S + r + (unsigned)xm0)), Form<T>::ld_dev(src + (a * S + r)));
+            } else {                  // sources x + 1: cell 0's is cell 1's column
+                d[a] = make_float2(Form<T>::ld_dev(src + (a * S + r + 1u)), Form<T>::ld_dev(src + (a * S + r + (unsigned)xp1)));
             }
         }
     } else {
+        const Pull P0 = make_pull(D, g0), P1 = make_pull(D, g0 + 1);
         // walls, or odd nx (the pair may straddle two rows): every link of
         // each cell on its own, a wall cell's bounced links chosen without a
         // branch
-        const bool w0 = v0 && (f0 & K_WALL), w1 = v1 && (f1 & K_WALL);
+        const bool k0 = v0 && (f0 & K_WALL), k1 = v1 && (f1 & K_WALL);
         d[0] = make_float2(Form<T>::ld_dev(src + gi), Form<T>::ld_dev(src + gi + 1u));
 #pragma unroll
         for (int a = 1; a < 19; ++a) {
             const unsigned y0 = gi + (unsigned)(P0.ox[1 - cx(a)] + P0.oy[1 - cy(a)] + P0.oz[1 - cz(a)]);
             const unsigned y1 = gi + 1u + (unsigned)(P1.ox[1 - cx(a)] + P1.oy[1 - cy(a)] + P1.oz[1 - cz(a)]);
-            const uint8_t t0 = w0 ? ctype(A.flag[y0]) : (uint8_t)LIQ;
-            const uint8_t t1 = w1 ? ctype(A.flag[y1]) : (uint8_t)LIQ;
+            const uint8_t t0 = k0 ? ctype(A.flag[y0]) : (uint8_t)LIQ;
+            const uint8_t t1 = k1 ? ctype(A.flag[y1]) : (uint8_t)LIQ;
             // bounce-back reads the cell's own opposite PDF (w_a = w_abar)
             float x0 = Form<T>::ld_dev(src + ((t0 == OBS || t0 == LID) ? opp(a) * S + gi : a * S + y0));
             float x1 = Form<T>::ld_dev(src + ((t1 == OBS || t1 == LID) ? opp(a) * S + gi + 1u : a * S + y1));
@@ -800,12 +827,13 @@ __device__ __forceinline__ void liquid_pairs(const StepArgs& A, long long bid) {
         }
     }
     // each output is stored as soon as it is formed: one 32-bit store per
-    // direction when both cells are liquid, else the liquid lane's 16 bits
+    // direction when both cells are liquid, else the liquid lane's 16 bits of
+    // the same rounded pair (a rounded pair's halves are the values rounded
+    // one by one), as predicated stores rather than divergent paths
+    const bool both = v0 && v1;
     auto out = [&](int a, float2 v) {
         if (a == 0 && ((v0 && !(v.x == v.x)) || (v1 && !(v.y == v.y)))) set_status(A.status, ST_NAN);
-        if (v0 && v1) Form<T>::st_dev2(dst + (a * S + gi), v);
-        else if (v0) Form<T>::st_dev(dst + (a * S + gi), v.x);
-        else Form<T>::st_dev(dst + (a * S + gi + 1u), v.y);
+        Form<T>::st_dev2m(dst + (a * S + gi), v, both, v0 && !v1, v1 && !v0);
     };
     if (D.has_force)
         collide_dev2<true>(d, out, R.omp, R.omm, R.g[0], R.g[1], R.g[2]);
@@ -1275,54 +1303,208 @@ __device__ __forceinline__ void interface_cells(const StepArgs& A, int bid, int 
 }
 
 // ------------------------------------------- interface cells, one per thread
-// The 81 fill levels the curvature needs (Eq. 15 through the divergence of the
-// Parker-Youngs normals at the six face neighbours): every offset within +-1
-// on all axes (27), and those with one axis at +-2 and the other two within
-// +-1 (54).  Compact index of such an offset:
-__host__ __device__ constexpr int st81(int dx, int dy, int dz) {
-    return (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
-               ? (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)
-           : (dx == 2 || dx == -2) ? 27 + (dx > 0 ? 9 : 0) + (dy + 1) + 3 * (dz + 1)
-           : (dy == 2 || dy == -2) ? 45 + (dy > 0 ? 9 : 0) + (dx + 1) + 3 * (dz + 1)
-                                   : 63 + (dz > 0 ? 9 : 0) + (dx + 1) + 3 * (dy + 1);
-}
-__host__ __device__ constexpr bool in81(int dx, int dy, int dz) {
-    return ((dx == 2 || dx == -2) ? 1 : 0) + ((dy == 2 || dy == -2) ? 1 : 0) + ((dz == 2 || dz == -2) ? 1 : 0) <= 1;
-}
-
-// Threads (cells) per block of the one-thread-per-cell interface kernel; the
-// block's stencil staging is 81 values per thread in shared memory.
+// Threads (cells) per block of the one-thread-per-cell interface kernel.
 template <typename T> struct IfThreads {
     static constexpr int n = sizeof(typename Form<T>::C) == 8 ? 64 : 128;
 };
 
-// Parker-Youngs gradient at offset (ox, oy, oz) of the staged stencil, the
-// weighted central differences summed in the order of the two-level loop the
-// other interface path (and the oracle) use.
-template <typename C, int IB, int ox, int oy, int oz>
-__device__ __forceinline__ void pyg(const C* stc, int t, C& gx, C& gy, C& gz) {
+// ------------------------------------------------------------ normals pass
+// The Parker-Youngs gradient at a cell from its 27 stencil values v(dx, dy, dz),
+// summed in the order of pyg (and of the oracle's two-level loop).
+template <typename C, class V>
+__device__ __forceinline__ void pyg_of(V&& v, C& gx, C& gy, C& gz) {
     gx = (C)0; gy = (C)0; gz = (C)0;
 #pragma unroll
     for (int b = -1; b <= 1; ++b) {
 #pragma unroll
         for (int a = -1; a <= 1; ++a) {
             const C W = (a == 0 && b == 0) ? (C)4 : ((a == 0 || b == 0) ? (C)2 : (C)1);
-            gx = gx + W * (stc[st81(ox + 1, oy + a, oz + b) * IB + t] - stc[st81(ox - 1, oy + a, oz + b) * IB + t]);
-            gy = gy + W * (stc[st81(ox + a, oy + 1, oz + b) * IB + t] - stc[st81(ox + a, oy - 1, oz + b) * IB + t]);
-            gz = gz + W * (stc[st81(ox + a, oy + b, oz + 1) * IB + t] - stc[st81(ox + a, oy + b, oz - 1) * IB + t]);
+            gx = gx + W * (v(1, a, b) - v(-1, a, b));
+            gy = gy + W * (v(a, 1, b) - v(a, -1, b));
+            gz = gz + W * (v(a, b, 1) - v(a, b, -1));
         }
     }
 }
-// Unit normal -g/|g| at a face neighbour (0 where g = 0).
-template <typename C, int IB, int ox, int oy, int oz>
-__device__ __forceinline__ void pyn(const C* stc, int t, C& nx, C& ny, C& nz) {
-    pyg<C, IB, ox, oy, oz>(stc, t, nx, ny, nz);
+
+// Stores of the normals pass for a cell g that needs a normal: the normal-test
+// bits of an interface cell, and the unit normal -grad/|grad| (0 where the
+// gradient is 0), with the arithmetic of the interface kernels.
+template <typename C>
+__device__ __forceinline__ void normal_out(const StepArgs& A, unsigned g, bool ifc, C gx, C gy, C gz) {
+    if (ifc) {
+        unsigned mk = 0;
+#pragma unroll
+        for (int a = 1; a < 19; ++a)
+            mk |= (unsigned)(((C)cx(a) * gx + (C)cy(a) * gy) + (C)cz(a) * gz > (C)0) << a;
+        A.nmask[g] = mk;
+    }
+    C nx = gx, ny = gy, nz = gz;
     const C qq = nx * nx + ny * ny + nz * nz;
     if (qq > (C)0) {
         const C len = sqrt(qq);
         nx = -(nx / len); ny = -(ny / len); nz = -(nz / len);
     } else {
         nx = (C)0; ny = (C)0; nz = (C)0;
+    }
+    C* __restrict__ nr = (C*)A.nrm;
+    const unsigned S = (unsigned)A.stride;
+    nr[g] = nx;
+    nr[S + g] = ny;
+    nr[2u * S + g] = nz;
+}
+
+// Normals pass, one thread per cell of the padded lattice, ahead of the
+// stream-collide kernels that take the interface cells one per thread.  The
+// curvature of an interface cell x (Eq. 15) is half the divergence of the unit
+// normals -grad(phi)/|grad(phi)| at its six face neighbours, and the
+// reconstruction's normal test (Eq. 11) uses the gradient at x itself.  Each
+// normal is computed here once, for every cell that is an interface cell or a
+// face neighbour of one (walls included: the stencil reads walls as full), and
+// stored in nrm; each interface cell also stores its 18 normal-test bits in
+// nmask.  The stencil values are the stored copy phit (walls and liquid 1, gas
+// 0, interface clamp(phi, 0, 1)) and the arithmetic is that of the interface
+// kernels, so their curvature and reconstruction come out as if they had
+// computed the normals themselves.
+//
+// A warp whose 32 cells lie in one row of one domain (the usual case: rows
+// start on multiples of 32 when nx is one) works on the row segment: the y / z
+// offsets are common to the warp, each lane loads the 9 (dy, dz) rows at its
+// own x and takes x - 1 and x + 1 from its neighbour lanes (the segment's end
+// lanes load them, wrapping within the row), and the warp returns at once when
+// no cell of the segment needs a normal.  Other warps take one cell per
+// thread with the general stencil addressing.
+template <typename T, bool ONE>
+__global__ void __launch_bounds__(FSL_BLOCK) k_normals(StepArgs A) {
+    using C = typename Form<T>::C;
+    const long long g = (long long)blockIdx.x * FSL_BLOCK + threadIdx.x;   // stride: a multiple of the block
+    const Dom& D = dom_at<ONE>(A, g);
+    const C* __restrict__ ph;
+    if constexpr (sizeof(C) == 8) ph = A.phit;
+    else ph = A.phitf;
+    const unsigned lane = threadIdx.x & 31u;
+    const long long l0 = g - lane - D.off;   // the warp's first cell in its domain
+    int x0, y, z;
+    local_xyz(D, (int)(l0 < D.n ? l0 : 0), x0, y, z);
+    if (l0 + 31 < D.n && x0 + 31 < D.nx) {
+        const unsigned gi = (unsigned)g;
+        const int sy = D.nx, sz = D.nx * D.ny;
+        const int oy[3] = {y == 0 ? (D.ny - 1) * sy : -sy, 0, y == D.ny - 1 ? -(D.ny - 1) * sy : sy};
+        const int oz[3] = {z == 0 ? (D.nz - 1) * sz : -sz, 0, z == D.nz - 1 ? -(D.nz - 1) * sz : sz};
+        const int oxm = x0 == 0 ? D.nx - 1 : -1;          // lane 0: x - 1
+        const int oxp = x0 + 32 == D.nx ? 1 - D.nx : 1;    // lane 31: x + 1
+        const unsigned t = ctype(A.flag[gi]);
+        const unsigned ty0 = ctype(A.flag[gi + oy[0]]), ty2 = ctype(A.flag[gi + oy[2]]);
+        const unsigned tz0 = ctype(A.flag[gi + oz[0]]), tz2 = ctype(A.flag[gi + oz[2]]);
+        const unsigned tl0 = lane == 0 ? ctype(A.flag[gi + oxm]) : 0u, tr0 = lane == 31 ? ctype(A.flag[gi + oxp]) : 0u;
+        unsigned tl = __shfl_up_sync(0xffffffffu, t, 1), tr = __shfl_down_sync(0xffffffffu, t, 1);
+        if (lane == 0) tl = tl0;
+        if (lane == 31) tr = tr0;
+        const bool need = (t == IFC) | (tl == IFC) | (tr == IFC) | (ty0 == IFC) | (ty2 == IFC) | (tz0 == IFC) |
+                          (tz2 == IFC);
+        if (!__any_sync(0xffffffffu, need)) return;
+        C v[3][3][3];   // [dz + 1][dy + 1][dx + 1]
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const unsigned r = gi + (unsigned)(oy[dy + 1] + oz[dz + 1]);
+                const C c = ph[r];
+                const C e = lane == 0 ? ph[r + oxm] : (lane == 31 ? ph[r + oxp] : c);
+                C l = __shfl_up_sync(0xffffffffu, c, 1), rr = __shfl_down_sync(0xffffffffu, c, 1);
+                if (lane == 0) l = e;
+                if (lane == 31) rr = e;
+                v[dz + 1][dy + 1][0] = l;
+                v[dz + 1][dy + 1][1] = c;
+                v[dz + 1][dy + 1][2] = rr;
+            }
+        if (!need) return;
+        C gx, gy, gz;
+        pyg_of<C>([&](int dx, int dy, int dz) { return v[dz + 1][dy + 1][dx + 1]; }, gx, gy, gz);
+        normal_out<C>(A, gi, t == IFC, gx, gy, gz);
+        return;
+    }
+    if (g - D.off >= D.n) return;   // padding after the domain
+    const Stencil st = make_stencil(D, g);
+    // the seven types are loaded together (no load waits for another's result)
+    const uint8_t t = ctype(A.flag[g]);
+    const uint8_t t1 = ctype(A.flag[st.at(1, 0, 0)]), t2 = ctype(A.flag[st.at(-1, 0, 0)]);
+    const uint8_t t3 = ctype(A.flag[st.at(0, 1, 0)]), t4 = ctype(A.flag[st.at(0, -1, 0)]);
+    const uint8_t t5 = ctype(A.flag[st.at(0, 0, 1)]), t6 = ctype(A.flag[st.at(0, 0, -1)]);
+    const int need = (t == IFC) | (t1 == IFC) | (t2 == IFC) | (t3 == IFC) | (t4 == IFC) | (t5 == IFC) | (t6 == IFC);
+    if (!need) return;
+    C gx, gy, gz;
+    pyg_of<C>([&](int dx, int dy, int dz) { return ph[st.at(dx, dy, dz)]; }, gx, gy, gz);
+    normal_out<C>(A, (unsigned)g, t == IFC, gx, gy, gz);
+}
+
+// The normals pass of a single-domain handle by 3D tiles: a block takes a
+// tile of NT_X x NT_Y x NT_Z cells, loads the types and stencil values of the
+// tile and its one-cell halo (wrapping periodically, as the stencil does)
+// into shared memory with every load independent of the others, then each
+// thread walks its (x, y) column through the tile's z-planes and stores the
+// normals of the cells that need one, from the shared copy.  The values and
+// the arithmetic are those of k_normals.  Needs nx >= NT_X, ny >= NT_Y and
+// nz >= NT_Z (a halo coordinate is then at most one domain length out).
+constexpr int NT_X = 32, NT_Y = 8, NT_Z = 8;
+constexpr int NH_X = NT_X + 2, NH_Y = NT_Y + 2, NH_Z = NT_Z + 2;
+template <typename T>
+__global__ void __launch_bounds__(NT_X * NT_Y) k_normals_tiled(StepArgs A) {
+    using C = typename Form<T>::C;
+    __shared__ C vs[NH_Z][NH_Y][NH_X];
+    __shared__ uint8_t ts[NH_Z][NH_Y][NH_X];
+    const Dom& D = A.d0;
+    const int ntx = (D.nx + NT_X - 1) / NT_X, nty = (D.ny + NT_Y - 1) / NT_Y;
+    const int b = (int)blockIdx.x;
+    const int x0 = (b % ntx) * NT_X, y0 = ((b / ntx) % nty) * NT_Y, z0 = (b / (ntx * nty)) * NT_Z;
+    const C* __restrict__ ph;
+    if constexpr (sizeof(C) == 8) ph = A.phit;
+    else ph = A.phitf;
+    const unsigned off = (unsigned)D.off;
+    // all loads of the thread first, then the shared stores (element i of the
+    // halo tile is entry i of the flattened shared arrays)
+    constexpr int NH = NH_X * NH_Y * NH_Z, NTH = NT_X * NT_Y, NIT = (NH + NTH - 1) / NTH;
+    C lv[NIT];
+    uint8_t lt[NIT];
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+        const int i = (int)threadIdx.x + k * NTH;
+        if (i < NH) {
+            const int hx = i % NH_X, hy = (i / NH_X) % NH_Y, hz = i / (NH_X * NH_Y);
+            int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+            x = x < 0 ? x + D.nx : (x >= D.nx ? x - D.nx : x);
+            y = y < 0 ? y + D.ny : (y >= D.ny ? y - D.ny : y);
+            z = z < 0 ? z + D.nz : (z >= D.nz ? z - D.nz : z);
+            const unsigned c = off + (unsigned)(x + D.nx * (y + D.ny * z));
+            lv[k] = ph[c];
+            lt[k] = ctype(A.flag[c]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+        const int i = (int)threadIdx.x + k * NTH;
+        if (i < NH) {
+            (&vs[0][0][0])[i] = lv[k];
+            (&ts[0][0][0])[i] = lt[k];
+        }
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % NT_X, ty = threadIdx.x / NT_X;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x >= D.nx || y >= D.ny) return;
+    const int hx = tx + 1, hy = ty + 1;
+#pragma unroll 1
+    for (int tz = 0; tz < NT_Z; ++tz) {
+        const int z = z0 + tz;
+        if (z >= D.nz) break;
+        const int hz = tz + 1;
+        const uint8_t t = ts[hz][hy][hx];
+        const int need = (t == IFC) | (ts[hz][hy][hx + 1] == IFC) | (ts[hz][hy][hx - 1] == IFC) |
+                         (ts[hz][hy + 1][hx] == IFC) | (ts[hz][hy - 1][hx] == IFC) | (ts[hz + 1][hy][hx] == IFC) |
+                         (ts[hz - 1][hy][hx] == IFC);
+        if (!need) continue;
+        C gx, gy, gz;
+        pyg_of<C>([&](int dx, int dy, int dz) { return vs[hz + dz][hy + dy][hx + dx]; }, gx, gy, gz);
+        normal_out<C>(A, off + (unsigned)(x + D.nx * (y + D.ny * z)), t == IFC, gx, gy, gz);
     }
 }
 
@@ -1331,12 +1513,12 @@ __device__ __forceinline__ void pyn(const C* stc, int t, C& nx, C& ny, C& nz) {
 // interface pass (stream with bounce-back, Eq. 7; mass exchange over the 18
 // links in direction order, Eq. 10; reconstruction from the bubble's gas
 // density 3 (p_V + 2 sigma kappa), Eqs. 8, 11-15; collision, Eq. 6; filled /
-// emptied marks).  stc: the block's stencil staging, [81][IB].  Returns
-// whether the cell was marked.
-template <typename T, bool ONE, int IB>
-__device__ __forceinline__ bool iface_one(const StepArgs& A, long long g, typename Form<T>::C* stc) {
+// emptied marks).  The curvature and the normal test come from the normals
+// pass (k_normals), run before this kernel in the same step.  Returns whether
+// the cell was marked.
+template <typename T, bool ONE>
+__device__ __forceinline__ bool iface_one(const StepArgs& A, long long g) {
     using C = typename Form<T>::C;
-    const int t = threadIdx.x;
     const Dom& D = dom_at<ONE>(A, g);
     const Par<C> R = par_of<C>(D);
     const Stencil st = make_stencil(D, g);
@@ -1344,24 +1526,8 @@ __device__ __forceinline__ bool iface_one(const StepArgs& A, long long g, typena
     const T* __restrict__ src = (const T*)A.fsrc;
     T* __restrict__ dst = (T*)A.fdst;
     const C* __restrict__ phic;
-    const C* __restrict__ phtc;
-    if constexpr (sizeof(C) == 8) { phic = A.phi; phtc = A.phit; }
-    else { phic = A.phif; phtc = A.phitf; }
-    // the stencil fill levels into the staging; those of the cell and of its
-    // 18 neighbours follow below from the types and fill levels loaded there
-#pragma unroll
-    for (int dz = -2; dz <= 2; ++dz)
-#pragma unroll
-        for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-            for (int dx = -2; dx <= 2; ++dx) {
-                const int nz = (dx != 0) + (dy != 0) + (dz != 0);
-                const bool d3q19 = nz <= 2 && dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
-                if (in81(dx, dy, dz) && !d3q19) stc[st81(dx, dy, dz) * IB + t] = phtc[st.at(dx, dy, dz)];
-            }
-    // (no load of the next group is moved above these stores: the two groups
-    // in flight together would not fit the registers)
-    asm volatile("" ::: "memory");
+    if constexpr (sizeof(C) == 8) phic = A.phi;
+    else phic = A.phif;
     // own PDFs, and per direction a the source x - c_a: its type, the PDF
     // streaming in and its fill level
     // (the 18 source types packed 3 bits each: ty(a) = (tym >> 3a) & 7)
@@ -1377,20 +1543,7 @@ __device__ __forceinline__ bool iface_one(const StepArgs& A, long long g, typena
         phy[a] = phic[y];
     }
     auto ty = [&](int a) { return (uint8_t)((tym >> (3 * a)) & 7u); };
-    // the stencil value of a cell is a function of its type and fill level
-    // (walls and liquid 1, gas 0, interface the fill level clamped to [0, 1]),
-    // the same expression that keeps the stored copy
-    auto stv = [&](uint8_t ty_, C ph) -> C {
-        if (ty_ == IFC) {
-            if constexpr (sizeof(C) == 8) return ph < 0.0 ? 0.0 : (ph > 1.0 ? 1.0 : ph);
-            else return fminf(fmaxf(ph, 0.f), 1.f);
-        }
-        return ty_ == GAS ? (C)0 : (C)1;
-    };
-#pragma unroll
-    for (int a = 1; a < 19; ++a) stc[st81(-cx(a), -cy(a), -cz(a)) * IB + t] = stv(ty(a), phy[a]);
     const C phx = phic[g];
-    stc[st81(0, 0, 0) * IB + t] = stv(IFC, phx);
     const double m0 = A.m[g];
     const int bub = A.id[g];
     C pv;
@@ -1413,19 +1566,14 @@ __device__ __forceinline__ bool iface_one(const StepArgs& A, long long g, typena
         has_gas |= tz == GAS;
         has_liq |= tz == LIQ;
     }
-    // gradient at the cell and unit normals at the face neighbours; curvature
-    C gx, gy, gz, n1x, n1y, n1z, n2x, n2y, n2z;
-    pyg<C, IB, 0, 0, 0>(stc, t, gx, gy, gz);
-    pyn<C, IB, 1, 0, 0>(stc, t, n1x, n1y, n1z);
-    pyn<C, IB, -1, 0, 0>(stc, t, n2x, n2y, n2z);
-    const C dX = n1x - n2x;
-    pyn<C, IB, 0, 1, 0>(stc, t, n1x, n1y, n1z);
-    pyn<C, IB, 0, -1, 0>(stc, t, n2x, n2y, n2z);
-    const C dY = n1y - n2y;
-    pyn<C, IB, 0, 0, 1>(stc, t, n1x, n1y, n1z);
-    pyn<C, IB, 0, 0, -1>(stc, t, n2x, n2y, n2z);
-    const C dZ = n1z - n2z;
+    // curvature (Eq. 15): half the divergence of the face neighbours' unit
+    // normals by central differences; the normal test bits of the cell
+    const C* __restrict__ nr = (const C*)A.nrm;
+    const C dX = nr[st.at(1, 0, 0)] - nr[st.at(-1, 0, 0)];
+    const C dY = nr[S + st.at(0, 1, 0)] - nr[S + st.at(0, -1, 0)];
+    const C dZ = nr[2u * S + st.at(0, 0, 1)] - nr[2u * S + st.at(0, 0, -1)];
     const C kappa = (C)0.25 * ((dX + dY) + dZ);
+    const unsigned nmk = A.nmask[g];
     // gas velocity: that of the cell's own post-collision PDFs
     C rs, jsx, jsy, jsz;
     moments<C>(fs, rs, jsx, jsy, jsz);
@@ -1453,7 +1601,7 @@ __device__ __forceinline__ bool iface_one(const StepArgs& A, long long g, typena
                 fin[a] = (fga + fgb) - fsb;
             } else {
                 fin[a] = fy[a];
-                if (D.normal_rule && ((C)cx(a) * gx + (C)cy(a) * gy) + (C)cz(a) * gz > (C)0) fin[a] = (fga + fgb) - fsb;
+                if (D.normal_rule && ((nmk >> a) & 1u)) fin[a] = (fga + fgb) - fsb;
             }
         }
     }
@@ -1500,10 +1648,8 @@ __device__ __forceinline__ bool iface_one(const StepArgs& A, long long g, typena
 // The interface cells of the list, one per thread, by a resident grid (block
 // b takes list entries b IB .. b IB + IB - 1, then those a grid further).
 template <typename T, bool ONE>
-__global__ void __launch_bounds__(IfThreads<T>::n, sizeof(T) == 8 ? 4 : 4) k_iface(StepArgs A) {
-    using C = typename Form<T>::C;
+__global__ void __launch_bounds__(IfThreads<T>::n, sizeof(T) == 8 ? 4 : 5) k_iface(StepArgs A) {
     constexpr int IB = IfThreads<T>::n;
-    __shared__ C stc[81 * IB];
     pdl_trigger();   // the conversion kernel may be placed as blocks finish
     if (blockIdx.x == 0) step_counters(A);
     const int cnt = *A.icount;
@@ -1513,7 +1659,7 @@ __global__ void __launch_bounds__(IfThreads<T>::n, sizeof(T) == 8 ? 4 : 4) k_ifa
         long long g = 0;
         if (i < cnt) {
             g = A.ilist[i];
-            mk = iface_one<T, ONE, IB>(A, g, stc);
+            mk = iface_one<T, ONE>(A, g);
         }
         list_append(A.mlist, A.mcount, mk, (int)g);
     }
@@ -1526,14 +1672,10 @@ __device__ inline unsigned ifc_mask16(const uint8_t* flag, long long j);
 // memory (ballot compaction), then processes those one per thread.  The
 // interface cells' neighbour data is what the block has just read, and both
 // kinds of stores to a 32-byte sector meet in L2 before it is written back.
-// Dynamic shared memory: the stencil staging, 81 values per thread.
 template <typename T, bool ONE, int TPB>
 __global__ void __launch_bounds__(FSL_BLOCK, 2) k_stream_tile(StepArgs A) {
-    using C = typename Form<T>::C;
     constexpr long long TILE = Form<T>::shifted ? 2 * FSL_BLOCK : FSL_BLOCK;
     constexpr int SUPER = (int)(TPB * TILE);
-    extern __shared__ __align__(16) unsigned char tile_smem[];
-    C* stc = (C*)tile_smem;
     __shared__ int il[SUPER];
     __shared__ int nil;
     pdl_trigger();   // the conversion kernel may be placed as blocks finish
@@ -1573,13 +1715,11 @@ __global__ void __launch_bounds__(FSL_BLOCK, 2) k_stream_tile(StepArgs A) {
         long long g = 0;
         if (i < ni) {
             g = il[i];
-            mk = iface_one<T, ONE, FSL_BLOCK>(A, g, stc);
+            mk = iface_one<T, ONE>(A, g);
         }
         list_append(A.mlist, A.mcount, mk, (int)g);
     }
 }
-// dynamic shared memory of the tile-fused form
-template <typename T> constexpr int tile_smem_bytes() { return 81 * FSL_BLOCK * (int)sizeof(typename Form<T>::C); }
 
 // The liquid cells only (a tile per block), for the two-kernel form.
 template <typename T, bool ONE>
@@ -2757,6 +2897,23 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_mass_partials(const T* f, const u
     }
 }
 
+// The normals pass ahead of the forms that take interface cells one per
+// thread: by tiles for a single domain at least one tile in size, else one
+// thread per cell.
+template <typename T>
+inline void launch_normals(const StepArgs& A, long long nb, cudaStream_t s) {
+    const Dom& D = A.d0;
+    if (A.ndom == 1 && D.nx >= NT_X && D.ny >= NT_Y && D.nz >= NT_Z) {
+        const unsigned nt = (unsigned)(((D.nx + NT_X - 1) / NT_X) * ((D.ny + NT_Y - 1) / NT_Y) *
+                                       ((D.nz + NT_Z - 1) / NT_Z));
+        k_normals_tiled<T><<<nt, NT_X * NT_Y, 0, s>>>(A);
+    } else if (A.ndom == 1) {
+        k_normals<T, true><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);
+    } else {
+        k_normals<T, false><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);
+    }
+}
+
 // Launch helpers instantiated once per storage form.
 template <typename T> void launch_stream(const StepArgs& A, long long nblocks, int ifblocks, int form, int pgrid,
                                          cudaStream_t s, cudaEvent_t el, cudaEvent_t ei, cudaStream_t s2,
@@ -2791,17 +2948,19 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
             const long long tile = Form<T>::shifted ? 2LL * FSL_BLOCK : (long long)FSL_BLOCK;                \
             const int tpb = form == SC_TILE2 ? 2 : 4;                                                       \
             const unsigned nsup = (unsigned)((A.stride + tpb * tile - 1) / (tpb * tile));                    \
-            const int sm = tile_smem_bytes<T>();                                                             \
             if (A.ndom == 1) {                                                                               \
-                if (tpb == 2) k_stream_tile<T, true, 2><<<nsup, FSL_BLOCK, sm, s>>>(A);                      \
-                else k_stream_tile<T, true, 4><<<nsup, FSL_BLOCK, sm, s>>>(A);                               \
+                launch_normals<T>(A, nb, s);                                                                 \
+                if (tpb == 2) k_stream_tile<T, true, 2><<<nsup, FSL_BLOCK, 0, s>>>(A);                       \
+                else k_stream_tile<T, true, 4><<<nsup, FSL_BLOCK, 0, s>>>(A);                                \
             } else {                                                                                         \
-                if (tpb == 2) k_stream_tile<T, false, 2><<<nsup, FSL_BLOCK, sm, s>>>(A);                     \
-                else k_stream_tile<T, false, 4><<<nsup, FSL_BLOCK, sm, s>>>(A);                              \
+                launch_normals<T>(A, nb, s);                                                                 \
+                if (tpb == 2) k_stream_tile<T, false, 2><<<nsup, FSL_BLOCK, 0, s>>>(A);                      \
+                else k_stream_tile<T, false, 4><<<nsup, FSL_BLOCK, 0, s>>>(A);                               \
             }                                                                                                \
         } else if (form == SC_TWOC) {                                                                        \
             /* the interface kernel on a second stream, beside the liquid kernel */                          \
             const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                     \
+            launch_normals<T>(A, nb, s);                                                                     \
             cudaEventRecord(efork, s);                                                                       \
             cudaStreamWaitEvent(s2, efork, 0);                                                               \
             if (A.ndom == 1) k_iface<T, true><<<pg, IfThreads<T>::n, 0, s2>>>(A);                            \
@@ -2813,9 +2972,11 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
         } else if (form == SC_TWO) {                                                                         \
             const long long nliq = Form<T>::shifted ? (nb + 1) / 2 : nb;                                     \
             if (A.ndom == 1) {                                                                               \
+                launch_normals<T>(A, nb, s);                                                                 \
                 k_liquid<T, true><<<(unsigned)nliq, FSL_BLOCK, 0, s>>>(A);                                   \
                 k_iface<T, true><<<pg, IfThreads<T>::n, 0, s>>>(A);                                          \
             } else {                                                                                         \
+                launch_normals<T>(A, nb, s);                                                                 \
                 k_liquid<T, false><<<(unsigned)nliq, FSL_BLOCK, 0, s>>>(A);                                  \
                 k_iface<T, false><<<pg, IfThreads<T>::n, 0, s>>>(A);                                         \
             }                                                                                                \
@@ -2838,14 +2999,8 @@ template <typename T> void launch_mass_partials(const void* f, const uint8_t* fl
         int nb = 0;                                                                                          \
         if (form == SC_SPLIT) nb = 1;                                                                        \
         else if (form == SC_TILE2 || form == SC_TILE4) {                                                     \
-            /* the staging exceeds the default 48 KB: allow it, then ask */                                  \
-            const int sm = tile_smem_bytes<T>();                                                             \
-            cudaFuncSetAttribute(k_stream_tile<T, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
-            cudaFuncSetAttribute(k_stream_tile<T, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
-            cudaFuncSetAttribute(k_stream_tile<T, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
-            cudaFuncSetAttribute(k_stream_tile<T, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);\
-            if (one) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, true, 2>, FSL_BLOCK, sm); \
-            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, false, 2>, FSL_BLOCK, sm); \
+            if (one) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, true, 2>, FSL_BLOCK, 0); \
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stream_tile<T, false, 2>, FSL_BLOCK, 0); \
         }                                                                                                    \
         else if (form == SC_TWOC && one)                                                                     \
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iface<T, true>, IfThreads<T>::n, 0);        \
