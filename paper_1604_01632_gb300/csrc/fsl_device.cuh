@@ -1440,18 +1440,21 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_normals(StepArgs A) {
 // The normals pass of a single-domain handle by 3D tiles: a block takes a
 // tile of NT_X x NT_Y x NT_Z cells, loads the types and stencil values of the
 // tile and its one-cell halo (wrapping periodically, as the stencil does)
-// into shared memory with every load independent of the others, then each
-// thread walks its (x, y) column through the tile's z-planes and stores the
-// normals of the cells that need one, from the shared copy.  The values and
-// the arithmetic are those of k_normals.  Needs nx >= NT_X, ny >= NT_Y and
+// into shared memory with every load independent of the others, lists the
+// tile's cells that need a normal and computes those one per thread from the
+// shared copy.  The values and the arithmetic are those of k_normals.  Needs nx >= NT_X, ny >= NT_Y and
 // nz >= NT_Z (a halo coordinate is then at most one domain length out).
 constexpr int NT_X = 32, NT_Y = 8, NT_Z = 8;
 constexpr int NH_X = NT_X + 2, NH_Y = NT_Y + 2, NH_Z = NT_Z + 2;
+static_assert(NT_X == 32 && NT_Y == 8 && NT_Z <= 8, "the tile's cell list packs x, y, z into 5 + 3 + 3 bits");
 template <typename T>
 __global__ void __launch_bounds__(NT_X * NT_Y) k_normals_tiled(StepArgs A) {
     using C = typename Form<T>::C;
     __shared__ C vs[NH_Z][NH_Y][NH_X];
     __shared__ uint8_t ts[NH_Z][NH_Y][NH_X];
+    __shared__ unsigned short clist[NT_X * NT_Y * NT_Z];
+    __shared__ int nlist;
+    if (threadIdx.x == 0) nlist = 0;
     const Dom& D = A.d0;
     const int ntx = (D.nx + NT_X - 1) / NT_X, nty = (D.ny + NT_Y - 1) / NT_Y;
     const int b = (int)blockIdx.x;
@@ -1488,23 +1491,34 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_normals_tiled(StepArgs A) {
         }
     }
     __syncthreads();
+    // the tile's cells that need a normal, listed (warp ballots), then taken
+    // one per thread, so that no lane idles through a normal of its warp
     const int tx = threadIdx.x % NT_X, ty = threadIdx.x / NT_X;
-    const int x = x0 + tx, y = y0 + ty;
-    if (x >= D.nx || y >= D.ny) return;
-    const int hx = tx + 1, hy = ty + 1;
+    const unsigned lane = threadIdx.x & 31u;
+    const bool col = x0 + tx < D.nx && y0 + ty < D.ny;
 #pragma unroll 1
     for (int tz = 0; tz < NT_Z; ++tz) {
-        const int z = z0 + tz;
-        if (z >= D.nz) break;
-        const int hz = tz + 1;
-        const uint8_t t = ts[hz][hy][hx];
-        const int need = (t == IFC) | (ts[hz][hy][hx + 1] == IFC) | (ts[hz][hy][hx - 1] == IFC) |
+        const int hx = tx + 1, hy = ty + 1, hz = tz + 1;
+        const bool nd = col && z0 + tz < D.nz &&
+                        ((ts[hz][hy][hx] == IFC) | (ts[hz][hy][hx + 1] == IFC) | (ts[hz][hy][hx - 1] == IFC) |
                          (ts[hz][hy + 1][hx] == IFC) | (ts[hz][hy - 1][hx] == IFC) | (ts[hz + 1][hy][hx] == IFC) |
-                         (ts[hz - 1][hy][hx] == IFC);
-        if (!need) continue;
+                         (ts[hz - 1][hy][hx] == IFC));
+        const unsigned bal = __ballot_sync(0xffffffffu, nd);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&nlist, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (nd) clist[base + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)(tx | (ty << 5) | (tz << 8));
+    }
+    __syncthreads();
+    const int n = nlist;
+    for (int i = threadIdx.x; i < n; i += NT_X * NT_Y) {
+        const unsigned c = clist[i];
+        const int cx_ = (int)(c & 31u), cy_ = (int)((c >> 5) & 7u), cz_ = (int)(c >> 8);
+        const int hx = cx_ + 1, hy = cy_ + 1, hz = cz_ + 1;
         C gx, gy, gz;
         pyg_of<C>([&](int dx, int dy, int dz) { return vs[hz + dz][hy + dy][hx + dx]; }, gx, gy, gz);
-        normal_out<C>(A, off + (unsigned)(x + D.nx * (y + D.ny * z)), t == IFC, gx, gy, gz);
+        normal_out<C>(A, off + (unsigned)((x0 + cx_) + D.nx * ((y0 + cy_) + D.ny * (z0 + cz_))),
+                      ts[hz][hy][hx] == IFC, gx, gy, gz);
     }
 }
 
