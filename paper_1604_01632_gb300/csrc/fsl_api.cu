@@ -85,6 +85,8 @@ struct fsl_domain {
     // device state
     Dom* d_doms = nullptr;
     int* d_blk_dom = nullptr;
+    int4* d_ntiles = nullptr;      // normals-pass tiles of a batch (null: some domain is smaller)
+    int nntiles = 0;
     int* d_slot_dom = nullptr;
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
@@ -115,6 +117,8 @@ struct fsl_domain {
     int *hused = nullptr, *nhused = nullptr, *nused = nullptr, *nfree = nullptr, *freelist = nullptr;
     int *aff = nullptr, *afflist = nullptr, *naff = nullptr, *plist = nullptr, *np = nullptr;
     int *newslots = nullptr, *nnew = nullptr;
+    int* bbox = nullptr;                 // per slot: box of its cells (6 ints)
+    long long *rowoff = nullptr, *nrows = nullptr;   // box rows of the marked slots
     long long* vtot = nullptr;
     int* minidx = nullptr;
     long long* counts = nullptr;
@@ -223,6 +227,8 @@ StepArgs step_args(fsl_domain* h, int src) {
     StepArgs A;
     A.doms = h->d_doms;
     A.blk_dom = h->d_blk_dom;
+    A.ntiles = h->d_ntiles;
+    A.nntiles = h->nntiles;
     A.stride = h->stride;
     A.fsrc = h->f[src];
     A.fdst = h->f[1 - src];
@@ -233,6 +239,7 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.phit = h->phit;
     A.phif = h->phif;
     A.phitf = h->phitf;
+    A.bbox = h->bbox;
     A.nrm = h->nrm;
     A.nmask = h->nmask;
     A.rhoi = h->rhoi;
@@ -298,6 +305,8 @@ CclArgs ccl_args(fsl_domain* h, int initial) {
     K.np = h->np;
     K.newslots = h->newslots;
     K.nnew = h->nnew;
+    K.rowoff = h->rowoff;
+    K.nrows = h->nrows;
     K.slot_dom = h->d_slot_dom;
     K.runs = h->runs;
     K.vsfx = h->vsfx;
@@ -610,6 +619,20 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
 #define AL(ptr, bytes) if (e == cudaSuccess) e = dalloc(h, &(ptr), (bytes))
     AL(h->d_doms, sizeof(Dom) * n_domains);
     AL(h->d_blk_dom, sizeof(int) * h->blk_dom.size());
+    // tiles of the normals pass over a batch, when every domain holds a whole tile
+    std::vector<int4> ntl;
+    bool tiled = n_domains > 1;
+    for (const Dom& D : h->hdoms) tiled = tiled && D.nx >= NT_X && D.ny >= NT_Y && D.nz >= NT_Z;
+    if (tiled) {
+        for (int d = 0; d < n_domains; ++d) {
+            const Dom& D = h->hdoms[d];
+            for (int z0 = 0; z0 < D.nz; z0 += NT_Z)
+                for (int y0 = 0; y0 < D.ny; y0 += NT_Y)
+                    for (int x0 = 0; x0 < D.nx; x0 += NT_X) ntl.push_back(make_int4(d, x0, y0, z0));
+        }
+        h->nntiles = (int)ntl.size();
+        AL(h->d_ntiles, sizeof(int4) * ntl.size());
+    }
     AL(h->d_slot_dom, sizeof(int) * NS);
     AL(h->f[0], 19 * N * h->fbytes);
     AL(h->f[1], 19 * N * h->fbytes);
@@ -677,6 +700,9 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->np, sizeof(int));
     AL(h->newslots, 4 * NS);
     AL(h->nnew, sizeof(int));
+    AL(h->bbox, 6 * 4 * NS);
+    AL(h->rowoff, 8 * NS);
+    AL(h->nrows, 8);
     AL(h->minidx, 4 * NS);
     AL(h->counts, 8 * 8);
     for (const Dom& D : h->hdoms) h->max_dom_blocks = std::max(h->max_dom_blocks, ((long long)D.n + FSL_BLOCK - 1) / FSL_BLOCK);
@@ -690,6 +716,8 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     }
     e = cudaMemcpy(h->d_doms, h->hdoms.data(), sizeof(Dom) * n_domains, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_blk_dom, h->blk_dom.data(), sizeof(int) * h->blk_dom.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && h->d_ntiles)
+        e = cudaMemcpy(h->d_ntiles, ntl.data(), sizeof(int4) * ntl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_slot_dom, h->slot_dom.data(), sizeof(int) * NS, cudaMemcpyHostToDevice);
     // padding and not-yet-initialised cells are obstacles
     if (e == cudaSuccess) e = cudaMemset(h->flag, OBS, N);
@@ -702,6 +730,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess && h->phitf) e = cudaMemset(h->phitf, 0, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->nrm, 0, 3 * N * (precision == FSL_P_FP64 ? 8 : 4));
     if (e == cudaSuccess) e = cudaMemset(h->nmask, 0, 4 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->bbox, 0, 6 * 4 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->rhoi, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->exs, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->f[0], 0, 19 * N * h->fbytes);

@@ -106,6 +106,9 @@ __device__ inline void local_xyz(const Dom& D, int l, int& x, int& y, int& z) {
 struct StepArgs {
     const Dom* doms;
     const int* blk_dom;         // block -> domain
+    const int4* ntiles;         // normals pass of a batch: (domain, x0, y0, z0) per tile, or null
+                                // when a domain is smaller than a tile
+    int nntiles;
     long long stride;           // cells in the padded global lattice
     const void* fsrc;           // PDFs after the previous step (post-collision)
     void* fdst;                 // PDFs written by this step
@@ -151,6 +154,9 @@ struct StepArgs {
     int spins;                  // polls a block waits at a grid barrier before it gives up
     int bar_extra;              // arrivals a barrier waits for beyond the grid (0; 1 only to
                                 // test the timeout path: no block is then the last)
+    int* bbox;                  // per bubble slot: the box [6 s .. 6 s + 2] min x, y, z and
+                                // [6 s + 3 .. 6 s + 5] max x, y, z (domain coordinates) that holds
+                                // all of its cells; a box spanning a periodic seam is the full axis
     void* nrm;                  // normals pass: unit normals of the cells that need one,
                                 // three planes of the arithmetic type (x, y, z), stride apart
     unsigned* nmask;            // normals pass: per interface cell, bit a set when the
@@ -231,6 +237,14 @@ inline cudaError_t launch_pdl(void (*k)(Args...), unsigned grid, unsigned block,
 
 // Append v to list for every lane with pred set, one atomic per warp.  Every
 // lane of the warp must call.
+// Grow bubble slot b's box to hold the cell (x, y, z).
+__device__ inline void bbox_extend(int* bbox, int b, int x, int y, int z) {
+    if (b < 0) return;
+    int* q = bbox + 6 * (long long)b;
+    atomicMin(q + 0, x); atomicMin(q + 1, y); atomicMin(q + 2, z);
+    atomicMax(q + 3, x); atomicMax(q + 4, y); atomicMax(q + 5, z);
+}
+
 __device__ inline void list_append(int* list, int* count, bool pred, int v) {
     const unsigned full = 0xffffffffu;
     const unsigned m = __ballot_sync(full, pred);
@@ -1447,7 +1461,7 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_normals(StepArgs A) {
 constexpr int NT_X = 32, NT_Y = 8, NT_Z = 8;
 constexpr int NH_X = NT_X + 2, NH_Y = NT_Y + 2, NH_Z = NT_Z + 2;
 static_assert(NT_X == 32 && NT_Y == 8 && NT_Z <= 8, "the tile's cell list packs x, y, z into 5 + 3 + 3 bits");
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(NT_X * NT_Y) k_normals_tiled(StepArgs A) {
     using C = typename Form<T>::C;
     __shared__ C vs[NH_Z][NH_Y][NH_X];
@@ -1455,10 +1469,21 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_normals_tiled(StepArgs A) {
     __shared__ unsigned short clist[NT_X * NT_Y * NT_Z];
     __shared__ int nlist;
     if (threadIdx.x == 0) nlist = 0;
-    const Dom& D = A.d0;
-    const int ntx = (D.nx + NT_X - 1) / NT_X, nty = (D.ny + NT_Y - 1) / NT_Y;
-    const int b = (int)blockIdx.x;
-    const int x0 = (b % ntx) * NT_X, y0 = ((b / ntx) % nty) * NT_Y, z0 = (b / (ntx * nty)) * NT_Z;
+    // the block's tile: from its index in a single domain, from the tile
+    // table in a batch
+    int x0, y0, z0;
+    const Dom* Dp;
+    if constexpr (ONE) {
+        Dp = &A.d0;
+        const int ntx = (Dp->nx + NT_X - 1) / NT_X, nty = (Dp->ny + NT_Y - 1) / NT_Y;
+        const int b = (int)blockIdx.x;
+        x0 = (b % ntx) * NT_X; y0 = ((b / ntx) % nty) * NT_Y; z0 = (b / (ntx * nty)) * NT_Z;
+    } else {
+        const int4 t = A.ntiles[blockIdx.x];
+        Dp = &get_dom(A, t.x);
+        x0 = t.y; y0 = t.z; z0 = t.w;
+    }
+    const Dom& D = *Dp;
     const C* __restrict__ ph;
     if constexpr (sizeof(C) == 8) ph = A.phit;
     else ph = A.phitf;
@@ -1996,6 +2021,7 @@ __device__ inline void convert_ab_phase(const StepArgs& A) {
                     for (int q = 1; q < 19; ++q) r = r + (double)Form<T>::ld(f + (long long)q * S + z, q);
                     A.mark[z] = MK_NEWL;
                     A.id[z] = A.id[p];
+                    bbox_extend(A.bbox, A.id[p], cz_.x, cz_.y, cz_.z);
                     A.m[z] = r;
                     A.rhoi[z] = r;
                     atomicAdd((unsigned long long*)&A.nif[d], 1ull);
@@ -2193,6 +2219,8 @@ struct CclArgs {
     int* np;
     int* newslots;               // slots handed out in the pass
     int* nnew;
+    long long* rowoff;           // per marked slot (afflist order): first box row of its scan
+    long long* nrows;            // box rows over all marked slots
     const int* slot_dom;         // slot -> domain
     long long* runs;             // labelling passes run after initialisation
     long long* vsfx;             // bubble tables written by the install phase
@@ -2531,31 +2559,92 @@ __device__ inline long long dom_ntiles(const StepArgs& A, int d) {
     for (long long base_ = (long long)blockIdx.x * blockDim.x, i = base_ + threadIdx.x; base_ < (n);      \
          base_ += (long long)gridDim.x * blockDim.x, i = base_ + threadIdx.x)
 
-// Phase 1: the cells taking part (every gas / interface cell in the initial
-// pass; afterwards those of the marked bubbles, found by a scan of the
-// triggered domains' tiles, one cell per thread of a 256-thread block) start
-// as their own roots and are listed; marked slots go onto their domain's free
-// stack.  A marked bubble's cells touch no gas or interface cell outside the
-// pass: two bubbles become adjacent only through a new interface cell from
-// liquid, and phase C marks every bubble around such a cell.
+// Phase 0 (passes after the initial one): block 0 lays the box rows of the
+// marked bubbles end to end, rowoff[k] = rows of the boxes of afflist[0 .. k).
+__device__ inline void ccl_rows_phase(const StepArgs& A, const CclArgs& K) {
+    if (blockIdx.x != 0) return;
+    const int na = *K.naff;
+    long long base = 0;
+    for (int k0 = 0; k0 < na; k0 += blockDim.x) {
+        const int k = k0 + (int)threadIdx.x;
+        long long rows = 0;
+        if (k < na) {
+            const int* q = A.bbox + 6 * (long long)K.afflist[k];
+            if (q[3] >= q[0]) rows = (long long)(q[4] - q[1] + 1) * (long long)(q[5] - q[2] + 1);
+        }
+        // block-wide exclusive sum of the row counts (64-bit, warp shuffles
+        // and one shared word per warp)
+        __shared__ long long ws[32];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        long long x = rows;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        long long before = 0, tot = 0;
+        for (int v = 0; v < nw; ++v) {
+            if (v < w) before += ws[v];
+            tot += ws[v];
+        }
+        if (k < na) K.rowoff[k] = base + before + x - rows;
+        base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *K.nrows = base;
+}
+
+// Phase 1: the cells taking part start as their own roots and are listed.  In
+// the initial pass that is every gas / interface cell (a scan of the whole
+// lattice, one cell per thread of a 256-thread block, which also writes -1
+// into the labels of the other cells).  Afterwards it is the cells of the
+// bubbles phase C marked, found by scanning only their boxes, a warp per box
+// row (a cell is listed by the box of its own bubble, so at most once); the
+// labels of all other cells are -1 already (each pass resets those it set),
+// and the marked slots go onto their domains' free stacks.  A marked bubble's
+// cells touch no gas or interface cell outside the pass: two bubbles become
+// adjacent only through a new interface cell from liquid, and phase C marks
+// every bubble around such a cell.
 __device__ inline void ccl_init_phase(const StepArgs& A, const CclArgs& K) {
-    for (int dd = 0, nd = K.initial ? 1 : A.ndom; dd < nd; ++dd) {
-        if (!K.initial && A.trig[1 + dd] == 0) continue;
-        const long long t0 = K.initial ? 0 : dom_tile0(A, dd);
-        const long long t1 = K.initial ? A.stride / FSL_BLOCK : t0 + dom_ntiles(A, dd);
-        for (long long tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
+    if (K.initial) {
+        for (long long tile = blockIdx.x; tile < A.stride / FSL_BLOCK; tile += gridDim.x) {
             const long long g = tile * FSL_BLOCK + threadIdx.x;
-            bool part = is_fg(A.flag[g]);
-            if (part && !K.initial) {
-                const int b = A.id[g];
-                part = b >= 0 && K.aff[b] == 1;
-            }
+            const bool part = is_fg(A.flag[g]);
             K.lab[g] = part ? (int)g : -1;
             list_append(K.plist, K.np, part, (int)g);
         }
+        return;
     }
-    if (K.initial) return;
     const int na = *K.naff;
+    const long long nrows = *K.nrows;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nrows; r += nwarps) {
+        // the marked slot whose rows hold r: the last k with rowoff[k] <= r
+        int lo = 0, hi = na - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (K.rowoff[mid] <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        const int b = K.afflist[lo];
+        const int* q = A.bbox + 6 * (long long)b;
+        const long long ri = r - K.rowoff[lo];
+        const int nyb = q[4] - q[1] + 1;
+        const int y = q[1] + (int)(ri % nyb), z = q[2] + (int)(ri / nyb);
+        const Dom& D = get_dom(A, K.slot_dom[b]);
+        const long long row = D.off + (long long)D.nx * ((long long)y + (long long)D.ny * z);
+        for (int x0 = q[0]; x0 <= q[3]; x0 += 32) {
+            const int x = x0 + lane;
+            const long long g = row + x;
+            bool part = false;
+            if (x <= q[3] && is_fg(A.flag[g])) part = A.id[g] == b;
+            if (part) K.lab[g] = (int)g;
+            list_append(K.plist, K.np, part, (int)g);
+        }
+    }
     FSL_LIST_LOOP(i, na) {
         if (i >= na) continue;
         const int b = K.afflist[i];
@@ -2612,8 +2701,29 @@ __device__ inline void ccl_compress_phase(const StepArgs& A, const CclArgs& K) {
         if (sl < 0) continue;
         K.aff[sl] = 2;
         K.croot[sl] = r;
+        int* q = A.bbox + 6 * (long long)sl;
+        q[0] = INT_MAX; q[1] = INT_MAX; q[2] = INT_MAX; q[3] = INT_MIN; q[4] = INT_MIN; q[5] = INT_MIN;
         K.nvfx[sl] = 0; K.nvxfx[sl] = 0; K.nvsfx[sl] = 0; K.nncells[sl] = 0; K.nconstp[sl] = 0;
         K.newslots[atomicAdd(K.nnew, 1)] = sl;
+    }
+}
+
+// Grow the box of slot c by cell g, every lane of the warp calling (c < 0:
+// nothing): the lanes with the same slot reduce their coordinates first, so a
+// warp of one bubble's cells costs six atomics.
+__device__ inline void warp_bbox(const StepArgs& A, long long g, int c) {
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    int x = 0, y = 0, z = 0;
+    if (c >= 0) {
+        const Dom& D = get_dom(A, block_dom(A, g));
+        local_xyz(D, (int)(g - D.off), x, y, z);
+    }
+    const int mnx = __reduce_min_sync(peers, x), mny = __reduce_min_sync(peers, y), mnz = __reduce_min_sync(peers, z);
+    const int mxx = __reduce_max_sync(peers, x), mxy = __reduce_max_sync(peers, y), mxz = __reduce_max_sync(peers, z);
+    if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+        int* q = A.bbox + 6 * (long long)c;
+        atomicMin(q + 0, mnx); atomicMin(q + 1, mny); atomicMin(q + 2, mnz);
+        atomicMax(q + 3, mxx); atomicMax(q + 4, mxy); atomicMax(q + 5, mxz);
     }
 }
 
@@ -2652,6 +2762,7 @@ __device__ inline void ccl_pairs_phase(const StepArgs& A, const CclArgs& K) {
         }
         warp_add(K.nvfx, c, term);
         warp_add(K.nncells, c, c >= 0 ? 1 : 0);
+        warp_bbox(A, valid ? g : -1, c);
         if (c < 0) continue;
         if (!K.initial && A.id[g] >= 0) {
             const int b = A.id[g];
@@ -2702,6 +2813,11 @@ __device__ inline void ccl_table_phase(const StepArgs& A, const CclArgs& K) {
 // positions taken are emptied; the marks are cleared.
 __device__ inline void ccl_install_phase(const StepArgs& A, const CclArgs& K) {
     if (!K.initial && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)K.runs, 1ull);
+    // the labels this pass set go back to -1 (the next pass scans boxes only)
+    const int np = *K.np;
+    FSL_LIST_LOOP(i, np) {
+        if (i < np) K.lab[K.plist[i]] = -1;
+    }
     const int nn = *K.nnew;
     FSL_LIST_LOOP(i, nn) {
         if (i >= nn) continue;
@@ -2798,6 +2914,8 @@ __global__ void __launch_bounds__(FSL_CONV_THREADS, 3) k_convert(StepArgs A, Ccl
         order_write_phase(A);
     }
     if (!relabel) return;
+    if (!grid_barrier(A)) return;
+    ccl_rows_phase(A, K);
     if (!grid_barrier(A)) return;
     ccl_init_phase(A, K);
     if (!grid_barrier(A)) return;
@@ -2912,15 +3030,17 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_mass_partials(const T* f, const u
 }
 
 // The normals pass ahead of the forms that take interface cells one per
-// thread: by tiles for a single domain at least one tile in size, else one
-// thread per cell.
+// thread: by tiles when every domain is at least one tile in size (a batch
+// through its tile table), else one thread per cell.
 template <typename T>
 inline void launch_normals(const StepArgs& A, long long nb, cudaStream_t s) {
     const Dom& D = A.d0;
     if (A.ndom == 1 && D.nx >= NT_X && D.ny >= NT_Y && D.nz >= NT_Z) {
         const unsigned nt = (unsigned)(((D.nx + NT_X - 1) / NT_X) * ((D.ny + NT_Y - 1) / NT_Y) *
                                        ((D.nz + NT_Z - 1) / NT_Z));
-        k_normals_tiled<T><<<nt, NT_X * NT_Y, 0, s>>>(A);
+        k_normals_tiled<T, true><<<nt, NT_X * NT_Y, 0, s>>>(A);
+    } else if (A.ndom > 1 && A.ntiles) {
+        k_normals_tiled<T, false><<<(unsigned)A.nntiles, NT_X * NT_Y, 0, s>>>(A);
     } else if (A.ndom == 1) {
         k_normals<T, true><<<(unsigned)nb, FSL_BLOCK, 0, s>>>(A);
     } else {

@@ -163,11 +163,16 @@ def test_reduced_precision_static_bubble(fsl, oracle_mod, precision, tol_u, tol_
     assert (g["flags"] == r["flags"]).mean() > 0.999
 
 
-def test_batched_bubble_population_parity(fsl, oracle_mod):
+@pytest.mark.parametrize("form", [-1, 5])
+def test_batched_bubble_population_parity(fsl, oracle_mod, form):
     """Three domains of the bubble-population workload (axes from {32, 48}) in one
-    handle against three oracles."""
+    handle against three oracles: the tuned stream-collide form, and the
+    two-kernel form, whose normals pass takes the batch through its tile table
+    (every domain holds a whole 32 x 8 x 8 tile)."""
     scs = S.bubble_population(n_domains=3, seed=5, sides=(32, 48))
     sim = fsl.Simulation.from_scenarios(scs, precision="fp64")
+    if form >= 0:
+        sim.set_stream_form(form)
     oras = [oracle_mod.Oracle.from_scenario(s) for s in scs]
     prev = 0
     for k in (1, 6):
