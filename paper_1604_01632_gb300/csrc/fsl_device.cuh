@@ -2033,8 +2033,10 @@ __device__ inline void convert_ab_phase(const StepArgs& A) {
     }
 }
 
-// Sum v over the warp into base[key] with one atomic when every lane has the
-// same key; key < 0 contributes nothing.  Every lane of the warp must call.
+// Sum v over the lanes of the warp that share a key into base[key], one
+// atomic per distinct key (the values are fixed point, so the order of the
+// additions does not matter); key < 0 contributes nothing.  Every lane of the
+// warp must call.
 __device__ inline void warp_add(long long* base, int key, long long v) {
     const unsigned full = 0xffffffffu;
     const int k0 = __shfl_sync(full, key, 0);
@@ -2043,9 +2045,13 @@ __device__ inline void warp_add(long long* base, int key, long long v) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
         if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd((unsigned long long*)&base[k0], (unsigned long long)v);
-    } else if (key >= 0 && v != 0) {
-        atomicAdd((unsigned long long*)&base[key], (unsigned long long)v);
+        return;
     }
+    const unsigned peers = __match_any_sync(full, key);
+    long long sum = 0;
+    for (unsigned m = peers; m; m &= m - 1) sum += __shfl_sync(peers, v, __ffs(m) - 1);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && key >= 0 && sum != 0)
+        atomicAdd((unsigned long long*)&base[key], (unsigned long long)sum);
 }
 
 // 3x3x3 cube around a cell, bit k = (dx+1) + 3 (dy+1) + 9 (dz+1); bit 13 is the
@@ -2374,6 +2380,7 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
     const int total = ni + ng + nl;
     const int step = *A.stepno;
     const int stride = gridDim.x * blockDim.x;
+    long long kept = 0;   // interface cells kept by this thread (one domain)
     for (int base = blockIdx.x * blockDim.x; base < total; base += stride) {
         const int i = base + threadIdx.x;
         const bool valid = i < total;
@@ -2462,8 +2469,15 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
         }
         warp_add(A.vfx, dv != 0 ? key : -1, dv);
         warp_add(A.ncells, ckey, dc);
-        warp_add(A.icnt, keep ? d : -1, 1);
+        if (A.ndom == 1) kept += keep ? 1 : 0;
+        else warp_add(A.icnt, keep ? d : -1, 1);
         if (!A.order) list_append(A.ilist_next, A.icount_next, keep, (int)g);
+    }
+    if (A.ndom == 1) {
+        // one domain: the interface count by one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(0xffffffffu, kept, o);
+        if ((threadIdx.x & 31) == 0 && kept) atomicAdd((unsigned long long*)&A.icnt[0], (unsigned long long)kept);
     }
     if (blockIdx.x == 0) {
         // reservoir drain of every domain whose seed cell is still gas or
