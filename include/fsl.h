@@ -175,8 +175,9 @@ int64_t fsl_kernel_launches(const fsl_domain* h);
  * connectivity); synchronises.  -1 on error. */
 int64_t fsl_labelling_runs(fsl_domain* h);
 
-/* Device time of the stream-collide kernels of the last fsl_step call, in
- * milliseconds, summed over its steps (0 when timing is off).  Timing is
+/* Device time of the stream-collide kernels of the steps run since timing was
+ * switched on or since the previous fsl_sync, in milliseconds, summed over
+ * those steps; fsl_sync evaluates it (0 when timing is off).  Timing is
  * switched on with fsl_set_timing(h, 1); it brackets each stream-collide
  * launch with CUDA events on the handle's stream. */
 fsl_status fsl_set_timing(fsl_domain* h, int32_t on);

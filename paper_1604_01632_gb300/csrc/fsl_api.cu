@@ -1208,7 +1208,7 @@ fsl_status fsl_fields(fsl_domain* h, int32_t d, uint32_t mask, void* const* dst,
             if (mask & (1u << bit)) dev[bit] = parts[m++];
     }
     if (mask & (FSL_F_FLAGS | FSL_F_FILL | FSL_F_MASS | FSL_F_ID)) {
-        launch_export_cells(h->flag, h->phi, h->m, h->id, h->minidx, D.off, D.n, (uint8_t*)dev[0], (double*)dev[1],
+        launch_export_cells(h->flag, h->phi, h->phif, h->m, h->id, h->minidx, D.off, D.n, (uint8_t*)dev[0], (double*)dev[1],
                             (double*)dev[2], (long long*)dev[3], nullptr, h->ls);
         h->launches += 1;
     }
@@ -1240,7 +1240,7 @@ fsl_status fsl_cell_counts(fsl_domain* h, int32_t d, int64_t* counts) {
     join_in(h);
     const Dom& D = h->hdoms[d];
     CK(h, cudaMemsetAsync(h->counts, 0, 64, h->ls));
-    launch_export_cells(h->flag, h->phi, h->m, h->id, h->minidx, D.off, D.n, nullptr, nullptr, nullptr, nullptr,
+    launch_export_cells(h->flag, h->phi, h->phif, h->m, h->id, h->minidx, D.off, D.n, nullptr, nullptr, nullptr, nullptr,
                         h->counts, h->ls);
     h->launches += 1;
     long long c[8];

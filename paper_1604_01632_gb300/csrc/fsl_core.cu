@@ -47,7 +47,9 @@ __global__ void k_export_minid(const int* id, long long off, int n, int* minidx)
     if (b >= 0) atomicMin(&minidx[b], (int)l);
 }
 
-__global__ void k_export_cells(const uint8_t* flag, const double* phi, const double* m, const int* id,
+// Cell export; phif (the FP32-collide forms' fill level, null in FP64) takes the
+// place of phi where given.
+__global__ void k_export_cells(const uint8_t* flag, const double* phi, const float* phif, const double* m, const int* id,
                                const int* minidx, long long off, int n, uint8_t* oflag, double* ophi, double* om,
                                long long* oid, long long* counts) {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,7 +64,7 @@ __global__ void k_export_cells(const uint8_t* flag, const double* phi, const dou
     if (l >= n) return;
     const long long g = off + l;
     if (oflag) oflag[l] = ctype(flag[g]);
-    if (ophi) ophi[l] = phi[g];
+    if (ophi) ophi[l] = phif ? (double)phif[g] : phi[g];
     if (om) om[l] = m[g];
     if (oid) {
         const int b = id[g];
@@ -89,11 +91,11 @@ void launch_export_minid(const int* id, long long off, int n, int* minidx, cudaS
     k_export_minid<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(id, off, n, minidx);
 }
 
-void launch_export_cells(const uint8_t* flag, const double* phi, const double* m, const int* id, const int* minidx,
-                         long long off, int n, uint8_t* oflag, double* ophi, double* om, long long* oid,
-                         long long* counts, cudaStream_t s) {
-    k_export_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flag, phi, m, id, minidx, off, n, oflag, ophi, om,
-                                                              oid, counts);
+void launch_export_cells(const uint8_t* flag, const double* phi, const float* phif, const double* m, const int* id,
+                         const int* minidx, long long off, int n, uint8_t* oflag, double* ophi, double* om,
+                         long long* oid, long long* counts, cudaStream_t s) {
+    k_export_cells<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(flag, phi, phif, m, id, minidx, off, n, oflag, ophi,
+                                                              om, oid, counts);
 }
 
 }  // namespace fsl

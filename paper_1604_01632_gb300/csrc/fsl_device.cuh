@@ -2163,12 +2163,21 @@ __device__ inline int block_exclusive_sum(int v, int* total) {
     return before + x - v;
 }
 
+// Each thread takes OU consecutive 16-cell words per pass, loaded before use.
+constexpr int OU = 4;
+
 // Pass 1: interface cells in each block's range.
 __device__ inline void order_count_phase(const StepArgs& A) {
     long long lo, hi;
     order_range(A, lo, hi);
     int n = 0;
-    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) n += __popc(ifc_mask16(A.flag, j));
+    for (long long j0 = lo + (long long)threadIdx.x * OU; j0 < hi; j0 += (long long)blockDim.x * OU) {
+        unsigned m[OU];
+#pragma unroll
+        for (int u = 0; u < OU; ++u) m[u] = j0 + u < hi ? ifc_mask16(A.flag, j0 + u) : 0u;
+#pragma unroll
+        for (int u = 0; u < OU; ++u) n += __popc(m[u]);
+    }
     int tot;
     block_exclusive_sum(n, &tot);
     if (threadIdx.x == 0) A.ocnt[blockIdx.x] = tot;
@@ -2183,12 +2192,20 @@ __device__ inline void order_write_phase(const StepArgs& A) {
     for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) part += A.ocnt[k];
     int off;
     block_exclusive_sum(part, &off);
-    for (long long j0 = lo; j0 < hi; j0 += blockDim.x) {
-        const long long j = j0 + threadIdx.x;
-        const unsigned m = j < hi ? ifc_mask16(A.flag, j) : 0u;
+    for (long long j0 = lo; j0 < hi; j0 += (long long)blockDim.x * OU) {
+        // thread t takes words jt .. jt + OU - 1, after those of the threads before it
+        const long long jt = j0 + (long long)threadIdx.x * OU;
+        unsigned m[OU];
+        int c = 0;
+#pragma unroll
+        for (int u = 0; u < OU; ++u) m[u] = jt + u < hi ? ifc_mask16(A.flag, jt + u) : 0u;
+#pragma unroll
+        for (int u = 0; u < OU; ++u) c += __popc(m[u]);
         int tot;
-        int pos = off + block_exclusive_sum(__popc(m), &tot);
-        for (unsigned b = m; b; b &= b - 1) A.ilist_next[pos++] = (int)(16 * j + (__ffs(b) - 1));
+        int pos = off + block_exclusive_sum(c, &tot);
+#pragma unroll
+        for (int u = 0; u < OU; ++u)
+            for (unsigned b = m[u]; b; b &= b - 1) A.ilist_next[pos++] = (int)(16 * (jt + u) + (__ffs(b) - 1));
         off += tot;
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *A.icount_next = off;
@@ -2398,7 +2415,9 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
             const uint8_t mk = A.mark[g];
             key = A.id[g];
             const double m0 = A.m[g], rh = A.rhoi[g];
-            // FP32-collide forms: fill levels and volume terms from the FP32 copy
+            // FP32-collide forms: fill levels and volume terms from the FP32 copies,
+            // which are the only ones kept (the FP64 fill level and stencil level
+            // belong to the FP64 form)
             const bool f32 = A.phif != nullptr;
             const double ph0 = f32 ? 0.0 : A.phi[g];
             const float ph0f = f32 ? A.phif[g] : 0.f;
@@ -2411,17 +2430,15 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
                 ckey = key;
                 dc = -1;
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | LIQ);
-                A.phi[g] = 1.0;
-                A.phit[g] = 1.0;
-                if (A.phif) { A.phif[g] = 1.f; A.phitf[g] = 1.f; }
+                if (f32) { A.phif[g] = 1.f; A.phitf[g] = 1.f; }
+                else { A.phi[g] = 1.0; A.phit[g] = 1.0; }
                 A.id[g] = -1;
                 A.mark[g] = MK_NONE;
             } else if (t == IFC && mk == MK_CEMPTIED) {
                 dv = FSL_VOL_ONE - (f32 ? volume_term_f(IFC, ph0f) : volume_term(IFC, ph0));
                 A.flag[g] = (uint8_t)((f & ~K_TYPE) | GAS);
-                A.phi[g] = 0.0;
-                A.phit[g] = 0.0;
-                if (A.phif) { A.phif[g] = 0.f; A.phitf[g] = 0.f; }
+                if (f32) { A.phif[g] = 0.f; A.phitf[g] = 0.f; }
+                else { A.phi[g] = 0.0; A.phit[g] = 0.0; }
                 A.m[g] = 0.0;
                 A.mark[g] = MK_NONE;
             } else {
@@ -2451,7 +2468,6 @@ __device__ inline void convert_d_phase(const StepArgs& A) {
                     // phi = m / rho in FP32 (Eq. 9); three conversions are the
                     // only FP64-pipe work of the cell
                     const float phf = (float)sm / (float)rh;
-                    A.phi[g] = (double)phf;
                     A.phif[g] = phf;
                     A.phitf[g] = fminf(fmaxf(phf, 0.f), 1.f);
                     dv = volume_term_f(IFC, phf) - volume_term_f(t, ph0f);
