@@ -564,7 +564,9 @@ __device__ __forceinline__ void collide_dev2(const float2* d, Out&& out, float o
         jy = p2fma(p2(0.5f), K.Fy, jy);
         jz = p2fma(p2(0.5f), K.Fz, jz);
     }
-    const float2 ir = make_float2(1.f / K.rho.x, 1.f / K.rho.y);
+    // 1 / rho by the fast reciprocal (within 2 ulp of FP32; the 16-bit storage
+    // these forms serve rounds the deviations to 11 or 8 bits)
+    const float2 ir = make_float2(__fdividef(1.f, K.rho.x), __fdividef(1.f, K.rho.y));
     K.ux = p2mul(jx, ir); K.uy = p2mul(jy, ir); K.uz = p2mul(jz, ir);
     K.nusq15 = p2mul(p2fma(K.uz, K.uz, p2fma(K.uy, K.uy, p2mul(K.ux, K.ux))), p2(-1.5f));
     if constexpr (FORCE) K.uF = p2fma(K.uz, K.Fz, p2fma(K.uy, K.Fy, p2mul(K.ux, K.Fx)));
@@ -1342,7 +1344,8 @@ __device__ __forceinline__ void pyg_of(V&& v, C& gx, C& gy, C& gz) {
 
 // Stores of the normals pass for a cell g that needs a normal: the normal-test
 // bits of an interface cell, and the unit normal -grad/|grad| (0 where the
-// gradient is 0), with the arithmetic of the interface kernels.
+// gradient is 0), with the arithmetic of the interface kernels (in FP64; the
+// FP32-collide forms scale by a reciprocal square root).
 template <typename C>
 __device__ __forceinline__ void normal_out(const StepArgs& A, unsigned g, bool ifc, C gx, C gy, C gz) {
     if (ifc) {
@@ -1355,8 +1358,14 @@ __device__ __forceinline__ void normal_out(const StepArgs& A, unsigned g, bool i
     C nx = gx, ny = gy, nz = gz;
     const C qq = nx * nx + ny * ny + nz * nz;
     if (qq > (C)0) {
-        const C len = sqrt(qq);
-        nx = -(nx / len); ny = -(ny / len); nz = -(nz / len);
+        if constexpr (sizeof(C) == 8) {
+            const C len = sqrt(qq);
+            nx = -(nx / len); ny = -(ny / len); nz = -(nz / len);
+        } else {
+            // FP32-collide forms: one reciprocal square root (within 2 ulp)
+            const float il = rsqrtf(qq);
+            nx = -(nx * il); ny = -(ny * il); nz = -(nz * il);
+        }
     } else {
         nx = (C)0; ny = (C)0; nz = (C)0;
     }
