@@ -287,6 +287,7 @@ def run_gpu(args, rank: int, world: int):
     sim = make(args.precision)
     mass0 = sim.total_mass()
     tuning = tune(sim)
+    rb0, lr0 = sim.relabelled_bubbles, sim.labelling_runs
     clk = Clocks(dev)
     clk.start()
     ms, _, launches, counts, lruns = timed_steps(sim, args.steps, args.warmup, timing=False, barrier=True)
@@ -296,6 +297,8 @@ def run_gpu(args, rank: int, world: int):
     # records add a few microseconds to a step, so they stay out of the headline)
     _, k1_ms, _, _, _ = timed_steps(sim, args.steps, args.warmup, timing=True)
     mass1 = sim.total_mass()
+    # bubbles a labelling pass takes: only those phase C marked (out of all)
+    relab = (sim.relabelled_bubbles - rb0) / max(1, sim.labelling_runs - lr0)
     steps_run = tuning["steps"] + 2 * (args.steps + args.warmup)
     ms_max = max_over_ranks(ms, world, "cuda")
     value = whole_job_mlups(n, args.steps, world, ms_max)
@@ -389,6 +392,7 @@ def run_gpu(args, rank: int, world: int):
                              "exceeds L2); steps timed by CUDA events",
                        "parallelism": f"replicas x{world}",
                        "labelling_runs_per_step": round(lruns / args.steps, 3),
+                       "bubbles_relabelled_per_pass": round(relab, 1),
                        "cell_counts_liquid_interface_gas_obstacle_lid": [int(c) for c in counts[:5]],
                        "stream_collide_tuning": tuning,
                        "mass_drift_rel": float(f"{(mass1 - mass0) / mass0:.3e}"),
@@ -433,11 +437,13 @@ def run_batched(args, fsl, torch, stream, flush, steps: int = 20):
 
     sim = fsl.Simulation.from_scenarios(doms, precision=args.precision, stream=int(stream.cuda_stream))
     rec = tune(sim)
-    r0 = sim.labelling_runs
+    r0, rb0 = sim.labelling_runs, sim.relabelled_bubbles
     ms = timed(lambda: sim.step(1), sim.sync)
     out["batched_mlups"] = round(cells * steps / (ms * 1e-3) / 1e6, 1)
     out["batched_ms_per_step"] = round(ms / steps, 4)
     out["labelling_runs_per_step"] = round((sim.labelling_runs - r0) / (steps + 3), 3)
+    out["bubbles_relabelled_per_pass"] = round((sim.relabelled_bubbles - rb0) / max(1, sim.labelling_runs - r0), 1)
+    out["bubbles"] = int(sum(len(sim.bubbles(d)) for d in range(len(doms))))
     out["tuned_form"] = rec["form_name"]
     out["tuning_ms_per_form"] = rec["ms_per_form"]
     sim.close()

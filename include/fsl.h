@@ -175,6 +175,12 @@ int64_t fsl_kernel_launches(const fsl_domain* h);
  * connectivity); synchronises.  -1 on error. */
 int64_t fsl_labelling_runs(fsl_domain* h);
 
+/* Number of bubbles those passes relabelled, summed over the passes after
+ * initialisation (a pass takes only the bubbles that phase C marked as
+ * possibly merged or split, and only their cells); synchronises.  -1 on
+ * error. */
+int64_t fsl_relabelled_bubbles(fsl_domain* h);
+
 /* Device time of the stream-collide kernels of the steps run since timing was
  * switched on or since the previous fsl_sync, in milliseconds, summed over
  * those steps; fsl_sync evaluates it (0 when timing is off).  Timing is

@@ -707,7 +707,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->counts, 8 * 8);
     for (const Dom& D : h->hdoms) h->max_dom_blocks = std::max(h->max_dom_blocks, ((long long)D.n + FSL_BLOCK - 1) / FSL_BLOCK);
     AL(h->mass_part, 8 * (size_t)h->max_dom_blocks);
-    AL(h->runs, 8);
+    AL(h->runs, 16);   // [0] labelling passes, [1] bubbles they relabelled
 #undef AL
     if (e != cudaSuccess) {
         fsl_status st = (e == cudaErrorMemoryAllocation) ? FSL_ERR_OOM : FSL_ERR_CUDA;
@@ -749,7 +749,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess) e = cudaMemset(h->cstep, 0xff, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->recv, 0xff, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->icnt, 0, 8 * n_domains);
-    if (e == cudaSuccess) e = cudaMemset(h->runs, 0, 8);
+    if (e == cudaSuccess) e = cudaMemset(h->runs, 0, 16);
     if (e == cudaSuccess) e = cudaMemset(h->vfx, 0, 8 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->vxfx, 0, 8 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->vsfx, 0, 8 * NS);
@@ -1116,6 +1116,14 @@ int64_t fsl_labelling_runs(fsl_domain* h) {
     long long r = 0;
     if (cudaStreamSynchronize(h->ls) != cudaSuccess) return -1;
     if (cudaMemcpy(&r, h->runs, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    return r;
+}
+
+int64_t fsl_relabelled_bubbles(fsl_domain* h) {
+    if (!h) return -1;
+    long long r = 0;
+    if (cudaStreamSynchronize(h->ls) != cudaSuccess) return -1;
+    if (cudaMemcpy(&r, h->runs + 1, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
     return r;
 }
 

@@ -2254,7 +2254,7 @@ struct CclArgs {
     long long* rowoff;           // per marked slot (afflist order): first box row of its scan
     long long* nrows;            // box rows over all marked slots
     const int* slot_dom;         // slot -> domain
-    long long* runs;             // labelling passes run after initialisation
+    long long* runs;             // labelling passes run after initialisation, bubbles they took
     long long* vsfx;             // bubble tables written by the install phase
     int* constp;
     int initial;                 // 1: first labelling after initialisation (every bubble, V* = V)
@@ -2851,7 +2851,10 @@ __device__ inline void ccl_table_phase(const StepArgs& A, const CclArgs& K) {
 // not handed out again are emptied (they stay on the free stack); the hash
 // positions taken are emptied; the marks are cleared.
 __device__ inline void ccl_install_phase(const StepArgs& A, const CclArgs& K) {
-    if (!K.initial && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)K.runs, 1ull);
+    if (!K.initial && blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd((unsigned long long*)K.runs, 1ull);
+        atomicAdd((unsigned long long*)K.runs + 1, (unsigned long long)*K.naff);
+    }
     // the labels this pass set go back to -1 (the next pass scans boxes only)
     const int np = *K.np;
     FSL_LIST_LOOP(i, np) {

@@ -28,7 +28,7 @@ FIELD_DTYPES = {"flags": (np.uint8, 1), "fill": (np.float64, 1), "mass": (np.flo
 # names the library must export (checked by the CPU test suite)
 EXPORTS = ["fsl_create", "fsl_init_geometry", "fsl_set_bubble_source", "fsl_step", "fsl_sync", "fsl_bubbles",
            "fsl_fields", "fsl_destroy", "fsl_last_error", "fsl_kernel_launches", "fsl_set_timing",
-           "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_set_graphs",
+           "fsl_stream_collide_ms", "fsl_cell_counts", "fsl_labelling_runs", "fsl_relabelled_bubbles", "fsl_set_graphs",
            "fsl_label_bubbles_static", "fsl_phase_ms", "fsl_set_limits",
            "fsl_total_mass", "fsl_set_stream_form", "fsl_stream_form",
            "fsl_set_interface_order", "fsl_interface_order", "fsl_tuning", "fsl_forget_tuning"]
@@ -119,6 +119,8 @@ def load_library():
     L.fsl_set_limits.argtypes = [vp, i64, i64, i32]
     L.fsl_labelling_runs.restype = i64
     L.fsl_labelling_runs.argtypes = [vp]
+    L.fsl_relabelled_bubbles.restype = i64
+    L.fsl_relabelled_bubbles.argtypes = [vp]
     L.fsl_cell_counts.restype = i32
     L.fsl_cell_counts.argtypes = [vp, i32, ctypes.POINTER(i64)]
     _lib = L
@@ -325,6 +327,11 @@ class Simulation:
     @property
     def labelling_runs(self) -> int:
         return int(self.L.fsl_labelling_runs(self._h))
+
+    @property
+    def relabelled_bubbles(self) -> int:
+        """Bubbles the labelling passes took, summed over the passes."""
+        return int(self.L.fsl_relabelled_bubbles(self._h))
 
     def set_timing(self, on: bool):
         self._check(self.L.fsl_set_timing(self._h, 1 if on else 0))

@@ -36,3 +36,20 @@ def test_kernels_per_step(fsl, graphs, form):
     per_step = 4 if form in (5, 8) else 3 if form in (6, 7) else 2
     assert sim.launches - l0 == 5 * per_step
     sim.close()
+
+
+def test_labelling_counters(fsl):
+    """The labelling passes and the bubbles they take: a pass runs only on steps
+    whose conversions may have merged or split a bubble, and takes only the
+    bubbles marked then (at least one, never more than exist)."""
+    scs = S.bubble_population(n_domains=3, seed=5, sides=(32, 48))
+    sim = fsl.Simulation.from_scenarios(scs, precision="f16s")
+    sim.step(1)
+    r0, b0 = sim.labelling_runs, sim.relabelled_bubbles
+    sim.step(40)
+    runs, took = sim.labelling_runs - r0, sim.relabelled_bubbles - b0
+    nb = sum(len(sim.bubbles(d)) for d in range(len(scs)))
+    assert 0 < runs <= 40
+    assert runs <= took
+    assert took / runs <= nb + 50   # bubbles that merged away in a pass no longer count at the end
+    sim.close()
