@@ -95,6 +95,7 @@ struct fsl_domain {
     float *phif = nullptr, *phitf = nullptr;   // FP32 copies (FP32-collide forms only)
     void* nrm = nullptr;           // normals pass: 3 planes of the arithmetic type
     unsigned* nmask = nullptr;     // normals pass: reconstruction directions per interface cell
+    void* pvc = nullptr;           // normals pass: bubble pressure per interface cell
     int* id = nullptr;
     long long *vfx = nullptr, *vxfx = nullptr, *vsfx = nullptr, *ncells = nullptr;
     int* constp = nullptr;
@@ -242,6 +243,7 @@ StepArgs step_args(fsl_domain* h, int src) {
     A.bbox = h->bbox;
     A.nrm = h->nrm;
     A.nmask = h->nmask;
+    A.pvc = h->pvc;
     A.rhoi = h->rhoi;
     A.exs = h->exs;
     A.id = h->id;
@@ -647,6 +649,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     }
     AL(h->nrm, 3 * N * (precision == FSL_P_FP64 ? 8 : 4));
     AL(h->nmask, 4 * N);
+    AL(h->pvc, N * (precision == FSL_P_FP64 ? 8 : 4));
     AL(h->rhoi, 8 * N);
     AL(h->exs, 8 * N);
     AL(h->id, 4 * N);
@@ -730,6 +733,7 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     if (e == cudaSuccess && h->phitf) e = cudaMemset(h->phitf, 0, 4 * N);
     if (e == cudaSuccess) e = cudaMemset(h->nrm, 0, 3 * N * (precision == FSL_P_FP64 ? 8 : 4));
     if (e == cudaSuccess) e = cudaMemset(h->nmask, 0, 4 * N);
+    if (e == cudaSuccess) e = cudaMemset(h->pvc, 0, N * (precision == FSL_P_FP64 ? 8 : 4));
     if (e == cudaSuccess) e = cudaMemset(h->bbox, 0, 6 * 4 * NS);
     if (e == cudaSuccess) e = cudaMemset(h->rhoi, 0, 8 * N);
     if (e == cudaSuccess) e = cudaMemset(h->exs, 0, 8 * N);

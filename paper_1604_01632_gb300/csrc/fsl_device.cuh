@@ -161,6 +161,8 @@ struct StepArgs {
                                 // three planes of the arithmetic type (x, y, z), stride apart
     unsigned* nmask;            // normals pass: per interface cell, bit a set when the
                                 // reconstruction's normal test holds for direction a
+    void* pvc;                  // normals pass: per interface cell, its bubble's pressure
+                                // p_V (Eq. 13) in the arithmetic type
     Dom d0;                     // domain 0, read from the parameter space when ndom == 1
 };
 
@@ -1349,6 +1351,16 @@ __device__ __forceinline__ void pyg_of(V&& v, C& gx, C& gy, C& gz) {
 template <typename C>
 __device__ __forceinline__ void normal_out(const StepArgs& A, unsigned g, bool ifc, C gx, C gy, C gz) {
     if (ifc) {
+        // the bubble pressure the interface kernel would look up through the
+        // cell's bubble (a load that waits on another): looked up here
+        const int bub = A.id[g];
+        C pv;
+        if constexpr (sizeof(C) == 8)
+            pv = bub >= 0 ? bubble_pressure(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : 1.0 / 3.0;
+        else
+            pv = bub >= 0 ? bubble_pressure_f(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub])
+                          : (float)(1.0 / 3.0);
+        ((C*)A.pvc)[g] = pv;
         unsigned mk = 0;
 #pragma unroll
         for (int a = 1; a < 19; ++a)
@@ -1384,10 +1396,10 @@ __device__ __forceinline__ void normal_out(const StepArgs& A, unsigned g, bool i
 // normal is computed here once, for every cell that is an interface cell or a
 // face neighbour of one (walls included: the stencil reads walls as full), and
 // stored in nrm; each interface cell also stores its 18 normal-test bits in
-// nmask.  The stencil values are the stored copy phit (walls and liquid 1, gas
-// 0, interface clamp(phi, 0, 1)) and the arithmetic is that of the interface
-// kernels, so their curvature and reconstruction come out as if they had
-// computed the normals themselves.
+// nmask, and the pressure of its bubble (Eq. 13) in pvc.  The stencil values
+// are the stored copy phit (walls and liquid 1, gas 0, interface clamp(phi, 0,
+// 1)) and the arithmetic is that of the interface kernels, so their curvature
+// and reconstruction come out as if they had computed the normals themselves.
 //
 // A warp whose 32 cells lie in one row of one domain (the usual case: rows
 // start on multiples of 32 when nx is one) works on the row segment: the y / z
@@ -1593,12 +1605,7 @@ __device__ __forceinline__ bool iface_one(const StepArgs& A, long long g) {
     auto ty = [&](int a) { return (uint8_t)((tym >> (3 * a)) & 7u); };
     const C phx = phic[g];
     const double m0 = A.m[g];
-    const int bub = A.id[g];
-    C pv;
-    if constexpr (sizeof(C) == 8)
-        pv = bub >= 0 ? bubble_pressure(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : 1.0 / 3.0;
-    else
-        pv = bub >= 0 ? bubble_pressure_f(A.vfx[bub], A.vxfx[bub], A.vsfx[bub], A.constp[bub]) : (float)(1.0 / 3.0);
+    const C pv = ((const C*)A.pvc)[g];   // the bubble's pressure, from the normals pass
     // mass exchange (Eq. 10): link a reaches x + c_a = x - c_b, b = opp(a), whose
     // type, PDF f_b streaming in and fill level are the loads of direction b
     C dm = (C)0;
