@@ -1149,7 +1149,11 @@ fsl_status fsl_bubbles(fsl_domain* h, int32_t d, fsl_bubble* out, int64_t cap, i
     st = compute_minidx(h, d);
     if (st != FSL_OK) return st;
     const Dom& D = h->hdoms[d];
-    const size_t C = (size_t)D.slot_cap;
+    // only the slots handed out so far (the domain's high-water mark) hold bubbles
+    int used = 0;
+    CK(h, cudaMemcpyAsync(&used, h->nused + d, sizeof(int), cudaMemcpyDeviceToHost, h->ls));
+    CK(h, cudaStreamSynchronize(h->ls));
+    const size_t C = (size_t)std::max(0, std::min(used, D.slot_cap));
     std::vector<long long> vfx(C), vxfx(C), vsfx(C), nc(C);
     std::vector<int> cp(C), mi(C);
     CK(h, cudaMemcpyAsync(vfx.data(), h->vfx + D.slot_off, 8 * C, cudaMemcpyDeviceToHost, h->ls));

@@ -40,11 +40,14 @@ __global__ void __launch_bounds__(FSL_BLOCK) k_ccl_install(StepArgs A, CclArgs K
 
 // ------------------------------------------------------------------ exports
 
+// Lowest cell index of every bubble slot (its canonical id).  The lanes of a
+// warp hold consecutive cells, so among the lanes with the same slot the
+// lowest lane has the lowest index: one atomic per slot and warp.
 __global__ void k_export_minid(const int* id, long long off, int n, int* minidx) {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n) return;
-    const int b = id[off + l];
-    if (b >= 0) atomicMin(&minidx[b], (int)l);
+    const int b = l < n ? id[off + l] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    if (b >= 0 && (int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicMin(&minidx[b], (int)l);
 }
 
 // Cell export; phif (the FP32-collide forms' fill level, null in FP64) takes the
