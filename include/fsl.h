@@ -118,8 +118,9 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
  * levels (interface cells), density and velocity; f = f_eq(rho, u), m = phi
  * rho.  Pointers are host memory (on_device = 0) or device memory on the
  * handle's GPU (on_device = 1); the caller keeps them.  Host data pass through
- * a device staging buffer owned by the handle, allocated on first use and
- * grown when a call needs more (FSL_ERR_CUDA when that fails).  Rejects
+ * a device staging buffer owned by the handle, allocated by fsl_create for the
+ * largest domain's initial state (41 bytes per cell) and grown when a later
+ * call needs more (FSL_ERR_CUDA when that fails).  Rejects
  * (FSL_ERR_GEOMETRY) a liquid cell with a gas neighbour.  Every domain must be
  * initialised before the first step; bubbles are found (flood fill, paper Sec.
  * 2.3.2) with V* = V, p = p0.  Synchronises. */

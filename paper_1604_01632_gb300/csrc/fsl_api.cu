@@ -712,6 +712,16 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     AL(h->mass_part, 8 * (size_t)h->max_dom_blocks);
     AL(h->runs, 16);   // [0] labelling passes, [1] bubbles they relabelled
 #undef AL
+    // the staging buffer of fsl_init_geometry from host buffers, sized for the
+    // largest domain, taken now with every other buffer rather than inside the
+    // first upload (it grows later only for larger exports)
+    if (e == cudaSuccess) {
+        long long nmax = 0;
+        for (const Dom& D : h->hdoms) nmax = std::max(nmax, (long long)D.n);
+        const size_t bytes[4] = {(size_t)nmax, 8 * (size_t)nmax, 8 * (size_t)nmax, 24 * (size_t)nmax};
+        void* parts[4];
+        e = staging(h, bytes, 4, parts);
+    }
     if (e != cudaSuccess) {
         fsl_status st = (e == cudaErrorMemoryAllocation) ? FSL_ERR_OOM : FSL_ERR_CUDA;
         fsl_destroy(h);
