@@ -45,7 +45,8 @@ METRIC = "FSLBM MLUPS & HBM roofline fraction: FP16-store/batched vs plain FP32/
 UNIT = "MLUPS"
 BYTES = {"fp64": 8, "fp32": 4, "f16s": 2, "bf16s": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "f16s": "f32", "bf16s": "f32"}
-KERNEL = "stream-collide kernel (interface and liquid cells, one launch per step)"
+KERNEL = ("stream-collide work of a step (interface and liquid cells): the tuned form's kernels, "
+          "in the 16-bit forms on the foam the normals pass and the tile-fused kernel, timed together")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1604_01632_gb300", "csrc", f) for f in
                   ("fsl_device.cuh", "fsl_fast.cu", "fsl_core.cu")]
