@@ -120,7 +120,9 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
  * handle's GPU (on_device = 1); the caller keeps them.  Host data pass through
  * a device staging buffer owned by the handle, allocated by fsl_create for the
  * largest domain's initial state (41 bytes per cell) and grown when a later
- * call needs more (FSL_ERR_CUDA when that fails).  Rejects
+ * call needs more (FSL_ERR_CUDA when that fails); fill, rho and u in
+ * page-locked host memory (all three) are read by the initialisation kernel in
+ * place instead, and must hold their n (3n for u) values.  Rejects
  * (FSL_ERR_GEOMETRY) a liquid cell with a gas neighbour.  Every domain must be
  * initialised before the first step; bubbles are found (flood fill, paper Sec.
  * 2.3.2) with V* = V, p = p0.  Synchronises. */

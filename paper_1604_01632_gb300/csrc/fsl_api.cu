@@ -787,6 +787,17 @@ fsl_status fsl_create(const fsl_params* params, int32_t n_domains, int32_t preci
     return FSL_OK;
 }
 
+// Device address of page-locked host memory (which the GPU reads in place
+// over the host link), or null for pageable memory.
+static const void* mapped_host(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, const double* fill, const double* rho,
                              const double* u, int32_t on_device) {
     if (!h || d < 0 || d >= h->ndom || !flags || !fill || !rho || !u) return fail(h, FSL_ERR_ARG, "bad argument");
@@ -803,11 +814,19 @@ fsl_status fsl_init_geometry(fsl_domain* h, int32_t d, const uint8_t* flags, con
         dfl = (uint8_t*)parts[0]; dfi = (double*)parts[1]; drh = (double*)parts[2]; du = (double*)parts[3];
         // on the library stream, so that the initialisation kernel below is
         // ordered after the copies (the stream is synchronised before return,
-        // which also covers the caller's host buffers)
+        // which also covers the caller's host buffers).  The cell types are
+        // always staged (the kernel reads each cell's neighbours); fill level,
+        // density and velocity in page-locked memory are read by the kernel
+        // in place, once each, instead of being copied first.
         CK(h, cudaMemcpyAsync(dfl, flags, n, cudaMemcpyHostToDevice, h->ls));
-        CK(h, cudaMemcpyAsync(dfi, fill, 8 * n, cudaMemcpyHostToDevice, h->ls));
-        CK(h, cudaMemcpyAsync(drh, rho, 8 * n, cudaMemcpyHostToDevice, h->ls));
-        CK(h, cudaMemcpyAsync(du, u, 24 * n, cudaMemcpyHostToDevice, h->ls));
+        const void *mfi = mapped_host(fill), *mrh = mapped_host(rho), *mu = mapped_host(u);
+        if (mfi && mrh && mu) {
+            dfi = (double*)mfi; drh = (double*)mrh; du = (double*)mu;
+        } else {
+            CK(h, cudaMemcpyAsync(dfi, fill, 8 * n, cudaMemcpyHostToDevice, h->ls));
+            CK(h, cudaMemcpyAsync(drh, rho, 8 * n, cudaMemcpyHostToDevice, h->ls));
+            CK(h, cudaMemcpyAsync(du, u, 24 * n, cudaMemcpyHostToDevice, h->ls));
+        }
     } else {
         dfl = (uint8_t*)flags; dfi = (double*)fill; drh = (double*)rho; du = (double*)u;
     }
