@@ -357,23 +357,26 @@ def run_gpu(args, rank: int, world: int):
         np.copyto(rho, sc.rho.reshape(-1))
         np.copyto(u, sc.u.reshape(-1))
         res = {"flags": pinned(n, np.uint8), "fill": pinned(n, np.float64), "id": pinned(n, np.int64)}
-        sim = fsl.Simulation([sc.params()], precision=args.precision, stream=int(stream.cuda_stream))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sim.init_geometry(0, flags, fill, rho, u)
-        for seed, extra, rate, constp in sc.sources:
-            sim.set_source(0, seed, extra, rate, constp)
-        sim.step(args.steps)
-        out = sim.fields(0, ("flags", "fill", "id"), out=res)
-        bub = sim.bubbles(0)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        reps = []
+        for _ in range(3):
+            sim = fsl.Simulation([sc.params()], precision=args.precision, stream=int(stream.cuda_stream))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.init_geometry(0, flags, fill, rho, u)
+            for seed, extra, rate, constp in sc.sources:
+                sim.set_source(0, seed, extra, rate, constp)
+            sim.step(args.steps)
+            out = sim.fields(0, ("flags", "fill", "id"), out=res)
+            bub = sim.bubbles(0)
+            torch.cuda.synchronize()
+            reps.append(n * args.steps * world / (time.perf_counter() - t0) / 1e6)
+            sim.close()
         h2d = flags.nbytes + fill.nbytes + rho.nbytes + u.nbytes
         d2h = sum(a.nbytes for a in out.values()) + bub.nbytes
-        e2e = {"value": round(n * args.steps * world / dt / 1e6, 1), "unit": UNIT,
+        e2e = {"value": round(float(np.median(reps)), 1), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps),
-               "note": f"{args.steps} steps per upload and read-back (tuning steps included)"}
-        sim.close()
+               "runs": [round(r, 1) for r in reps],
+               "note": f"median of 3 runs; {args.steps} steps per upload and read-back"}
         del flags, fill, rho, u, res
 
     cpu = cpu_single = None
