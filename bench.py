@@ -478,10 +478,10 @@ def cpu_sample():
     return S.foam(n=CPU_SAMPLE_N)
 
 
-def cpu_baselines(args, steps_omp: int = 8, steps_single: int = 3):
+def cpu_baselines(args, steps_omp: int = 40, steps_single: int = 10):
     """The FP64 oracle as it stands on the host cores: its OpenMP build on all
     cores (os.cpu_count()) and the serial build on one core, on a bounded
-    sample of the headline workload."""
+    sample of the headline workload (about 10 s of host work each)."""
     from oracle import oracle
     sc = cpu_sample()
     cores = os.cpu_count() or 1
